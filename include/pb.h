@@ -1,0 +1,193 @@
+/*
+ * pb.h -- C ABI of libpb: GB300-native (sm_103a) Jacobi-preconditioned CG for
+ * the linear finite-difference Poisson-Boltzmann equation of Qi,
+ * Botello-Smith & Luo, "Acceleration of Linear Finite-Difference
+ * Poisson-Boltzmann Methods on GPUs" (arXiv:1704.02745).
+ *
+ * Problem (Sec. 2.1, Eq. 2-4).  On a uniform nx*ny*nz grid of spacing h the
+ * library solves the h^2-scaled seven-point discretisation of Eq. (3),
+ *
+ *   sum over the six edges e of c:  eps_e (phi_c - phi_nb)
+ *       + kbar^2 h^2 lambda_c phi_c  =  4 pi q_c / h,
+ *
+ * i.e. A phi = b of Eq. (4), where eps_e is the dielectric on the edge between
+ * two nodes (eps_i(i,j,k) of Eq. 3 sits between (i,j,k) and (i+1,j,k)),
+ * lambda is the ion-exclusion mask of Eq. (1)-(2), kbar^2 = eps_out kappa^2
+ * collects the coefficients of the linearised Boltzmann term, and q_c is the
+ * charge of the cube centred on node c.  Units: lengths in Angstrom, charges
+ * in e, phi in e/Angstrom, energies in kcal/mol.
+ *
+ * Conventions shared by every entry point:
+ *  - Node arrays are dense, x fastest: index i + nx*(j + ny*k).
+ *  - Every call returns a pb_status.  Nothing calls exit/abort or traps on the
+ *    device; pb_last_error() returns a message for the calling thread.
+ *  - Host inputs are copied before the call returns.  Device pointers passed
+ *    in are borrowed (the caller keeps ownership).  Grids and servers are
+ *    owned by the library and freed by pb_free_grid / pb_server_destroy.
+ *  - All device work is issued on the context's stream; calls that return
+ *    results to the host synchronise that stream.
+ */
+#ifndef PB_H
+#define PB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pb_status;
+enum {
+    PB_OK = 0,
+    PB_ERR_ARG = 1,           /* bad argument: empty grid, h <= 0, eps <= 0, an atom whose
+                                 trilinear cell leaves the grid, unknown enum value */
+    PB_ERR_OOM = 2,           /* a device allocation failed */
+    PB_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in pb_last_error) */
+    PB_ERR_NOT_CONVERGED = 5, /* iteration cap reached before the tolerance */
+    PB_ERR_BREAKDOWN = 6,     /* p.Ap <= 0 or a non-finite CG scalar */
+    PB_ERR_TIMEOUT = 7,       /* pb_batch_poll: result not ready within the timeout */
+    PB_ERR_BUSY = 8,          /* pb_batch_submit: over the memory budget and queue full */
+    PB_ERR_NOT_FOUND = 9      /* unknown ticket */
+};
+
+/* Storage of the dielectric coefficients used by the FP32 operator. */
+enum {
+    PB_COEF_PACKED = 0, /* one byte per node: six edge flags (eps_in / eps_out) + lambda */
+    PB_COEF_F32 = 1,    /* explicit eps_x, eps_y, eps_z and diagonal arrays, FP32 */
+    PB_COEF_BF16 = 2,   /* explicit eps arrays in BF16 (exact for eps 1 and 80);
+                           the diagonal is rebuilt in FP32 from eps and lambda */
+    PB_COEF_F64 = 3     /* explicit arrays in FP64 (used by the FP64 operator) */
+};
+
+typedef enum { PB_F64 = 0, PB_F32 = 1 } pb_dtype;
+
+/* Arithmetic of a solve. */
+enum {
+    PB_PREC_F64 = 0,        /* the paper's PCG (Sec. 2.2) in FP64 throughout */
+    PB_PREC_F32 = 1,        /* PCG in FP32 (the paper's precision, Sec. 2.7), result
+                               accumulated into FP64 */
+    PB_PREC_F32_REFINE = 2  /* FP32 inner PCG, FP64 outer iterative refinement: true
+                               residual b - A x, accumulation x += d (not in the paper) */
+};
+
+enum { PB_PRECOND_NONE = 0, PB_PRECOND_JACOBI = 1 };
+
+/* Grid and physical parameters (Sec. 2.7: h = 0.5 A, eps 1 / 80, phi0 = 0). */
+typedef struct {
+    int nx, ny, nz;           /* nodes per axis, each >= 1 */
+    double h;                 /* spacing, A, > 0 */
+    double origin[3];         /* position of node (0,0,0), A */
+    double eps_in, eps_out;   /* solute / solvent dielectric, > 0 */
+    double ionic_strength;    /* mol/L of 1:1 salt, >= 0 */
+    double temperature;       /* K, > 0 */
+    int kappa_mask;           /* 1: lambda = 0 at nodes strictly inside an atom; 0: lambda = 1 */
+    int coef;                 /* PB_COEF_*: storage of the FP32 operator's coefficients */
+    int dh_precision;         /* pb_dtype of the Debye-Hueckel boundary sum */
+} pb_grid_desc;
+
+typedef struct {
+    int precond;      /* PB_PRECOND_* (Sec. 2.4: Jacobi, M = diag A) */
+    int precision;    /* PB_PREC_* */
+    double rel_tol;   /* stop when ||r|| / ||b|| < rel_tol (Sec. 2.2 stopping rule) */
+    int max_iter;     /* cap on CG iterations summed over all inner solves */
+    double inner_tol; /* PB_PREC_F32_REFINE: inner solve to ||r_in|| / ||r_outer|| < inner_tol */
+    int max_outer;    /* PB_PREC_F32_REFINE: cap on inner solves */
+    int warm_start;   /* 1: phi holds phi0 on entry; 0: phi0 = 0 */
+    int poll_every;   /* CG iterations per device-graph launch between host checks (0: auto) */
+    int profile;      /* 1: launch kernels one by one with CUDA events around each and report
+                         their device time in pb_solve_info (slower; for measurement only) */
+} pb_solve_opts;
+
+typedef struct {
+    int status;          /* pb_status of the solve */
+    int iterations;      /* CG iterations (alpha updates), summed over inner solves */
+    int outer_steps;     /* inner solves run (1 for PB_PREC_F64 / PB_PREC_F32) */
+    double relres;       /* recursive residual of the last inner solve, relative to its rhs */
+    double relres_true;  /* ||b - A phi|| / ||b|| evaluated in FP64 at exit */
+    /* profile = 1 only: summed device time (ms) and count of the launches of
+     * the stencil pass doing CG work, of the update pass doing CG work, and of
+     * the stencil pass doing the FP64 residual (refinement) work */
+    double ms_stencil, ms_update, ms_resid;
+    int n_stencil, n_update, n_resid;
+} pb_solve_info;
+
+typedef struct pb_ctx pb_ctx;
+typedef struct pb_grid pb_grid;
+typedef struct pb_server pb_server;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pb_last_error(void);
+
+/* Context on CUDA device `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t, borrowed).  NULL: the context creates and owns a
+ * non-blocking stream (the legacy default stream cannot hold device graphs). */
+pb_status pb_create(pb_ctx **out, int device, void *cuda_stream);
+pb_status pb_destroy(pb_ctx *ctx);
+
+/* Running totals of a context since pb_create: CUDA kernels the library has
+ * launched on the device (kernels inside device graphs counted one by one),
+ * and bytes it copied host->device and device->host.  Any pointer may be NULL. */
+pb_status pb_ctx_stats(pb_ctx *ctx, uint64_t *kernel_launches, uint64_t *h2d_bytes,
+                       uint64_t *d2h_bytes);
+
+/* Grid setup on the device (Eq. 3 coefficients; Sec. 2.7 conditions):
+ *  - eps on every edge: eps_in when the edge midpoint lies strictly inside an
+ *    atom sphere (|m - x_a|^2 < r_a^2), else eps_out;
+ *  - lambda = 0 at nodes strictly inside an atom (kappa_mask), else 1;
+ *  - grid charges by trilinear spreading, b = 4 pi q_node / h;
+ *  - Debye-Hueckel Dirichlet values on the ghost faces,
+ *    phi_g = sum_a q_a exp(-kappa r) / (eps_out r), folded into b.
+ * xyz (n_atoms x 3), q and radius are HOST arrays, copied.  n_atoms may be 0.
+ * On success *out owns all device arrays of the grid.  PB_ERR_ARG if an
+ * atom's trilinear cell leaves the grid. */
+pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_atoms, const double *xyz,
+                        const double *q, const double *radius, pb_grid **out);
+pb_status pb_free_grid(pb_grid *grid);
+
+/* Redo the setup of an existing grid for new atoms (a new snapshot of the same
+ * molecule on the same grid): same steps as pb_setup_grid, no allocation
+ * unless n_atoms exceeds every earlier call's.  Host arrays, copied.  The
+ * grid's solve workspace is kept, so the next pb_pcg_solve may warm-start. */
+pb_status pb_grid_update_atoms(pb_grid *grid, int n_atoms, const double *xyz, const double *q,
+                               const double *radius);
+
+/* Au = A u (Eq. 3-4, h^2-scaled; ghost values excluded: they live in b).
+ * u and Au are DEVICE arrays of nx*ny*nz elements of `dtype`, borrowed.
+ * PB_F64 uses the exact FP64 coefficients; PB_F32 uses the grid's FP32
+ * coefficient storage (desc.coef). */
+pb_status pb_apply_operator(pb_grid *grid, const void *u, void *Au, int dtype);
+
+/* Solve A phi = b (Sec. 2.2 preconditioned CG with the Jacobi preconditioner
+ * of Sec. 2.4, or plain CG).  phi is a DEVICE array of nx*ny*nz doubles,
+ * borrowed: phi0 on entry if opts->warm_start, the solution on return.
+ * Returns the solve's status (also in info->status). */
+pb_status pb_pcg_solve(pb_grid *grid, const pb_solve_opts *opts, double *phi,
+                       pb_solve_info *info);
+
+/* Electrostatic energy 1/2 * 332.0637 * sum_nodes q_node phi_node (kcal/mol)
+ * of a DEVICE potential phi (nx*ny*nz doubles, borrowed); the energies that
+ * Sec. 3.1 compares.  Evaluated in FP64 as sum_atoms q_a * (trilinear
+ * interpolation of phi at x_a), the adjoint of the charge spreading. */
+pb_status pb_energy(pb_grid *grid, const double *phi, double *energy_kcal);
+
+/* Export a setup array to HOST memory for inspection (dense layouts):
+ *   PB_EXPORT_EPS_X  double (nz, ny, nx+1): edge between x-nodes i-1 and i at [.., i]
+ *   PB_EXPORT_EPS_Y  double (nz, ny+1, nx)
+ *   PB_EXPORT_EPS_Z  double (nz+1, ny, nx)
+ *   PB_EXPORT_LAMBDA uint8  (nz, ny, nx)
+ *   PB_EXPORT_B      double (nz, ny, nx)
+ *   PB_EXPORT_GHOST  double, faces x-, x+ (nz, ny), y-, y+ (nz, nx), z-, z+ (ny, nx)
+ * `bytes` must equal the array's size. */
+enum { PB_EXPORT_EPS_X = 0, PB_EXPORT_EPS_Y = 1, PB_EXPORT_EPS_Z = 2, PB_EXPORT_LAMBDA = 3,
+       PB_EXPORT_B = 4, PB_EXPORT_GHOST = 5 };
+pb_status pb_grid_export(pb_grid *grid, int what, void *host_dst, size_t bytes);
+
+/* Device bytes a grid of these dimensions holds after setup and a solve of
+ * `precision` (the admission model of the server). */
+size_t pb_grid_bytes(const pb_grid_desc *desc, int precision);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PB_H */

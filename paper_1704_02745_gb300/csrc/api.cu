@@ -1,0 +1,718 @@
+// api.cu -- C ABI of libpb (declared in include/pb.h): contexts, grid setup,
+// operator application, the Jacobi-PCG solve driver and the energy.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pb.h"
+#include "pb_host.h"
+#include "pb_internal.cuh"
+#include "setup.cuh"
+#include "solve.cuh"
+
+using namespace pb;
+
+static thread_local std::string g_err;
+
+pb_status pb_fail(pb_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+extern "C" const char *pb_last_error(void) { return g_err.c_str(); }
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return pb_fail(e_ == cudaErrorMemoryAllocation ? PB_ERR_OOM : PB_ERR_CUDA,            \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+pb_status pb_dalloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return pb_fail(e == cudaErrorMemoryAllocation ? PB_ERR_OOM : PB_ERR_CUDA,
+                   std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  return PB_OK;
+}
+
+static void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
+// Context
+
+extern "C" pb_status pb_create(pb_ctx **out, int device, void *cuda_stream) {
+  if (!out) return pb_fail(PB_ERR_ARG, "pb_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CK(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return pb_fail(PB_ERR_ARG, "pb_create: no such device");
+  CK(cudaSetDevice(device));
+  pb_ctx *c = new pb_ctx();
+  c->device = device;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+    c->own_stream = false;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return pb_fail(PB_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost((void **)&c->host_scal, sizeof(Scal) * 64) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return pb_fail(PB_ERR_CUDA, "cudaMallocHost failed");
+  }
+  *out = c;
+  return PB_OK;
+}
+
+extern "C" pb_status pb_destroy(pb_ctx *c) {
+  if (!c) return PB_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaFreeHost(c->host_scal);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PB_OK;
+}
+
+extern "C" pb_status pb_ctx_stats(pb_ctx *c, uint64_t *launches, uint64_t *h2d, uint64_t *d2h) {
+  if (!c) return pb_fail(PB_ERR_ARG, "pb_ctx_stats: NULL ctx");
+  if (launches) *launches = c->launches;
+  if (h2d) *h2d = c->h2d;
+  if (d2h) *d2h = c->d2h;
+  return PB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Physics constants of the host side.
+
+// Inverse Debye length squared (1/A^2) of a 1:1 salt of ionic strength I
+// (mol/L) at temperature T in a solvent of relative permittivity eps:
+// 2 N_A e^2 (1000 I) / (eps0 eps k_B T) m^-2.
+static double debye_kappa2(double ionic, double temp, double eps) {
+  const double avogadro = 6.02214076e23, charge = 1.602176634e-19;
+  const double vacuum_perm = 8.8541878128e-12, boltzmann = 1.380649e-23;
+  return 2.0 * avogadro * charge * charge * (1000.0 * ionic) /
+         (vacuum_perm * eps * boltzmann * temp) * 1e-20;
+}
+
+static bool finite_all(const double *a, size_t n) {
+  for (size_t t = 0; t < n; t++)
+    if (!std::isfinite(a[t])) return false;
+  return true;
+}
+
+static pb_status check_desc(const pb_grid_desc *d) {
+  if (!d) return pb_fail(PB_ERR_ARG, "grid desc is NULL");
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return pb_fail(PB_ERR_ARG, "empty grid");
+  if ((double)d->nx * d->ny * d->nz > 2.0e9) return pb_fail(PB_ERR_ARG, "grid too large");
+  if (!(d->h > 0) || !std::isfinite(d->h)) return pb_fail(PB_ERR_ARG, "h must be > 0");
+  if (!(d->eps_in > 0) || !(d->eps_out > 0)) return pb_fail(PB_ERR_ARG, "eps must be > 0");
+  if (!(d->ionic_strength >= 0) || !(d->temperature > 0))
+    return pb_fail(PB_ERR_ARG, "ionic strength must be >= 0 and temperature > 0");
+  if (!finite_all(d->origin, 3)) return pb_fail(PB_ERR_ARG, "origin not finite");
+  if (d->coef < PB_COEF_PACKED || d->coef > PB_COEF_F64) return pb_fail(PB_ERR_ARG, "bad coef");
+  if (d->dh_precision != PB_F64 && d->dh_precision != PB_F32)
+    return pb_fail(PB_ERR_ARG, "bad dh_precision");
+  return PB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Grid
+
+void pb_grid_release(pb_grid *g) {
+  if (!g) return;
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  void *ptrs[] = {g->code, g->b, g->ghost, g->xyzq, g->xyzr, g->err, g->scratch, g->ex, g->ey,
+                  g->ez, g->diag, g->ex64, g->ey64, g->ez64, g->diag64, g->x64, g->x64b, g->d32,
+                  g->r32, g->p032, g->p132, g->ap32, g->r64, g->p064, g->p164, g->ap64, g->scal,
+                  g->dinst, g->st_items, g->ch_items, g->st_part, g->ch_part};
+  for (void *p : ptrs) dfree(p);
+  delete g;
+}
+
+extern "C" pb_status pb_free_grid(pb_grid *g) {
+  if (!g) return PB_OK;
+  cudaSetDevice(g->ctx->device);
+  cudaStreamSynchronize(g->ctx->stream);
+  pb_grid_release(g);
+  return PB_OK;
+}
+
+static void tile_plan(pb_grid *g, int num_sms) {
+  const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
+  g->tiles_x = (nx + TX - 1) / TX;
+  g->tiles_y = (ny + TY - 1) / TY;
+  const int txy = g->tiles_x * g->tiles_y;
+  const int target = 4 * num_sms;
+  const int nzc = (target + txy - 1) / txy;
+  int tz = (nz + nzc - 1) / nzc;
+  if (tz < 8) tz = 8;
+  if (tz > nz) tz = nz;
+  g->tz = tz;
+  g->tiles_z = (nz + tz - 1) / tz;
+  g->n_st = g->tiles_x * g->tiles_y * g->tiles_z;
+  g->n_ch = (int)((g->n_pad + CH - 1) / CH);
+}
+
+// (Re)run the setup kernels of a grid for the given host atoms.
+static pb_status run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
+                           const double *radius) {
+  cudaStream_t s = g->ctx->stream;
+  const pb_grid_desc *desc = &g->d;
+  if (n_atoms > g->atom_cap) {
+    if (g->xyzq) cudaFree(g->xyzq);
+    if (g->xyzr) cudaFree(g->xyzr);
+    if (g->scratch) cudaFree(g->scratch);
+    g->xyzq = g->xyzr = nullptr;
+    g->scratch = nullptr;
+    g->atom_cap = 0;
+    pb_status st;
+    if ((st = pb_dalloc((void **)&g->xyzq, (size_t)(n_atoms + 1) * sizeof(dbl4)))) return st;
+    if ((st = pb_dalloc((void **)&g->xyzr, (size_t)(n_atoms + 1) * sizeof(dbl4)))) return st;
+    if ((st = pb_dalloc((void **)&g->scratch, (264 + (size_t)n_atoms / 256 + 1) * sizeof(double))))
+      return st;
+    g->atom_cap = n_atoms;
+  }
+  g->n_atoms = n_atoms;
+  g->hq.resize(n_atoms);
+  g->hr.resize(n_atoms);
+  for (int a = 0; a < n_atoms; a++) {
+    g->hq[a] = dbl4{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], q[a]};
+    g->hr[a] = dbl4{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], radius[a]};
+  }
+  CK(cudaMemcpyAsync(g->xyzq, g->hq.data(), n_atoms * sizeof(dbl4), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g->xyzr, g->hr.data(), n_atoms * sizeof(dbl4), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(g->b, 0, g->n_pad * sizeof(double), s));
+  CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
+  SetupArgs a;
+  a.g = g->g;
+  a.n_atoms = n_atoms;
+  a.atoms_xyzr = g->xyzr;
+  a.atoms_xyzq = g->xyzq;
+  a.code = g->code;
+  a.b = g->b;
+  a.ghost = g->ghost;
+  a.scratch = g->scratch;
+  a.bnorm2 = g->scratch + 256;  // slot after the 256 partials
+  a.err = g->err;
+  a.kappa = g->kappa;
+  a.ein = desc->eps_in;
+  a.eout = desc->eps_out;
+  a.c4pi_h = 4.0 * M_PI / desc->h;
+  {
+    double qsum = 0;
+    for (int t = 0; t < n_atoms; t++) qsum += std::fabs(q[t]);
+    int ex2 = 0;
+    std::frexp(qsum + 1.0, &ex2);  // qsum + 1 < 2^ex2
+    a.q_scale = std::ldexp(1.0, 62 - ex2);
+  }
+  a.kappa_mask = desc->kappa_mask ? 1 : 0;
+  a.dh_f32 = desc->dh_precision == PB_F32;
+  CK(launch_setup(a, s));
+  g->ctx->launches += 5 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
+  g->ctx->h2d += 2 * (unsigned long long)n_atoms * sizeof(dbl4);
+  g->ctx->d2h += sizeof(int) + sizeof(double);
+  if (desc->coef == PB_COEF_F64)
+    CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, COEF_F64, g->ex64,
+                     g->ey64, g->ez64, g->diag64, s));
+  else if (desc->coef != PB_COEF_PACKED)
+    CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, desc->coef, g->ex, g->ey,
+                     g->ez, g->diag, s));
+  int *hbuf = (int *)g->ctx->host_scal;  // pinned staging: error word, then ||b||^2
+  CK(cudaMemcpyAsync(hbuf, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync((double *)hbuf + 1, a.bnorm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hbuf[0]) return pb_fail(PB_ERR_ARG, "an atom's trilinear cell leaves the grid");
+  g->bnorm = std::sqrt(((double *)hbuf)[1]);
+  return PB_OK;
+}
+
+static pb_status check_atoms(int n_atoms, const double *xyz, const double *q, const double *radius) {
+  if (n_atoms < 0) return pb_fail(PB_ERR_ARG, "n_atoms < 0");
+  if (n_atoms > 0 && (!xyz || !q || !radius)) return pb_fail(PB_ERR_ARG, "atom arrays are NULL");
+  if (n_atoms > 0 && (!finite_all(xyz, 3 * (size_t)n_atoms) || !finite_all(q, n_atoms) ||
+                      !finite_all(radius, n_atoms)))
+    return pb_fail(PB_ERR_ARG, "atom arrays hold a non-finite value");
+  return PB_OK;
+}
+
+extern "C" pb_status pb_grid_update_atoms(pb_grid *g, int n_atoms, const double *xyz,
+                                          const double *q, const double *radius) {
+  if (!g) return pb_fail(PB_ERR_ARG, "pb_grid_update_atoms: NULL grid");
+  pb_status st = check_atoms(n_atoms, xyz, q, radius);
+  if (st) return st;
+  CK(cudaSetDevice(g->ctx->device));
+  return run_setup(g, n_atoms, xyz, q, radius);
+}
+
+extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_atoms,
+                                   const double *xyz, const double *q, const double *radius,
+                                   pb_grid **out) {
+  if (!ctx || !out) return pb_fail(PB_ERR_ARG, "pb_setup_grid: NULL ctx or out");
+  *out = nullptr;
+  pb_status st = check_desc(desc);
+  if (st) return st;
+  if ((st = check_atoms(n_atoms, xyz, q, radius))) return st;
+  CK(cudaSetDevice(ctx->device));
+
+  pb_grid *g = new pb_grid();
+  g->ctx = ctx;
+  g->d = *desc;
+  g->n_atoms = n_atoms;
+  const int px = pitch_of(desc->nx);
+  g->g = Geom{desc->nx, desc->ny, desc->nz, px, desc->h, desc->origin[0], desc->origin[1],
+              desc->origin[2]};
+  g->n_pad = (size_t)px * desc->ny * desc->nz;
+  const double kd2 = debye_kappa2(desc->ionic_strength, desc->temperature, desc->eps_out);
+  g->kappa = std::sqrt(kd2);
+  g->kbh2 = desc->eps_out * kd2 * desc->h * desc->h;
+  g->n_ghost = 2L * ((long)desc->ny * desc->nz + (long)desc->nx * desc->nz + (long)desc->nx * desc->ny);
+
+#define ALLOC(ptr, bytes)                                  \
+  do {                                                     \
+    pb_status a_ = pb_dalloc((void **)&(ptr), (bytes));    \
+    if (a_) { pb_grid_release(g); return a_; }             \
+  } while (0)
+  ALLOC(g->code, g->n_pad);
+  ALLOC(g->b, g->n_pad * sizeof(double));
+  ALLOC(g->ghost, g->n_ghost * sizeof(double));
+  ALLOC(g->err, sizeof(int) * 4);
+  if (desc->coef != PB_COEF_PACKED) {
+    const size_t nc = (size_t)px * (desc->ny + 1) * (desc->nz + 1);
+    if (desc->coef == PB_COEF_F64) {
+      ALLOC(g->ex64, g->n_pad * 8); ALLOC(g->ey64, nc * 8); ALLOC(g->ez64, nc * 8);
+      ALLOC(g->diag64, g->n_pad * 8);
+    } else {
+      const size_t es = desc->coef == PB_COEF_BF16 ? 2 : 4;
+      ALLOC(g->ex, g->n_pad * es); ALLOC(g->ey, nc * es); ALLOC(g->ez, nc * es);
+      ALLOC(g->diag, g->n_pad * 4);
+    }
+  }
+
+  st = run_setup(g, n_atoms, xyz, q, radius);
+  if (st) {
+    pb_grid_release(g);
+    return st;
+  }
+  tile_plan(g, ctx->num_sms);
+  *out = g;
+  return PB_OK;
+#undef ALLOC
+}
+
+extern "C" size_t pb_grid_bytes(const pb_grid_desc *d, int precision) {
+  if (!d || d->nx < 1 || d->ny < 1 || d->nz < 1) return 0;
+  const size_t px = pitch_of(d->nx), n = px * d->ny * d->nz;
+  const size_t nc = px * (d->ny + 1) * (d->nz + 1);
+  size_t bytes = n * (1 + 8) + 8 * 2 * ((size_t)d->ny * d->nz + (size_t)d->nx * d->nz + (size_t)d->nx * d->ny);
+  if (d->coef == PB_COEF_F64) bytes += 8 * (2 * n + 2 * nc);
+  else if (d->coef == PB_COEF_F32) bytes += 4 * (2 * n + 2 * nc);
+  else if (d->coef == PB_COEF_BF16) bytes += 2 * (n + 2 * nc) + 4 * n;
+  bytes += 16 * n;  // x64 pair
+  bytes += precision == PB_PREC_F64 ? 32 * n : 20 * n;
+  bytes += n / CH * 16 + n / 256 * 16 + (1 << 16);
+  return bytes;
+}
+
+// ---------------------------------------------------------------------------
+// Instance descriptor of a grid for a solve of (mode, coef).
+
+int pb_inner_coef(const pb_grid *g, int mode) {
+  if (mode == MODE_F64) return g->d.coef == PB_COEF_F64 ? COEF_F64 : COEF_PACKED;
+  if (g->d.coef == PB_COEF_F32 || g->d.coef == PB_COEF_BF16) return g->d.coef;
+  return COEF_PACKED;
+}
+
+pb_status pb_ensure_workspace(pb_grid *g, int mode) {
+  cudaStream_t s = g->ctx->stream;
+  auto alloc0 = [&](void **p, size_t bytes) -> pb_status {
+    if (*p) return PB_OK;
+    pb_status st = pb_dalloc(p, bytes);
+    if (st) return st;
+    if (cudaMemsetAsync(*p, 0, bytes, s) != cudaSuccess) return pb_fail(PB_ERR_CUDA, "memset");
+    return PB_OK;
+  };
+  pb_status st;
+  const size_t n = g->n_pad;
+  if ((st = alloc0((void **)&g->x64, n * 8))) return st;
+  if ((st = alloc0((void **)&g->x64b, n * 8))) return st;
+  if (mode == MODE_F64) {
+    if ((st = alloc0((void **)&g->r64, n * 8))) return st;
+    if ((st = alloc0((void **)&g->p064, n * 8))) return st;
+    if ((st = alloc0((void **)&g->p164, n * 8))) return st;
+    if ((st = alloc0((void **)&g->ap64, n * 8))) return st;
+  } else {
+    if ((st = alloc0(&g->d32, n * 4))) return st;
+    if ((st = alloc0(&g->r32, n * 4))) return st;
+    if ((st = alloc0(&g->p032, n * 4))) return st;
+    if ((st = alloc0(&g->p132, n * 4))) return st;
+    if ((st = alloc0(&g->ap32, n * 4))) return st;
+  }
+  if ((st = alloc0((void **)&g->scal, sizeof(Scal)))) return st;
+  if ((st = alloc0((void **)&g->dinst, sizeof(Inst)))) return st;
+  if (!g->st_items) {
+    std::vector<Item> si(g->n_st), ci(g->n_ch);
+    for (int t = 0; t < g->n_st; t++) si[t] = Item{0, t};
+    for (int t = 0; t < g->n_ch; t++) ci[t] = Item{0, t};
+    if ((st = pb_dalloc((void **)&g->st_items, si.size() * sizeof(Item)))) return st;
+    if ((st = pb_dalloc((void **)&g->ch_items, ci.size() * sizeof(Item)))) return st;
+    if ((st = pb_dalloc((void **)&g->st_part, 2 * sizeof(double) * g->n_st))) return st;
+    if ((st = pb_dalloc((void **)&g->ch_part, 2 * sizeof(double) * g->n_ch))) return st;
+    if (cudaMemcpy(g->st_items, si.data(), si.size() * sizeof(Item), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(g->ch_items, ci.data(), ci.size() * sizeof(Item), cudaMemcpyHostToDevice))
+      return pb_fail(PB_ERR_CUDA, "copy work items");
+  }
+  return PB_OK;
+}
+
+Inst pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef) {
+  Inst I;
+  memset(&I, 0, sizeof(I));
+  I.nx = g->d.nx; I.ny = g->d.ny; I.nz = g->d.nz; I.px = g->g.px;
+  I.tiles_x = g->tiles_x; I.tiles_y = g->tiles_y; I.tiles_z = g->tiles_z; I.tz = g->tz;
+  I.n_st = g->n_st; I.n_ch = g->n_ch;
+  I.st_base = 0; I.ch_base = 0;
+  I.mode = mode;
+  I.precond = o ? (o->precond == PB_PRECOND_JACOBI) : 1;
+  I.coef = coef;
+  I.max_iter = o ? o->max_iter : 0;
+  I.max_outer = o ? o->max_outer : 0;
+  I.tol = o ? o->rel_tol : 0;
+  I.inner_tol = o ? o->inner_tol : 0;
+  I.bnorm = g->bnorm;
+  I.n_pad = g->n_pad;
+  I.code = g->code;
+  if (coef == COEF_F64) {
+    I.ex = g->ex64; I.ey = g->ey64; I.ez = g->ez64; I.diag = g->diag64;
+  } else if (coef == COEF_F32 || coef == COEF_BF16) {
+    I.ex = g->ex; I.ey = g->ey; I.ez = g->ez; I.diag = g->diag;
+  }
+  I.x64 = g->x64; I.x64b = g->x64b;
+  I.b = g->b;
+  if (mode == MODE_F64) {
+    I.d = nullptr; I.r = g->r64; I.p0 = g->p064; I.p1 = g->p164; I.ap = g->ap64;
+  } else {
+    I.d = g->d32; I.r = g->r32; I.p0 = g->p032; I.p1 = g->p132; I.ap = g->ap32;
+  }
+  I.s = g->scal;
+  const double ein = g->d.eps_in, eout = g->d.eps_out;
+  I.ein = ein; I.eout = eout; I.kbh2 = g->kbh2;
+  I.ein32 = (float)ein; I.eout32 = (float)eout;
+  for (int nin = 0; nin <= 6; nin++)
+    for (int lam = 0; lam <= 1; lam++) {
+      double s = 0;
+      float s32 = 0;
+      for (int t = 0; t < 6; t++) {
+        s = s + (t < nin ? ein : eout);
+        s32 = s32 + (t < nin ? (float)ein : (float)eout);
+      }
+      s = s + g->kbh2 * lam;
+      s32 = s32 + (float)g->kbh2 * (float)lam;
+      I.dtab[2 * nin + lam] = s;
+      I.idtab[2 * nin + lam] = 1.0 / s;
+      I.dtab32[2 * nin + lam] = s32;
+      I.idtab32[2 * nin + lam] = 1.0f / s32;
+    }
+  return I;
+}
+
+Scal pb_initial_scal() {
+  Scal S;
+  memset(&S, 0, sizeof(S));
+  S.phase = PH_RESID;
+  S.ref_norm = 1.0;
+  S.rz_old = 1.0;
+  return S;
+}
+
+// ---------------------------------------------------------------------------
+// Operator, solve, energy
+
+extern "C" pb_status pb_apply_operator(pb_grid *g, const void *u, void *au, int dtype) {
+  if (!g || !u || !au) return pb_fail(PB_ERR_ARG, "pb_apply_operator: NULL argument");
+  if (dtype != PB_F64 && dtype != PB_F32) return pb_fail(PB_ERR_ARG, "bad dtype");
+  CK(cudaSetDevice(g->ctx->device));
+  const int mode = dtype == PB_F64 ? MODE_F64 : MODE_F32;
+  pb_status st = pb_ensure_workspace(g, mode);
+  if (st) return st;
+  Inst I = pb_make_inst(g, nullptr, mode, pb_inner_coef(g, mode));
+  cudaStream_t s = g->ctx->stream;
+  CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
+  CK(launch_apply(I, g->dinst, u, au, dtype == PB_F64 ? 0 : 1, s));
+  g->ctx->launches += 1;
+  CK(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
+static pb_status check_opts(const pb_solve_opts *o) {
+  if (!o) return pb_fail(PB_ERR_ARG, "opts is NULL");
+  if (o->precision < PB_PREC_F64 || o->precision > PB_PREC_F32_REFINE)
+    return pb_fail(PB_ERR_ARG, "bad precision");
+  if (o->precond != PB_PRECOND_NONE && o->precond != PB_PRECOND_JACOBI)
+    return pb_fail(PB_ERR_ARG, "bad precond");
+  if (!(o->rel_tol > 0) || o->max_iter < 0) return pb_fail(PB_ERR_ARG, "bad tolerance or max_iter");
+  if (o->precision == PB_PREC_F32_REFINE && (!(o->inner_tol > 0) || o->max_outer < 1))
+    return pb_fail(PB_ERR_ARG, "refinement needs inner_tol > 0 and max_outer >= 1");
+  return PB_OK;
+}
+
+Batch pb_single_batch(pb_grid *g) {
+  Batch B;
+  B.inst = g->dinst;
+  B.st_items = g->st_items;
+  B.ch_items = g->ch_items;
+  B.n_st_items = g->n_st;
+  B.n_ch_items = g->n_ch;
+  B.st_part = g->st_part;
+  B.ch_part = g->ch_part;
+  B.error = g->err;
+  return B;
+}
+
+static int auto_ticks(const pb_grid *g) {
+  // enough work per host check that the poll is cheap, few enough that a
+  // converged solve does not idle long
+  const double n = (double)g->n_pad;
+  if (n >= 4e6) return 8;
+  if (n >= 5e5) return 16;
+  return 32;
+}
+
+pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
+  cudaStream_t s = g->ctx->stream;
+  if (!g->graph || g->graph_mode != mode || g->graph_coef != coef || g->graph_ticks != ticks) {
+    if (g->graph) {
+      cudaGraphExecDestroy(g->graph);
+      g->graph = nullptr;
+    }
+    KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms);
+    kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
+    kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
+    Batch B = pb_single_batch(g);
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int t = 0; t < ticks; t++) {
+      cudaError_t e = launch_tick(B, mode, coef, kg, s);
+      if (e != cudaSuccess) {
+        cudaStreamEndCapture(s, &graph);
+        return pb_fail(PB_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+      }
+    }
+    CK(cudaStreamEndCapture(s, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return pb_fail(PB_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e));
+    g->graph_mode = mode;
+    g->graph_coef = coef;
+    g->graph_ticks = ticks;
+  }
+  CK(cudaGraphLaunch(g->graph, s));
+  g->ctx->launches += 2ull * ticks;
+  return PB_OK;
+}
+
+// Measurement mode: every kernel launched on its own between CUDA events,
+// with a synchronisation after each so that its work kind is known.
+static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, pb_solve_info *info) {
+  cudaStream_t s = g->ctx->stream;
+  KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms);
+  kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
+  kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
+  Batch B = pb_single_batch(g);
+  Scal *hs = g->ctx->host_scal;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  pb_solve_info acc;
+  memset(&acc, 0, sizeof(acc));
+  int phase = PH_RESID;
+  pb_status st = PB_OK;
+  for (long t = 0; t < 2 * max_ticks; t++) {
+    const int which = (t & 1) ? 2 : 1;
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (!e) e = launch_phase(B, mode, coef, kg, which, s);
+    if (!e) e = cudaEventRecord(e1, s);
+    if (!e) e = cudaMemcpyAsync(hs, g->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    float ms = 0;
+    if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e) {
+      st = pb_fail(PB_ERR_CUDA, std::string("profiled launch: ") + cudaGetErrorString(e));
+      break;
+    }
+    g->ctx->launches += 1;
+    g->ctx->d2h += sizeof(Scal);
+    if (which == 1) {
+      if (phase == PH_RESID) { acc.ms_resid += ms; acc.n_resid++; }
+      else if (phase != PH_DONE) { acc.ms_stencil += ms; acc.n_stencil++; }
+    } else if (phase == PH_INNER) {
+      acc.ms_update += ms;
+      acc.n_update++;
+    }
+    phase = hs->phase;
+    if (phase == PH_DONE) break;
+  }
+  if (phase != PH_DONE && !st) hs->status = PB_ERR_TIMEOUT;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->ms_stencil = acc.ms_stencil; info->n_stencil = acc.n_stencil;
+    info->ms_update = acc.ms_update; info->n_update = acc.n_update;
+    info->ms_resid = acc.ms_resid; info->n_resid = acc.n_resid;
+  }
+  return st;
+}
+
+extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *phi,
+                                  pb_solve_info *info) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!g || !phi) return pb_fail(PB_ERR_ARG, "pb_pcg_solve: NULL grid or phi");
+  pb_status st = check_opts(o);
+  if (st) return st;
+  CK(cudaSetDevice(g->ctx->device));
+  cudaStream_t s = g->ctx->stream;
+  const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
+  if (g->bnorm == 0.0) {  // A phi = 0 has the solution phi = 0
+    CK(cudaMemsetAsync(phi, 0, n * sizeof(double), s));
+    CK(cudaStreamSynchronize(s));
+    if (info) info->status = PB_OK;
+    return PB_OK;
+  }
+  const int mode = o->precision == PB_PREC_F64 ? MODE_F64
+                   : o->precision == PB_PREC_F32 ? MODE_F32 : MODE_F32_REFINE;
+  const int coef = pb_inner_coef(g, mode);
+  if ((st = pb_ensure_workspace(g, mode))) return st;
+  pb_solve_opts oo = *o;
+  if (mode != MODE_F32_REFINE) oo.max_outer = 1;
+  Inst I = pb_make_inst(g, &oo, mode, coef);
+  Scal S0 = pb_initial_scal();
+  CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g->scal, &S0, sizeof(Scal), cudaMemcpyHostToDevice, s));
+  g->ctx->h2d += sizeof(Inst) + sizeof(Scal);
+  if (o->warm_start) {
+    CK(launch_pack(phi, g->x64, g->d.nx, g->d.ny, g->d.nz, g->g.px, s));
+    g->ctx->launches += 1;
+  } else {
+    CK(cudaMemsetAsync(g->x64, 0, g->n_pad * sizeof(double), s));
+  }
+  const int ticks = o->poll_every > 0 ? o->poll_every : auto_ticks(g);
+  // every tick advances at least one phase step; bound the host loop
+  const long max_ticks = (long)oo.max_iter + 2L * (oo.max_outer + 2) + 4L * ticks;
+  Scal *hs = g->ctx->host_scal;
+  long done_ticks = 0;
+  if (o->profile) {
+    if ((st = profiled_loop(g, mode, coef, max_ticks, info))) return st;
+  } else {
+    for (;;) {
+      if ((st = pb_run_ticks(g, mode, coef, ticks))) return st;
+      done_ticks += ticks;
+      CK(cudaMemcpyAsync(hs, g->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+      g->ctx->d2h += sizeof(Scal);
+      CK(cudaStreamSynchronize(s));
+      if (hs->phase == PH_DONE) break;
+      if (done_ticks > max_ticks) {
+        hs->status = PB_ERR_TIMEOUT;
+        break;
+      }
+    }
+  }
+  const Scal S = *hs;
+  CK(launch_unpack(S.xbuf ? g->x64b : g->x64, phi, g->d.nx, g->d.ny, g->d.nz, g->g.px, s));
+  g->ctx->launches += 1;
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    info->status = S.status;
+    info->iterations = S.total_iter;
+    info->outer_steps = S.outer;
+    info->relres = S.relres;
+    info->relres_true = S.relres_true;
+  }
+  if (S.status != PB_OK) {
+    const char *why = S.status == PB_ERR_NOT_CONVERGED ? "iteration cap reached"
+                      : S.status == PB_ERR_BREAKDOWN   ? "CG breakdown (p.Ap <= 0 or non-finite)"
+                                                       : "solve did not finish";
+    return pb_fail(S.status, why);
+  }
+  return PB_OK;
+}
+
+extern "C" pb_status pb_energy(pb_grid *g, const double *phi, double *energy) {
+  if (!g || !phi || !energy) return pb_fail(PB_ERR_ARG, "pb_energy: NULL argument");
+  CK(cudaSetDevice(g->ctx->device));
+  cudaStream_t s = g->ctx->stream;
+  // scratch[0] receives the energy, scratch[8..] the per-CTA partials
+  CK(launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.h, g->d.origin[0],
+                   g->d.origin[1], g->d.origin[2], phi, g->scratch + 8, g->scratch, s));
+  CK(cudaMemcpyAsync(energy, g->scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+  g->ctx->launches += g->n_atoms > 0 ? 2 : 1;
+  g->ctx->d2h += sizeof(double);
+  CK(cudaStreamSynchronize(s));
+  return PB_OK;
+}
+
+extern "C" pb_status pb_grid_export(pb_grid *g, int what, void *dst, size_t bytes) {
+  if (!g || !dst) return pb_fail(PB_ERR_ARG, "pb_grid_export: NULL argument");
+  CK(cudaSetDevice(g->ctx->device));
+  cudaStream_t s = g->ctx->stream;
+  const size_t nx = g->d.nx, ny = g->d.ny, nz = g->d.nz, px = g->g.px;
+  auto need = [&](size_t b) { return bytes == b; };
+  if (what == PB_EXPORT_B) {
+    if (!need(nx * ny * nz * 8)) return pb_fail(PB_ERR_ARG, "export: size mismatch");
+    CK(cudaMemcpy2DAsync(dst, nx * 8, g->b, px * 8, nx * 8, ny * nz, cudaMemcpyDeviceToHost, s));
+  } else if (what == PB_EXPORT_GHOST) {
+    if (!need(g->n_ghost * 8)) return pb_fail(PB_ERR_ARG, "export: size mismatch");
+    CK(cudaMemcpyAsync(dst, g->ghost, g->n_ghost * 8, cudaMemcpyDeviceToHost, s));
+  } else if (what == PB_EXPORT_LAMBDA) {
+    if (!need(nx * ny * nz)) return pb_fail(PB_ERR_ARG, "export: size mismatch");
+    uint8_t *tmp = nullptr;
+    pb_status st = pb_dalloc((void **)&tmp, nx * ny * nz);
+    if (st) return st;
+    cudaError_t e = launch_export_lambda(g->code, g->g, tmp, s);
+    if (!e) e = cudaMemcpyAsync(dst, tmp, nx * ny * nz, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (e) return pb_fail(PB_ERR_CUDA, cudaGetErrorString(e));
+  } else if (what >= PB_EXPORT_EPS_X && what <= PB_EXPORT_EPS_Z) {
+    const size_t nc = px * (ny + 1) * (nz + 1);
+    size_t width, height;
+    if (what == PB_EXPORT_EPS_X) { width = nx + 1; height = ny * nz; }
+    else if (what == PB_EXPORT_EPS_Y) { width = nx; height = (ny + 1) * nz; }
+    else { width = nx; height = ny * (nz + 1); }
+    if (!need(width * height * 8)) return pb_fail(PB_ERR_ARG, "export: size mismatch");
+    double *ex = nullptr, *ey = nullptr, *ez = nullptr;
+    pb_status st;
+    if ((st = pb_dalloc((void **)&ex, nc * 8))) return st;
+    if ((st = pb_dalloc((void **)&ey, nc * 8))) { cudaFree(ex); return st; }
+    if ((st = pb_dalloc((void **)&ez, nc * 8))) { cudaFree(ex); cudaFree(ey); return st; }
+    cudaError_t e = launch_expand(g->code, g->g, g->d.eps_in, g->d.eps_out, g->kbh2, COEF_F64, ex,
+                                  ey, ez, nullptr, s);
+    const double *src = what == PB_EXPORT_EPS_X ? ex : what == PB_EXPORT_EPS_Y ? ey : ez;
+    if (!e) e = cudaMemcpy2DAsync(dst, width * 8, src, px * 8, width * 8, height,
+                                  cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaFree(ex); cudaFree(ey); cudaFree(ez);
+    if (e) return pb_fail(PB_ERR_CUDA, cudaGetErrorString(e));
+  } else {
+    return pb_fail(PB_ERR_ARG, "export: unknown array");
+  }
+  CK(cudaStreamSynchronize(s));
+  return PB_OK;
+}

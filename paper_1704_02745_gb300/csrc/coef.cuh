@@ -1,0 +1,73 @@
+// coef.cuh -- decoding of the operator coefficients of Eq. (3) (h^2-scaled)
+// for one node, shared by the phase kernels and the helper kernels.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "pb_internal.cuh"
+
+namespace pb {
+
+template <typename T> __device__ __forceinline__ T tab_d(const Inst &I, int k);
+template <> __device__ __forceinline__ float tab_d<float>(const Inst &I, int k) { return I.dtab32[k]; }
+template <> __device__ __forceinline__ double tab_d<double>(const Inst &I, int k) { return I.dtab[k]; }
+template <typename T> __device__ __forceinline__ T tab_i(const Inst &I, int k);
+template <> __device__ __forceinline__ float tab_i<float>(const Inst &I, int k) { return I.idtab32[k]; }
+template <> __device__ __forceinline__ double tab_i<double>(const Inst &I, int k) { return I.idtab[k]; }
+template <typename T> __device__ __forceinline__ T e_in(const Inst &I);
+template <> __device__ __forceinline__ float e_in<float>(const Inst &I) { return I.ein32; }
+template <> __device__ __forceinline__ double e_in<double>(const Inst &I) { return I.ein; }
+template <typename T> __device__ __forceinline__ T e_out(const Inst &I);
+template <> __device__ __forceinline__ float e_out<float>(const Inst &I) { return I.eout32; }
+template <> __device__ __forceinline__ double e_out<double>(const Inst &I) { return I.eout; }
+
+template <int CM> struct Store;  // storage type of explicit edge coefficients
+template <> struct Store<COEF_PACKED> { typedef float type; };
+template <> struct Store<COEF_F32> { typedef float type; };
+template <> struct Store<COEF_BF16> { typedef __nv_bfloat16 type; };
+template <> struct Store<COEF_F64> { typedef double type; };
+
+__device__ __forceinline__ float cvt(float v) { return v; }
+__device__ __forceinline__ double cvt(double v) { return v; }
+__device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> struct NodeCoef { T exm, exp, eym, eyp, ezm, ezp, diag; };
+
+// Coefficients of node e = (k*ny + j)*px + i for the operator of precision T.
+template <typename T, int CM>
+__device__ __forceinline__ NodeCoef<T> node_coef(const Inst &I, size_t e, int k) {
+  NodeCoef<T> c;
+  if (CM == COEF_PACKED) {
+    const uint32_t b = I.code[e];
+    const T ei = e_in<T>(I), eo = e_out<T>(I);
+    c.exm = (b & 1u) ? ei : eo; c.exp = (b & 2u) ? ei : eo;
+    c.eym = (b & 4u) ? ei : eo; c.eyp = (b & 8u) ? ei : eo;
+    c.ezm = (b & 16u) ? ei : eo; c.ezp = (b & 32u) ? ei : eo;
+    c.diag = tab_d<T>(I, dtab_index(b));
+  } else {
+    typedef typename Store<CM>::type C;
+    const C *ex = (const C *)I.ex, *ey = (const C *)I.ey, *ez = (const C *)I.ez;
+    const size_t px = I.px, ey0 = e + (size_t)k * px, plane = px * I.ny;
+    c.exm = (T)cvt(ex[e]); c.exp = (T)cvt(ex[e + 1]);
+    c.eym = (T)cvt(ey[ey0]); c.eyp = (T)cvt(ey[ey0 + px]);
+    c.ezm = (T)cvt(ez[e]); c.ezp = (T)cvt(ez[e + plane]);
+    c.diag = ((const T *)I.diag)[e];
+  }
+  return c;
+}
+
+// z = M^-1 r at node e (Jacobi), or z = r without preconditioner.
+template <typename T, int CM>
+__device__ __forceinline__ T zval(const Inst &I, size_t e, T r) {
+  if (!I.precond) return r;
+  if (CM == COEF_PACKED) return r * tab_i<T>(I, dtab_index(I.code[e]));
+  return r / ((const T *)I.diag)[e];
+}
+
+// Exact FP64 operator coefficients (from the codes, or the FP64 arrays).
+template <int CM>
+__device__ __forceinline__ NodeCoef<double> node_coef64(const Inst &I, size_t e, int k) {
+  if (CM == COEF_F64) return node_coef<double, COEF_F64>(I, e, k);
+  return node_coef<double, COEF_PACKED>(I, e, k);
+}
+
+}  // namespace pb

@@ -1,0 +1,56 @@
+// pb_host.h -- host-side objects of libpb shared by the C-ABI translation units.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "pb.h"
+#include "pb_internal.cuh"
+#include "setup.cuh"
+
+struct pb_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 1;
+  pb::Scal *host_scal = nullptr;  // pinned, for convergence polls
+  unsigned long long launches = 0, h2d = 0, d2h = 0;  // pb_ctx_stats counters
+};
+
+struct pb_grid {
+  pb_ctx *ctx = nullptr;
+  pb_grid_desc d{};
+  pb::Geom g{};
+  size_t n_pad = 0;
+  long n_ghost = 0;
+  int n_atoms = 0, atom_cap = 0;
+  std::vector<pb::dbl4> hq, hr;  // host staging of the atoms
+  double kappa = 0, kbh2 = 0, bnorm = 0;
+  // setup arrays
+  uint8_t *code = nullptr;
+  double *b = nullptr, *ghost = nullptr, *scratch = nullptr;
+  pb::dbl4 *xyzq = nullptr, *xyzr = nullptr;
+  int *err = nullptr;
+  // explicit coefficients (FP32 / BF16 eps with an FP32 diagonal, or FP64)
+  void *ex = nullptr, *ey = nullptr, *ez = nullptr, *diag = nullptr;
+  void *ex64 = nullptr, *ey64 = nullptr, *ez64 = nullptr, *diag64 = nullptr;
+  // solve workspace
+  double *x64 = nullptr, *x64b = nullptr;
+  void *d32 = nullptr, *r32 = nullptr, *p032 = nullptr, *p132 = nullptr, *ap32 = nullptr;
+  double *r64 = nullptr, *p064 = nullptr, *p164 = nullptr, *ap64 = nullptr;
+  pb::Scal *scal = nullptr;
+  pb::Inst *dinst = nullptr;
+  pb::Item *st_items = nullptr, *ch_items = nullptr;
+  double *st_part = nullptr, *ch_part = nullptr;
+  int tiles_x = 0, tiles_y = 0, tiles_z = 0, tz = 0, n_st = 0, n_ch = 0;
+  // cached device graph of `graph_ticks` ticks
+  cudaGraphExec_t graph = nullptr;
+  int graph_mode = -1, graph_coef = -1, graph_ticks = 0;
+};
+
+pb_status pb_fail(pb_status s, const std::string &msg);
+pb_status pb_dalloc(void **p, size_t bytes);
+void pb_grid_release(pb_grid *g);
+int pb_inner_coef(const pb_grid *g, int mode);
+pb_status pb_ensure_workspace(pb_grid *g, int mode);
+pb::Inst pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef);
+pb::Scal pb_initial_scal();

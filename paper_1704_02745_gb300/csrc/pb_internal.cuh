@@ -1,0 +1,108 @@
+// pb_internal.cuh -- device data layout and shared definitions of libpb.
+//
+// HBM layout of one grid (all node arrays padded in x to a pitch px, a
+// multiple of 4 elements with px >= nx + 1, so every row starts 16-byte
+// aligned and the (nx+1)-th x-edge fits in the row):
+//   code   uint8  [nz][ny][px]   packed coefficients, one byte per node:
+//                                bit 0/1 x-/x+ edge inside (eps_in), bit 2/3 y-/y+,
+//                                bit 4/5 z-/z+, bit 6 lambda (1 = ion accessible);
+//                                pad bytes are 0
+//   b      f64    [nz][ny][px]   right-hand side of Eq. (4) with the boundary folded in
+//   x64    f64    [nz][ny][px]   solution (FP64)
+//   d,r,p0,p1,ap  T [nz][ny][px] CG work vectors in the inner precision T
+//   ex     C      [nz][ny][px]   explicit modes only: edge (i-1, i) at column i, i = 0..nx
+//   ey     C      [nz][ny+1][px] edge (j-1, j) at row j
+//   ez     C      [nz+1][ny][px] edge (k-1, k) at plane k
+//   diag   C      [nz][ny][px]   explicit modes only (pads hold 1)
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace pb {
+
+struct __align__(32) dbl4 {  // four doubles, 32-byte aligned (atoms: x, y, z, q or radius)
+  double x, y, z, w;
+};
+
+// Tile of the stencil kernels: TX x TY columns marching over a z range.
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NT = TX * TY;  // threads per CTA
+constexpr int CH = 4096;     // elements per chunk of the elementwise kernels
+constexpr int NDTAB = 14;    // diagonal table entries: (#inside edges 0..6) x (lambda 0/1)
+
+// RESID: FP64 residual pass pending; START: first iteration of an inner solve;
+// INNER: CG iterations; DONE: finished (convergence mask off).
+enum Phase : int { PH_RESID = 0, PH_INNER = 1, PH_DONE = 2, PH_START = 3 };
+enum Mode : int { MODE_F64 = 0, MODE_F32 = 1, MODE_F32_REFINE = 2 };
+enum Coef : int { COEF_PACKED = 0, COEF_F32 = 1, COEF_BF16 = 2, COEF_F64 = 3 };
+
+// Per-instance scalars of the CG recurrences (device resident, written only
+// by the finalising CTA of each phase kernel).
+struct Scal {
+  double alpha;        // alpha of the latest step; folded into x by the next kernel
+  double beta;         // beta for the next direction update
+  double rz_old;       // r.z of the current residual
+  double ref_norm;     // ||rhs|| of the current inner solve
+  double relres;       // recursive residual / ref_norm
+  double relres_true;  // ||b - A x|| / ||b|| (FP64)
+  int phase;           // Phase
+  int pbuf;            // index of the buffer holding the latest direction p
+  int iter;            // iterations of the current inner solve
+  int total_iter;      // iterations over all inner solves
+  int outer;           // inner solves started
+  int status;          // pb_status
+  unsigned cnt2, cnt3;  // tile-completion counters (last-CTA-done pattern)
+  int xbuf;             // which of x64 / x64b holds the current solution
+};
+
+// Everything a phase kernel needs to know about one instance (one grid).
+struct Inst {
+  int nx, ny, nz, px;
+  int tiles_x, tiles_y, tiles_z, tz;  // stencil tile decomposition
+  int n_st, n_ch;                     // stencil tiles, elementwise chunks
+  int st_base, ch_base;               // offsets into the partial-sum arrays
+  int mode, precond, coef, max_iter, max_outer, pad0;
+  double tol, inner_tol, bnorm;
+  size_t n_pad;                       // nz*ny*px
+  const uint8_t *code;
+  const void *ex, *ey, *ez, *diag;    // explicit coefficient arrays (inner precision)
+  double *x64, *x64b;                 // solution, double-buffered across RESID passes
+  const double *b;
+  void *d, *r, *p0, *p1, *ap;         // inner work vectors
+  Scal *s;
+  double ein, eout, kbh2;
+  double dtab[NDTAB], idtab[NDTAB];   // FP64 diagonal and its inverse by (n_in, lambda)
+  float dtab32[NDTAB], idtab32[NDTAB];
+  float ein32, eout32;
+};
+
+struct Item {  // one unit of work of a phase kernel
+  int inst;
+  int tile;
+};
+
+struct Batch {  // device pointers describing a batch of instances
+  const Inst *inst;
+  const Item *st_items;  // stencil tiles of all instances
+  const Item *ch_items;  // elementwise chunks of all instances
+  int n_st_items, n_ch_items;
+  double *st_part;       // 3 doubles per stencil tile
+  double *ch_part;       // 2 doubles per chunk
+  int *error;            // device error word
+};
+
+__host__ __device__ inline int dtab_index(uint32_t c) {
+#ifdef __CUDA_ARCH__
+  return 2 * __popc(c & 63u) + ((c >> 6) & 1u);
+#else
+  return 2 * __builtin_popcount(c & 63u) + ((c >> 6) & 1u);
+#endif
+}
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+inline int pitch_of(int nx) { return round_up(nx + 1, 4); }
+
+}  // namespace pb

@@ -1,0 +1,393 @@
+// setup.cu -- grid setup kernels (dielectric map, lambda, charges, Debye-Hueckel
+// boundary, right-hand side) of the linear FDPB method, arXiv:1704.02745
+// Sec. 2.1 (Eq. 3-4) and Sec. 2.7 (eps 1 / 80, free-space boundary).
+//
+// Coordinates are evaluated exactly as: node  o + i*h,  edge midpoint
+// o + (i + 0.5)*h, and the inside test |m - x_a|^2 < r_a^2 as
+// (dx*dx + dy*dy) + dz*dz, each operation rounded on its own (__d*_rn), so
+// the dielectric map is the same bit pattern whatever the evaluation order.
+#include "pb_internal.cuh"
+#include "setup.cuh"
+
+namespace pb {
+
+// ---------------------------------------------------------------------------
+// Packed codes: start with every edge outside (eps_out) and lambda = 1.
+__global__ void k_init_code(uint8_t *code, int nx, int px, size_t n_pad, uint8_t init) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e < n_pad; e += (size_t)gridDim.x * blockDim.x) code[e] = ((int)(e % px) < nx) ? init : 0;
+}
+
+__device__ __forceinline__ void set_bits(uint32_t *code32, size_t e, uint32_t bits) {
+  atomicOr(code32 + (e >> 2), bits << ((e & 3) * 8));
+}
+__device__ __forceinline__ void clear_bits(uint32_t *code32, size_t e, uint32_t bits) {
+  atomicAnd(code32 + (e >> 2), ~(bits << ((e & 3) * 8)));
+}
+
+__device__ __forceinline__ bool inside_sphere(double mx, double my, double mz, double ax, double ay,
+                                              double az, double r2) {
+  double dx = __dsub_rn(mx, ax), dy = __dsub_rn(my, ay), dz = __dsub_rn(mz, az);
+  double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+  return d2 < r2;
+}
+
+__device__ __forceinline__ double node_coord(double o, long i, double h) {
+  return __dadd_rn(o, __dmul_rn((double)i, h));
+}
+__device__ __forceinline__ double mid_coord(double o, long i, double h) {
+  return __dadd_rn(o, __dmul_rn(__dadd_rn((double)i, 0.5), h));
+}
+
+// One CTA per atom: every x/y/z edge and node of the atom's bounding box (one
+// spacing of margin) is tested; an inside edge sets the matching bit of both
+// nodes it joins, an inside node clears its lambda bit.  Writes are OR/AND of
+// the same bits, so the result does not depend on atom order.
+__global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *code32,
+                              int kappa_mask) {
+  const int a = blockIdx.x;
+  if (a >= n_atoms) return;
+  const dbl4 A = atoms[a];  // x, y, z, radius
+  const double r2 = __dmul_rn(A.w, A.w);
+  const long i0 = (long)floor(__ddiv_rn(A.x - A.w - g.ox, g.h)) - 1;
+  const long i1 = (long)ceil(__ddiv_rn(A.x + A.w - g.ox, g.h)) + 1;
+  const long j0 = (long)floor(__ddiv_rn(A.y - A.w - g.oy, g.h)) - 1;
+  const long j1 = (long)ceil(__ddiv_rn(A.y + A.w - g.oy, g.h)) + 1;
+  const long k0 = (long)floor(__ddiv_rn(A.z - A.w - g.oz, g.h)) - 1;
+  const long k1 = (long)ceil(__ddiv_rn(A.z + A.w - g.oz, g.h)) + 1;
+  const size_t rowp = (size_t)g.px, plane = (size_t)g.px * g.ny;
+  for (int kind = 0; kind < 4; kind++) {
+    // kind 0: x-edges (i from -1), 1: y-edges (j from -1), 2: z-edges (k from -1), 3: nodes
+    if (kind == 3 && !kappa_mask) break;
+    long ia = max(i0, kind == 0 ? -1L : 0L), ib = min(i1, (long)g.nx - 1);
+    long ja = max(j0, kind == 1 ? -1L : 0L), jb = min(j1, (long)g.ny - 1);
+    long ka = max(k0, kind == 2 ? -1L : 0L), kb = min(k1, (long)g.nz - 1);
+    if (ia > ib || ja > jb || ka > kb) continue;
+    const long ni = ib - ia + 1, nj = jb - ja + 1, nk = kb - ka + 1;
+    const long cnt = ni * nj * nk;
+    for (long t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const long i = ia + t % ni, j = ja + (t / ni) % nj, k = ka + t / (ni * nj);
+      double mx = kind == 0 ? mid_coord(g.ox, i, g.h) : node_coord(g.ox, i, g.h);
+      double my = kind == 1 ? mid_coord(g.oy, j, g.h) : node_coord(g.oy, j, g.h);
+      double mz = kind == 2 ? mid_coord(g.oz, k, g.h) : node_coord(g.oz, k, g.h);
+      if (!inside_sphere(mx, my, mz, A.x, A.y, A.z, r2)) continue;
+      if (kind == 0) {
+        if (i >= 0) set_bits(code32, k * plane + j * rowp + i, 2u);            // x+ of node i
+        if (i + 1 < g.nx) set_bits(code32, k * plane + j * rowp + i + 1, 1u);  // x- of node i+1
+      } else if (kind == 1) {
+        if (j >= 0) set_bits(code32, k * plane + j * rowp + i, 8u);
+        if (j + 1 < g.ny) set_bits(code32, k * plane + (j + 1) * rowp + i, 4u);
+      } else if (kind == 2) {
+        if (k >= 0) set_bits(code32, k * plane + j * rowp + i, 32u);
+        if (k + 1 < g.nz) set_bits(code32, (k + 1) * plane + j * rowp + i, 16u);
+      } else {
+        clear_bits(code32, k * plane + j * rowp + i, 64u);
+      }
+    }
+  }
+}
+
+// Trilinear charge spreading: f = (x - o)/h, i0 = floor(f), w = f - i0; the
+// 8 corner weights per axis are w or 1 - w, the contribution ((q*wx)*wy)*wz.
+// Contributions are accumulated as 64-bit fixed point (rounded to a multiple
+// of 1/scale, scale a power of two with sum|q| * scale <= 2^62): integer
+// addition is associative, so the grid charges do not depend on the order in
+// which the atomics land.  An atom whose cell leaves the grid sets *err.
+__global__ void k_spread(const dbl4 *xyzq, int n_atoms, Geom g, double scale,
+                         unsigned long long *qn, int *err) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_atoms) return;
+  const dbl4 A = xyzq[a];  // x, y, z, q
+  double f[3] = {__ddiv_rn(__dsub_rn(A.x, g.ox), g.h), __ddiv_rn(__dsub_rn(A.y, g.oy), g.h),
+                 __ddiv_rn(__dsub_rn(A.z, g.oz), g.h)};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  double w[3][2];
+  long c0[3];
+  for (int d = 0; d < 3; d++) {
+    double fl = floor(f[d]);
+    if (!(fl >= 0.0 && fl + 1.0 <= (double)(n[d] - 1))) {
+      atomicOr(err, 1);
+      return;
+    }
+    c0[d] = (long)fl;
+    w[d][1] = __dsub_rn(f[d], fl);
+    w[d][0] = __dsub_rn(1.0, w[d][1]);
+  }
+  for (int dk = 0; dk < 2; dk++)
+    for (int dj = 0; dj < 2; dj++)
+      for (int di = 0; di < 2; di++) {
+        double c = __dmul_rn(__dmul_rn(__dmul_rn(A.w, w[0][di]), w[1][dj]), w[2][dk]);
+        size_t e = ((size_t)(c0[2] + dk) * g.ny + (c0[1] + dj)) * g.px + (c0[0] + di);
+        atomicAdd(qn + e, (unsigned long long)__double2ll_rn(__dmul_rn(c, scale)));
+      }
+}
+
+// Ghost node t in the face order x-, x+, y-, y+, z-, z+ (dense faces).
+__device__ __forceinline__ void ghost_pos(const Geom &g, long t, double &px, double &py,
+                                          double &pz) {
+  const long fx = (long)g.ny * g.nz, fy = (long)g.nx * g.nz;
+  long i, j, k;
+  if (t < 2 * fx) {
+    int side = t >= fx; long u = t - side * fx;
+    i = side ? g.nx : -1; j = u % g.ny; k = u / g.ny;
+  } else if (t < 2 * fx + 2 * fy) {
+    long v = t - 2 * fx; int side = v >= fy; long u = v - side * fy;
+    j = side ? g.ny : -1; i = u % g.nx; k = u / g.nx;
+  } else {
+    long fz = (long)g.nx * g.ny, v = t - 2 * fx - 2 * fy; int side = v >= fz; long u = v - side * fz;
+    k = side ? g.nz : -1; i = u % g.nx; j = u / g.nx;
+  }
+  px = node_coord(g.ox, i, g.h);
+  py = node_coord(g.oy, j, g.h);
+  pz = node_coord(g.oz, k, g.h);
+}
+
+constexpr int DH_NT = 128;
+
+// Debye-Hueckel potential at each ghost node, FP64:
+//   phi_g = sum_a q_a exp(-kappa r) / (eps_out r), atoms in input order.
+__global__ void __launch_bounds__(DH_NT) k_dh_f64(const dbl4 *xyzq, int n_atoms, Geom g,
+                                                  double kappa, double eps_out, double *ghost,
+                                                  long n_ghost) {
+  __shared__ dbl4 sa[DH_NT];
+  const long t = blockIdx.x * (long)DH_NT + threadIdx.x;
+  double px = 0, py = 0, pz = 0;
+  if (t < n_ghost) ghost_pos(g, t, px, py, pz);
+  double s = 0.0;
+  for (int base = 0; base < n_atoms; base += DH_NT) {
+    __syncthreads();
+    if (base + threadIdx.x < n_atoms) sa[threadIdx.x] = xyzq[base + threadIdx.x];
+    __syncthreads();
+    const int m = min(DH_NT, n_atoms - base);
+    for (int u = 0; u < m; u++) {
+      const dbl4 A = sa[u];
+      double dx = __dsub_rn(px, A.x), dy = __dsub_rn(py, A.y), dz = __dsub_rn(pz, A.z);
+      double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+      double r = sqrt(d2);
+      double tq = __dmul_rn(A.w, exp(-__dmul_rn(kappa, r)));
+      s = __dadd_rn(s, __ddiv_rn(tq, __dmul_rn(eps_out, r)));
+    }
+  }
+  if (t < n_ghost) ghost[t] = s;
+}
+
+// Same sum in FP32 arithmetic with a compensated (Kahan) FP32 accumulator;
+// the ghost value is stored as FP64.
+__global__ void __launch_bounds__(DH_NT) k_dh_f32(const dbl4 *xyzq, int n_atoms, Geom g,
+                                                  double kappa, double eps_out, double *ghost,
+                                                  long n_ghost) {
+  __shared__ float4 sa[DH_NT];
+  const long t = blockIdx.x * (long)DH_NT + threadIdx.x;
+  double px = 0, py = 0, pz = 0;
+  if (t < n_ghost) ghost_pos(g, t, px, py, pz);
+  // positions relative to the grid origin keep FP32 rounding small
+  const float fx = (float)(px - g.ox), fy = (float)(py - g.oy), fz = (float)(pz - g.oz);
+  const float kf = (float)kappa, inv_eps = (float)(1.0 / eps_out);
+  float s = 0.f, comp = 0.f;
+  for (int base = 0; base < n_atoms; base += DH_NT) {
+    __syncthreads();
+    if (base + threadIdx.x < n_atoms) {
+      dbl4 A = xyzq[base + threadIdx.x];
+      sa[threadIdx.x] = make_float4((float)(A.x - g.ox), (float)(A.y - g.oy), (float)(A.z - g.oz),
+                                    (float)A.w * inv_eps);
+    }
+    __syncthreads();
+    const int m = min(DH_NT, n_atoms - base);
+    for (int u = 0; u < m; u++) {
+      const float4 A = sa[u];
+      float dx = fx - A.x, dy = fy - A.y, dz = fz - A.z;
+      float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      float rinv = rsqrtf(d2);
+      float term = A.w * expf(-kf * (d2 * rinv)) * rinv;
+      float y = term - comp;
+      float tt = s + y;
+      comp = (tt - s) - y;
+      s = tt;
+    }
+  }
+  if (t < n_ghost) ghost[t] = (double)s;
+}
+
+// b = (4 pi / h) q_node, then every boundary row adds eps_edge * phi_ghost for
+// its ghost neighbours in the face order x-, x+, y-, y+, z-, z+.  qn (fixed
+// point) and b may alias: each element is read before it is written.
+__global__ void k_fold_rhs(const long long *qn, const uint8_t *code, const double *ghost, Geom g,
+                           double inv_scale, double c4pi_h, double ein, double eout, double *b) {
+  const size_t n_pad = (size_t)g.px * g.ny * g.nz;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n_pad;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % g.px);
+    if (i >= g.nx) { b[e] = 0.0; continue; }
+    const size_t row = e / g.px;
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    double v = __dmul_rn(__dmul_rn((double)qn[e], inv_scale), c4pi_h);
+    const uint32_t c = code[e];
+    const long fx = (long)g.ny * g.nz, fy = (long)g.nx * g.nz, fz = (long)g.nx * g.ny;
+    if (i == 0) v = __dadd_rn(v, __dmul_rn((c & 1u) ? ein : eout, ghost[(long)k * g.ny + j]));
+    if (i == g.nx - 1) v = __dadd_rn(v, __dmul_rn((c & 2u) ? ein : eout, ghost[fx + (long)k * g.ny + j]));
+    if (j == 0) v = __dadd_rn(v, __dmul_rn((c & 4u) ? ein : eout, ghost[2 * fx + (long)k * g.nx + i]));
+    if (j == g.ny - 1)
+      v = __dadd_rn(v, __dmul_rn((c & 8u) ? ein : eout, ghost[2 * fx + fy + (long)k * g.nx + i]));
+    if (k == 0)
+      v = __dadd_rn(v, __dmul_rn((c & 16u) ? ein : eout, ghost[2 * fx + 2 * fy + (long)j * g.nx + i]));
+    if (k == g.nz - 1)
+      v = __dadd_rn(v, __dmul_rn((c & 32u) ? ein : eout,
+                                 ghost[2 * fx + 2 * fy + fz + (long)j * g.nx + i]));
+    b[e] = v;
+  }
+}
+
+// Explicit coefficient arrays from the packed codes (pitch px; see the layout
+// in pb_internal.cuh).  Pads hold 1 so that every diagonal is positive.
+template <typename C, typename D>
+__global__ void k_expand_coef(const uint8_t *code, Geom g, double ein, double eout, double kbh2,
+                              C *ex, C *ey, C *ez, D *diag) {
+  const size_t px = g.px, ny = g.ny, nz = g.nz, nx = g.nx;
+  const size_t n_ex = px * ny * nz, n_ey = px * (ny + 1) * nz, n_ez = px * ny * (nz + 1);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t n_all = n_ey > n_ez ? n_ey : n_ez;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n_all; e += stride) {
+    const size_t i = e % px, row = e / px;
+    if (e < n_ex) {
+      double v = 1.0;
+      if (i < nx) v = (code[row * px + i] & 1u) ? ein : eout;
+      else if (i == nx) v = (code[row * px + nx - 1] & 2u) ? ein : eout;
+      ex[e] = (C)v;
+    }
+    if (e < n_ey) {  // ey: row = k*(ny+1) + j
+      const size_t j = row % (ny + 1), k = row / (ny + 1);
+      double v = 1.0;
+      if (i < nx) {
+        if (j < ny) v = (code[(k * ny + j) * px + i] & 4u) ? ein : eout;
+        else v = (code[(k * ny + ny - 1) * px + i] & 8u) ? ein : eout;
+      }
+      ey[e] = (C)v;
+    }
+    if (e < n_ez) {  // ez: row = k*ny + j
+      const size_t j = row % ny, k = row / ny;
+      double v = 1.0;
+      if (i < nx) {
+        if (k < nz) v = (code[(k * ny + j) * px + i] & 16u) ? ein : eout;
+        else v = (code[((nz - 1) * ny + j) * px + i] & 32u) ? ein : eout;
+      }
+      ez[e] = (C)v;
+    }
+    if (e < n_ex && diag) {
+      D dv = (D)1;
+      if (i < nx) {
+        const uint32_t c = code[e];
+        D s = (D)((c & 1u) ? ein : eout);
+        s = s + (D)((c & 2u) ? ein : eout);
+        s = s + (D)((c & 4u) ? ein : eout);
+        s = s + (D)((c & 8u) ? ein : eout);
+        s = s + (D)((c & 16u) ? ein : eout);
+        s = s + (D)((c & 32u) ? ein : eout);
+        s = s + (D)kbh2 * (D)((c >> 6) & 1u);
+        dv = s;
+      }
+      diag[e] = dv;
+    }
+  }
+}
+
+// Dense lambda from the codes (for export).
+__global__ void k_export_lambda(const uint8_t *code, Geom g, uint8_t *lam) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = t % g.nx, row = t / g.nx;
+    lam[t] = (code[row * g.px + i] >> 6) & 1u;
+  }
+}
+
+// Sum of squares of b, deterministic: per-CTA partials then one CTA in order.
+__global__ void k_sumsq_partial(const double *b, size_t n, double *part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const size_t per = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * per, hi = min(n, lo + per);
+  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) s += b[e] * b[e];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void k_sum_final(const double *part, int n, double *out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) s += part[t];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+
+static int grid_for(size_t n, int nt) {
+  size_t b = (n + nt - 1) / nt;
+  return (int)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
+}
+
+cudaError_t launch_setup(const SetupArgs &a, cudaStream_t st) {
+  const Geom &g = a.g;
+  const size_t n_pad = (size_t)g.px * g.ny * g.nz;
+  k_init_code<<<grid_for(n_pad, 256), 256, 0, st>>>(a.code, g.nx, g.px, n_pad, 0x40);
+  if (a.n_atoms > 0) {
+    k_eps_scatter<<<a.n_atoms, 128, 0, st>>>(a.atoms_xyzr, a.n_atoms, g, (uint32_t *)a.code,
+                                             a.kappa_mask);
+    k_spread<<<(a.n_atoms + 127) / 128, 128, 0, st>>>(a.atoms_xyzq, a.n_atoms, g, a.q_scale,
+                                                      (unsigned long long *)a.b, a.err);
+  }
+  const long n_ghost = 2L * ((long)g.ny * g.nz + (long)g.nx * g.nz + (long)g.nx * g.ny);
+  if (a.n_atoms > 0) {
+    const int blocks = (int)((n_ghost + DH_NT - 1) / DH_NT);
+    if (a.dh_f32)
+      k_dh_f32<<<blocks, DH_NT, 0, st>>>(a.atoms_xyzq, a.n_atoms, g, a.kappa, a.eout, a.ghost,
+                                         n_ghost);
+    else
+      k_dh_f64<<<blocks, DH_NT, 0, st>>>(a.atoms_xyzq, a.n_atoms, g, a.kappa, a.eout, a.ghost,
+                                         n_ghost);
+  } else {
+    cudaMemsetAsync(a.ghost, 0, sizeof(double) * n_ghost, st);
+  }
+  k_fold_rhs<<<grid_for(n_pad, 256), 256, 0, st>>>((const long long *)a.b, a.code, a.ghost, g,
+                                                   1.0 / a.q_scale, a.c4pi_h, a.ein, a.eout, a.b);
+  k_sumsq_partial<<<256, 256, 0, st>>>(a.b, n_pad, a.scratch);
+  k_sum_final<<<1, 256, 0, st>>>(a.scratch, 256, a.bnorm2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const uint8_t *code, const Geom &g, double ein, double eout, double kbh2,
+                          int coef, void *ex, void *ey, void *ez, void *diag, cudaStream_t st) {
+  const size_t n = (size_t)g.px * (g.ny + 1) * (g.nz + 1);
+  const int blocks = grid_for(n, 256);
+  if (coef == COEF_F32)
+    k_expand_coef<float, float><<<blocks, 256, 0, st>>>(code, g, ein, eout, kbh2, (float *)ex,
+                                                        (float *)ey, (float *)ez, (float *)diag);
+  else if (coef == COEF_BF16)
+    k_expand_coef<__nv_bfloat16, float><<<blocks, 256, 0, st>>>(
+        code, g, ein, eout, kbh2, (__nv_bfloat16 *)ex, (__nv_bfloat16 *)ey, (__nv_bfloat16 *)ez,
+        (float *)diag);
+  else
+    k_expand_coef<double, double><<<blocks, 256, 0, st>>>(code, g, ein, eout, kbh2, (double *)ex,
+                                                          (double *)ey, (double *)ez,
+                                                          (double *)diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_lambda(const uint8_t *code, const Geom &g, uint8_t *lam, cudaStream_t st) {
+  k_export_lambda<<<grid_for((size_t)g.nx * g.ny * g.nz, 256), 256, 0, st>>>(code, g, lam);
+  return cudaGetLastError();
+}
+
+}  // namespace pb

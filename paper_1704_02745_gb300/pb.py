@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libpb (include/pb.h): argument marshalling only.
+
+Every step of the solve runs in libpb's CUDA kernels; this module converts
+Python arguments to the C structs and pointers of the C ABI and turns error
+codes into exceptions.  There is no fallback: if libpb.so is missing or no GPU
+is visible, the calls raise.
+
+Device arrays are passed as anything with a ``data_ptr()`` method (a CUDA
+torch.Tensor) or as an integer device address.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpb.so")
+
+PB_OK, PB_ERR_ARG, PB_ERR_OOM, PB_ERR_CUDA = 0, 1, 2, 3
+PB_ERR_NOT_CONVERGED, PB_ERR_BREAKDOWN, PB_ERR_TIMEOUT, PB_ERR_BUSY, PB_ERR_NOT_FOUND = 5, 6, 7, 8, 9
+COEF = {"packed": 0, "f32": 1, "bf16": 2, "f64": 3}
+PB_F64, PB_F32 = 0, 1
+PREC = {"f64": 0, "f32": 1, "f32_refine": 2}
+PRECOND = {"none": 0, "jacobi": 1}
+EXPORT = {"eps_x": 0, "eps_y": 1, "eps_z": 2, "lambda": 3, "b": 4, "ghost": 5}
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 5: "ERR_NOT_CONVERGED",
+                6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_BUSY", 9: "ERR_NOT_FOUND"}
+
+#: Every symbol include/pb.h declares (checked by the CPU tests).
+EXPORTED = ["pb_last_error", "pb_create", "pb_destroy", "pb_ctx_stats", "pb_setup_grid", "pb_free_grid",
+            "pb_grid_update_atoms", "pb_apply_operator", "pb_pcg_solve", "pb_energy",
+            "pb_grid_export", "pb_grid_bytes"]
+
+
+class PbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double), ("origin", ctypes.c_double * 3),
+                ("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double),
+                ("ionic_strength", ctypes.c_double), ("temperature", ctypes.c_double),
+                ("kappa_mask", ctypes.c_int), ("coef", ctypes.c_int),
+                ("dh_precision", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("poll_every", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("outer_steps", ctypes.c_int), ("relres", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("ms_stencil", ctypes.c_double),
+                ("ms_update", ctypes.c_double), ("ms_resid", ctypes.c_double),
+                ("n_stencil", ctypes.c_int), ("n_update", ctypes.c_int), ("n_resid", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH):
+    """Load libpb.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpb.so not built at {path}: run paper_1704_02745_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    lib.pb_last_error.restype = ctypes.c_char_p
+    lib.pb_last_error.argtypes = []
+    lib.pb_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, _P]
+    lib.pb_destroy.argtypes = [_P]
+    lib.pb_ctx_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64)]
+    lib.pb_setup_grid.argtypes = [_P, ctypes.POINTER(GridDesc), ctypes.c_int, _P, _P, _P,
+                                  ctypes.POINTER(_P)]
+    lib.pb_free_grid.argtypes = [_P]
+    lib.pb_grid_update_atoms.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+    lib.pb_apply_operator.argtypes = [_P, _P, _P, ctypes.c_int]
+    lib.pb_pcg_solve.argtypes = [_P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]
+    lib.pb_energy.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_double)]
+    lib.pb_grid_export.argtypes = [_P, ctypes.c_int, _P, ctypes.c_size_t]
+    lib.pb_grid_bytes.restype = ctypes.c_size_t
+    lib.pb_grid_bytes.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int]
+    for name in EXPORTED:
+        getattr(lib, name).restype = getattr(lib, name).restype if name in (
+            "pb_last_error", "pb_grid_bytes") else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != PB_OK:
+        raise PbError(st, load().pb_last_error().decode())
+
+
+def _dptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def grid_desc(g) -> GridDesc:
+    """GridDesc from an inputs.GridSpec."""
+    d = GridDesc()
+    d.nx, d.ny, d.nz = g.nx, g.ny, g.nz
+    d.h = g.h
+    d.origin[:] = list(g.origin)
+    d.eps_in, d.eps_out = g.eps_in, g.eps_out
+    d.ionic_strength, d.temperature = g.ionic_strength, g.temperature
+    d.kappa_mask = 1 if g.kappa_mask else 0
+    d.coef = COEF[g.coef]
+    d.dh_precision = PB_F32 if g.dh == "f32" else PB_F64
+    return d
+
+
+def solve_opts(precision="f64", tol=1e-6, precond="jacobi", max_iter=100000, inner_tol=1e-4,
+               max_outer=20, warm_start=False, poll_every=0, profile=False) -> SolveOpts:
+    o = SolveOpts()
+    o.precond = PRECOND[precond]
+    o.precision = PREC[precision]
+    o.rel_tol = tol
+    o.max_iter = max_iter
+    o.inner_tol = inner_tol
+    o.max_outer = max_outer
+    o.warm_start = 1 if warm_start else 0
+    o.poll_every = poll_every
+    o.profile = 1 if profile else 0
+    return o
+
+
+# --- the C ABI, one Python function per entry point -------------------------
+
+def pb_create(device: int = 0, stream=None) -> int:
+    h = _P()
+    _check(load().pb_create(ctypes.byref(h), device, _P(stream or 0)))
+    return h.value
+
+
+def pb_destroy(ctx: int):
+    _check(load().pb_destroy(_P(ctx)))
+
+
+def pb_ctx_stats(ctx: int):
+    """(kernel launches, host->device bytes, device->host bytes) since pb_create."""
+    a, b, c = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(load().pb_ctx_stats(_P(ctx), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def pb_setup_grid(ctx: int, desc: GridDesc, xyz: np.ndarray, q: np.ndarray, r: np.ndarray) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    h = _P()
+    _check(load().pb_setup_grid(_P(ctx), ctypes.byref(desc), int(q.shape[0]),
+                                xyz.ctypes.data_as(_P), q.ctypes.data_as(_P),
+                                r.ctypes.data_as(_P), ctypes.byref(h)))
+    return h.value
+
+
+def pb_free_grid(grid: int):
+    _check(load().pb_free_grid(_P(grid)))
+
+
+def pb_grid_update_atoms(grid: int, xyz: np.ndarray, q: np.ndarray, r: np.ndarray):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    _check(load().pb_grid_update_atoms(_P(grid), int(q.shape[0]), xyz.ctypes.data_as(_P),
+                                       q.ctypes.data_as(_P), r.ctypes.data_as(_P)))
+
+
+def pb_apply_operator(grid: int, u, au, dtype: int = PB_F64):
+    _check(load().pb_apply_operator(_P(grid), _P(_dptr(u)), _P(_dptr(au)), dtype))
+
+
+def pb_pcg_solve(grid: int, opts: SolveOpts, phi, check: bool = True) -> SolveInfo:
+    info = SolveInfo()
+    st = load().pb_pcg_solve(_P(grid), ctypes.byref(opts), _P(_dptr(phi)), ctypes.byref(info))
+    if check:
+        _check(st)
+    return info
+
+
+def pb_energy(grid: int, phi) -> float:
+    e = ctypes.c_double(0.0)
+    _check(load().pb_energy(_P(grid), _P(_dptr(phi)), ctypes.byref(e)))
+    return e.value
+
+
+def pb_grid_export(grid: int, what: str, shape, dtype) -> np.ndarray:
+    out = np.empty(shape, dtype=dtype)
+    _check(load().pb_grid_export(_P(grid), EXPORT[what], out.ctypes.data_as(_P), out.nbytes))
+    return out
+
+
+def pb_grid_bytes(desc: GridDesc, precision: str = "f32_refine") -> int:
+    return int(load().pb_grid_bytes(ctypes.byref(desc), PREC[precision]))
+
+
+# --- a small object layer over the same calls -------------------------------
+
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        self.handle = pb_create(device, stream)
+
+    def stats(self):
+        return pb_ctx_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            pb_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Grid:
+    """A set-up grid: pb_setup_grid on construction, pb_free_grid on close()."""
+
+    def __init__(self, ctx: Context, spec, atoms):
+        self.spec = spec
+        self.ctx = ctx
+        self.handle = pb_setup_grid(ctx.handle, grid_desc(spec), atoms.xyz, atoms.q, atoms.r)
+
+    def close(self):
+        if self.handle:
+            pb_free_grid(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def update_atoms(self, atoms):
+        pb_grid_update_atoms(self.handle, atoms.xyz, atoms.q, atoms.r)
+
+    def export(self, what: str) -> np.ndarray:
+        g = self.spec
+        nx, ny, nz = g.nx, g.ny, g.nz
+        shapes = {"eps_x": ((nz, ny, nx + 1), np.float64), "eps_y": ((nz, ny + 1, nx), np.float64),
+                  "eps_z": ((nz + 1, ny, nx), np.float64), "lambda": ((nz, ny, nx), np.uint8),
+                  "b": ((nz, ny, nx), np.float64),
+                  "ghost": ((2 * (ny * nz + nx * nz + nx * ny),), np.float64)}
+        shape, dt = shapes[what]
+        return pb_grid_export(self.handle, what, shape, dt)
+
+    def apply(self, u, au, dtype: int = PB_F64):
+        pb_apply_operator(self.handle, u, au, dtype)
+
+    def solve(self, phi, check: bool = True, **kw) -> SolveInfo:
+        return pb_pcg_solve(self.handle, solve_opts(**kw), phi, check=check)
+
+    def energy(self, phi) -> float:
+        return pb_energy(self.handle, phi)
