@@ -169,7 +169,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     problem = WORKLOADS[args.workload]()
-    spec = problem.grid.replace(coef=args.coef)
+    spec = problem.grid.replace(coef=args.coef, dh=args.dh)
     n_nodes = spec.n
     snaps = snapshots(problem, 8, seed=100 + rank)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -199,7 +199,12 @@ def run_ours(args):
             t = torch.tensor([total_dev_s, total_wall_s], dtype=torch.float64, device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_dev_s, total_wall_s = float(t[0]), float(t[1])
-        # plain FP64 PCG, one solve at a time, on the same snapshots
+        if args.quick:  # profiling runs: the timed loop only
+            if rank == 0:
+                print(json.dumps({"quick": True, "ms_per_step": sum(dev_ms) / len(dev_ms),
+                                  "iterations_mean": float(np.mean(iters))}), flush=True)
+            return
+        # plain FP64 PCG, one solve at a time, on the same snapshots and setup
         k64 = max(3, args.steps // 2)
         d64, w64, it64, _ = run_loop(g, phi, snaps, k64, 1, stream, flush,
                                      dict(precision="f64", tol=args.tol))
@@ -233,6 +238,7 @@ def run_ours(args):
                    "atoms": problem.atoms.n, "h": spec.h, "tol": args.tol,
                    "solver": "jacobi-pcg fp32 inner + fp64 refinement",
                    "inner_tol": args.inner_tol, "coef": args.coef,
+                   "debye_hueckel_sum": args.dh,
                    "snapshot_sigma_A": SNAPSHOT_SIGMA,
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{world}"},
@@ -354,7 +360,11 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--cpu-sample-iters", type=int, default=40)
+    ap.add_argument("--dh", default="f32", choices=["f32", "f64"],
+                    help="precision of the Debye-Hueckel boundary sum in the grid setup")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed loop only (no FP64 comparator, profiled solve or CPU baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

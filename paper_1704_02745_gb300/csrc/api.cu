@@ -7,6 +7,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "pb.h"
 #include "pb_host.h"
 #include "pb_internal.cuh"
@@ -156,20 +160,23 @@ extern "C" pb_status pb_free_grid(pb_grid *g) {
   return PB_OK;
 }
 
-static void tile_plan(pb_grid *g, int num_sms) {
+// Stencil tiles: the fewest x tiles of width <= WMAX, then the tallest H with
+// W*H <= NT, then z chunks so that all tiles fit in one wave of resident CTAs.
+static void tile_plan(pb_grid *g, int resident) {
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
-  g->tiles_x = (nx + TX - 1) / TX;
-  g->tiles_y = (ny + TY - 1) / TY;
-  const int txy = g->tiles_x * g->tiles_y;
-  const int target = 4 * num_sms;
-  const int nzc = (target + txy - 1) / txy;
-  int tz = (nz + nzc - 1) / nzc;
-  if (tz < 8) tz = 8;
-  if (tz > nz) tz = nz;
-  g->tz = tz;
-  g->tiles_z = (nz + tz - 1) / tz;
-  g->n_st = g->tiles_x * g->tiles_y * g->tiles_z;
-  g->n_ch = (int)((g->n_pad + CH - 1) / CH);
+  g->tiles_x = (nx + WMAX - 1) / WMAX;
+  g->W = round_up((nx + g->tiles_x - 1) / g->tiles_x, 4);
+  const int hmax = std::min(HMAX, NT / g->W);
+  g->tiles_y = (ny + hmax - 1) / hmax;
+  g->H = (ny + g->tiles_y - 1) / g->tiles_y;
+  const int cols = g->tiles_x * g->tiles_y;
+  int zc = std::max(1, resident / cols);
+  zc = std::min(zc, std::max(1, nz / 4));
+  g->tz = (nz + zc - 1) / zc;
+  g->tiles_z = (nz + g->tz - 1) / g->tz;
+  g->n_st = cols * g->tiles_z;
+  g->rows_per_chunk = std::max(1, CH / nx);
+  g->n_ch = (int)(((long)ny * nz + g->rows_per_chunk - 1) / g->rows_per_chunk);
 }
 
 // (Re)run the setup kernels of a grid for the given host atoms.
@@ -177,7 +184,7 @@ static pb_status run_setup(pb_grid *g, int n_atoms, const double *xyz, const dou
                            const double *radius) {
   cudaStream_t s = g->ctx->stream;
   const pb_grid_desc *desc = &g->d;
-  if (n_atoms > g->atom_cap) {
+  if (!g->scratch || n_atoms > g->atom_cap) {  // first call (also with no atoms) or growth
     if (g->xyzq) cudaFree(g->xyzq);
     if (g->xyzr) cudaFree(g->xyzr);
     if (g->scratch) cudaFree(g->scratch);
@@ -312,7 +319,7 @@ extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_
     pb_grid_release(g);
     return st;
   }
-  tile_plan(g, ctx->num_sms);
+  tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms).stencil_blocks);
   *out = g;
   return PB_OK;
 #undef ALLOC
@@ -383,12 +390,42 @@ pb_status pb_ensure_workspace(pb_grid *g, int mode) {
   return PB_OK;
 }
 
-Inst pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef) {
-  Inst I;
+// TMA descriptors are encoded through the driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 3-D map of a padded node array [nz][ny][px]; extent nx in x, so elements
+// beyond nx (and outside the grid in y, z) read as zero.
+static bool encode_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int es,
+                       const pb_grid *g, int box_w, int box_h) {
+  auto fn = tmap_encoder();
+  if (!fn || !base) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g->d.nx, (cuuint64_t)g->d.ny, (cuuint64_t)g->d.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)g->g.px * es, (cuuint64_t)g->g.px * g->d.ny * es};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef, Inst &I) {
   memset(&I, 0, sizeof(I));
   I.nx = g->d.nx; I.ny = g->d.ny; I.nz = g->d.nz; I.px = g->g.px;
+  I.W = g->W; I.H = g->H;
   I.tiles_x = g->tiles_x; I.tiles_y = g->tiles_y; I.tiles_z = g->tiles_z; I.tz = g->tz;
-  I.n_st = g->n_st; I.n_ch = g->n_ch;
+  I.n_st = g->n_st; I.n_ch = g->n_ch; I.rows_per_chunk = g->rows_per_chunk;
   I.st_base = 0; I.ch_base = 0;
   I.mode = mode;
   I.precond = o ? (o->precond == PB_PRECOND_JACOBI) : 1;
@@ -431,7 +468,28 @@ Inst pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef) 
       I.dtab32[2 * nin + lam] = s32;
       I.idtab32[2 * nin + lam] = 1.0f / s32;
     }
-  return I;
+  // TMA stage layout and descriptors for the stencil pass
+  const int es = mode == MODE_F64 ? 8 : 4;
+  const StageLayout L = stage_layout(g->W, g->H, es);
+  I.cw = L.cw;
+  I.stage_bytes = L.stage_bytes;
+  I.off_p = L.off_p;
+  I.off_c = L.off_c;
+  I.off_x = L.off_x;
+  I.tma_bytes = L.tma_bytes;
+  if (!o) return PB_OK;  // operator application needs no descriptors
+  const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const void *x0 = mode == MODE_F64 ? (const void *)g->x64 : g->d32;
+  const void *x1 = mode == MODE_F64 ? (const void *)g->x64b : g->d32;
+  if (!encode_map(&I.tm_r, I.r, dt, es, g, L.rw, L.rows) ||
+      !encode_map(&I.tm_p0, I.p0, dt, es, g, L.rw, L.rows) ||
+      !encode_map(&I.tm_p1, I.p1, dt, es, g, L.rw, L.rows) ||
+      !encode_map(&I.tm_code, g->code, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, L.cw, L.rows) ||
+      !encode_map(&I.tm_x0, x0, dt, es, g, g->W, g->H) ||
+      !encode_map(&I.tm_x1, x1, dt, es, g, g->W, g->H))
+    return pb_fail(PB_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return PB_OK;
 }
 
 Scal pb_initial_scal() {
@@ -453,7 +511,8 @@ extern "C" pb_status pb_apply_operator(pb_grid *g, const void *u, void *au, int 
   const int mode = dtype == PB_F64 ? MODE_F64 : MODE_F32;
   pb_status st = pb_ensure_workspace(g, mode);
   if (st) return st;
-  Inst I = pb_make_inst(g, nullptr, mode, pb_inner_coef(g, mode));
+  Inst I;
+  if ((st = pb_make_inst(g, nullptr, mode, pb_inner_coef(g, mode), I))) return st;
   cudaStream_t s = g->ctx->stream;
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
   CK(launch_apply(I, g->dinst, u, au, dtype == PB_F64 ? 0 : 1, s));
@@ -602,8 +661,10 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   if ((st = pb_ensure_workspace(g, mode))) return st;
   pb_solve_opts oo = *o;
   if (mode != MODE_F32_REFINE) oo.max_outer = 1;
-  Inst I = pb_make_inst(g, &oo, mode, coef);
+  Inst I;
+  if ((st = pb_make_inst(g, &oo, mode, coef, I))) return st;
   Scal S0 = pb_initial_scal();
+  CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(g->scal, &S0, sizeof(Scal), cudaMemcpyHostToDevice, s));
   g->ctx->h2d += sizeof(Inst) + sizeof(Scal);
@@ -634,7 +695,13 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
       }
     }
   }
-  const Scal S = *hs;
+  Scal S = *hs;
+  {
+    int *herr = (int *)(hs + 1);  // pinned slot after the scalars
+    CK(cudaMemcpyAsync(herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*herr & 2) S.status = PB_ERR_TIMEOUT;  // a device pipeline wait gave up
+  }
   CK(launch_unpack(S.xbuf ? g->x64b : g->x64, phi, g->d.nx, g->d.ny, g->d.nz, g->g.px, s));
   g->ctx->launches += 1;
   CK(cudaStreamSynchronize(s));
@@ -648,6 +715,7 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   if (S.status != PB_OK) {
     const char *why = S.status == PB_ERR_NOT_CONVERGED ? "iteration cap reached"
                       : S.status == PB_ERR_BREAKDOWN   ? "CG breakdown (p.Ap <= 0 or non-finite)"
+                      : S.status == PB_ERR_TIMEOUT     ? "solve did not finish (device wait timed out)"
                                                        : "solve did not finish";
     return pb_fail(S.status, why);
   }

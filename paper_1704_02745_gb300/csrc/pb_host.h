@@ -41,7 +41,8 @@ struct pb_grid {
   pb::Inst *dinst = nullptr;
   pb::Item *st_items = nullptr, *ch_items = nullptr;
   double *st_part = nullptr, *ch_part = nullptr;
-  int tiles_x = 0, tiles_y = 0, tiles_z = 0, tz = 0, n_st = 0, n_ch = 0;
+  int W = 0, H = 0, tiles_x = 0, tiles_y = 0, tiles_z = 0, tz = 0, n_st = 0, n_ch = 0;
+  int rows_per_chunk = 0;
   // cached device graph of `graph_ticks` ticks
   cudaGraphExec_t graph = nullptr;
   int graph_mode = -1, graph_coef = -1, graph_ticks = 0;
@@ -52,5 +53,5 @@ pb_status pb_dalloc(void **p, size_t bytes);
 void pb_grid_release(pb_grid *g);
 int pb_inner_coef(const pb_grid *g, int mode);
 pb_status pb_ensure_workspace(pb_grid *g, int mode);
-pb::Inst pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef);
+pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef, pb::Inst &I);
 pb::Scal pb_initial_scal();

@@ -1,8 +1,9 @@
 // pb_internal.cuh -- device data layout and shared definitions of libpb.
 //
 // HBM layout of one grid (all node arrays padded in x to a pitch px, a
-// multiple of 4 elements with px >= nx + 1, so every row starts 16-byte
-// aligned and the (nx+1)-th x-edge fits in the row):
+// multiple of 16 elements with px >= nx + 1, so every row of every array
+// starts 16-byte aligned -- a TMA requirement, also for the one-byte codes --
+// and the (nx+1)-th x-edge fits in the row):
 //   code   uint8  [nz][ny][px]   packed coefficients, one byte per node:
 //                                bit 0/1 x-/x+ edge inside (eps_in), bit 2/3 y-/y+,
 //                                bit 4/5 z-/z+, bit 6 lambda (1 = ion accessible);
@@ -17,6 +18,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -26,15 +28,17 @@ struct __align__(32) dbl4 {  // four doubles, 32-byte aligned (atoms: x, y, z, q
   double x, y, z, w;
 };
 
-// Tile of the stencil kernels: TX x TY columns marching over a z range.
-constexpr int TX = 32;
-constexpr int TY = 8;
-constexpr int NT = TX * TY;  // threads per CTA
-constexpr int CH = 4096;     // elements per chunk of the elementwise kernels
-constexpr int NDTAB = 14;    // diagonal table entries: (#inside edges 0..6) x (lambda 0/1)
+// Stencil tiles: W x H columns (W a multiple of 4, W <= 64, W*H <= NT) marching
+// over a z range; one CTA of NT threads per tile, one column per thread.
+constexpr int NT = 512;        // threads per stencil CTA
+constexpr int WMAX = 64;       // widest tile
+constexpr int HMAX = 16;       // tallest tile
+constexpr int NSTAGE = 4;      // TMA pipeline depth (z planes in flight per CTA)
+constexpr int NT_UPD = 256;    // threads per update CTA
+constexpr int CH = 8192;       // elements per chunk of the update pass
+constexpr int NDTAB = 14;      // diagonal table entries: (#inside edges 0..6) x (lambda 0/1)
+constexpr int PITCH_ALIGN = 16;  // node-array pitch in elements (TMA: 16-byte strides for bytes)
 
-// RESID: FP64 residual pass pending; START: first iteration of an inner solve;
-// INNER: CG iterations; DONE: finished (convergence mask off).
 enum Phase : int { PH_RESID = 0, PH_INNER = 1, PH_DONE = 2, PH_START = 3 };
 enum Mode : int { MODE_F64 = 0, MODE_F32 = 1, MODE_F32_REFINE = 2 };
 enum Coef : int { COEF_PACKED = 0, COEF_F32 = 1, COEF_BF16 = 2, COEF_F64 = 3 };
@@ -59,7 +63,13 @@ struct Scal {
 };
 
 // Everything a phase kernel needs to know about one instance (one grid).
-struct Inst {
+// The TMA descriptors come first (64-byte aligned).
+struct alignas(64) Inst {
+  CUtensorMap tm_r, tm_p0, tm_p1, tm_code, tm_x0, tm_x1;  // r, p buffers, codes, inner x
+  int W, H;                           // stencil tile
+  int cw;                             // width of the code box (bytes, multiple of 16)
+  int stage_bytes, off_p, off_c, off_x, tma_bytes;  // TMA stage layout and bytes per stage
+  int rows_per_chunk;                 // update-pass chunk
   int nx, ny, nz, px;
   int tiles_x, tiles_y, tiles_z, tz;  // stencil tile decomposition
   int n_st, n_ch;                     // stencil tiles, elementwise chunks
@@ -103,6 +113,6 @@ __host__ __device__ inline int dtab_index(uint32_t c) {
 }
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
-inline int pitch_of(int nx) { return round_up(nx + 1, 4); }
+inline int pitch_of(int nx) { return round_up(nx + 1, PITCH_ALIGN); }
 
 }  // namespace pb

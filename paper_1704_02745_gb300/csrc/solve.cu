@@ -23,6 +23,15 @@
 // results are bitwise reproducible and independent of the other instances in
 // a batch.  Every kernel loops persistently over a work list of (instance,
 // tile) items and skips instances in another phase (convergence masks).
+//
+// Stencil-pass data movement: a CTA owns a W x H column tile and marches over
+// its z range.  One thread issues TMA tile loads (cp.async.bulk.tensor) of r,
+// p_old (tile + one-node halo, x widened to the 16-byte rule), the code bytes
+// and the centre tile of x, NSTAGE planes ahead of the plane being computed,
+// each stage completing on its own mbarrier.  The grid boundary needs no test:
+// TMA fills out-of-range elements with zeros, which is exactly the zero ghost
+// of the operator.  New directions p are built in a triple-buffered shared
+// plane with halo; the z neighbours stay in registers.
 #include <cuda_bf16.h>
 
 #include <type_traits>
@@ -33,120 +42,244 @@
 
 namespace pb {
 
-// Halo bookkeeping: threads 0..2*TY+2*TX-1 each own one halo cell of a plane.
-struct Halo {
-  int hi, hj, sx, sy;
-  bool role;
-};
-__device__ __forceinline__ Halo halo_of(int x0, int y0) {
-  Halo h{-1, -1, 0, 0, false};
-  const int t = threadIdx.x;
-  if (t < TY) { h.hi = x0 - 1; h.hj = y0 + t; h.sx = 0; h.sy = t + 1; h.role = true; }
-  else if (t < 2 * TY) { h.hi = x0 + TX; h.hj = y0 + t - TY; h.sx = TX + 1; h.sy = t - TY + 1; h.role = true; }
-  else if (t < 2 * TY + TX) { h.hi = x0 + t - 2 * TY; h.hj = y0 - 1; h.sx = t - 2 * TY + 1; h.sy = 0; h.role = true; }
-  else if (t < 2 * TY + 2 * TX) { h.hi = x0 + t - 2 * TY - TX; h.hj = y0 + TY; h.sx = t - 2 * TY - TX + 1; h.sy = TY + 1; h.role = true; }
-  return h;
-}
+// ---------------------------------------------------------------------------
+// TMA / mbarrier primitives (inline PTX).
 
-struct TileGeo {
-  int i, j, z0, z1, x0, y0;
-  bool valid;
-};
-__device__ __forceinline__ TileGeo tile_geo(const Inst &I, int tile) {
-  TileGeo g;
-  const int bx = tile % I.tiles_x, rest = tile / I.tiles_x;
-  const int by = rest % I.tiles_y, bz = rest / I.tiles_y;
-  g.x0 = bx * TX; g.y0 = by * TY;
-  g.z0 = bz * I.tz; g.z1 = min(g.z0 + I.tz, I.nz);
-  g.i = g.x0 + (int)(threadIdx.x % TX);
-  g.j = g.y0 + (int)(threadIdx.x / TX);
-  g.valid = g.i < I.nx && g.j < I.ny;
-  return g;
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of a barrier, giving up after ~1 s of clock.
+constexpr long long WAIT_CYCLES = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
 }
 
 // ---------------------------------------------------------------------------
-// INNER phase, stencil pass of one tile.  Returns this thread's p.Ap.
+// Tile geometry.
+
+struct TileG {
+  int x0, y0, z0, z1, tx, ty;
+  bool in_tile;  // thread owns a column of the W x H tile
+  bool valid;    // ... and that column is inside the grid
+};
+__device__ __forceinline__ TileG tile_g(const Inst &I, int tile) {
+  TileG g;
+  const int bx = tile % I.tiles_x, rest = tile / I.tiles_x;
+  const int by = rest % I.tiles_y, bz = rest / I.tiles_y;
+  g.x0 = bx * I.W;
+  g.y0 = by * I.H;
+  g.z0 = bz * I.tz;
+  g.z1 = min(g.z0 + I.tz, I.nz);
+  g.tx = threadIdx.x % I.W;
+  g.ty = threadIdx.x / I.W;
+  g.in_tile = threadIdx.x < I.W * I.H;
+  g.valid = g.in_tile && g.x0 + g.tx < I.nx && g.y0 + g.ty < I.ny;
+  return g;
+}
+
+// Halo cell owned by this thread: left/right columns then bottom/top rows.
+struct HaloG {
+  int hx, hy;  // tile-relative position, -1 .. W / -1 .. H
+  bool role;
+};
+__device__ __forceinline__ HaloG halo_g(const Inst &I) {
+  HaloG h{0, 0, false};
+  const int t = threadIdx.x, W = I.W, H = I.H;
+  if (t < H) { h.hx = -1; h.hy = t; h.role = true; }
+  else if (t < 2 * H) { h.hx = W; h.hy = t - H; h.role = true; }
+  else if (t < 2 * H + W) { h.hx = t - 2 * H; h.hy = -1; h.role = true; }
+  else if (t < 2 * H + 2 * W) { h.hx = t - 2 * H - W; h.hy = H; h.role = true; }
+  return h;
+}
+
+// z = M^-1 r from a code byte (packed) -- or from the explicit diagonal.
 template <typename T, int CM>
-__device__ __forceinline__ double cg_tile(const Inst &I, const Scal &S, int tile,
-                                          T (*sp)[TY + 2][TX + 2]) {
+__device__ __forceinline__ T zval_code(const Inst &I, uint32_t code, T r, size_t e) {
+  if (!I.precond) return r;
+  if (CM == COEF_PACKED) return r * tab_i<T>(I, dtab_index(code));
+  return r / ((const T *)I.diag)[e];
+}
+
+// ---------------------------------------------------------------------------
+// INNER phase, stencil pass of one tile (TMA pipeline).  Returns this
+// thread's p.Ap; sets `abort` if a pipeline wait timed out.
+template <typename T, int CM>
+__device__ __forceinline__ double cg_tile(const Inst &I, const Scal &S, int tile, uint8_t *stages,
+                                          T *ring, uint64_t *full, uint32_t &seq, bool &abort) {
   constexpr bool SEP = sizeof(T) == 4;  // FP32 inner solves accumulate into d
-  const TileGeo G = tile_geo(I, tile);
-  const Halo H = halo_of(G.x0, G.y0);
-  const bool hvalid = H.role && H.hi >= 0 && H.hi < I.nx && H.hj >= 0 && H.hj < I.ny;
-  const size_t px = I.px, plane = (size_t)I.px * I.ny;
-  const size_t ec0 = (size_t)G.j * px + G.i, eh0 = (size_t)H.hj * px + H.hi;
+  constexpr int PAD = 16 / (int)sizeof(T);
+  const TileG G = tile_g(I, tile);
+  const HaloG Hh = halo_g(I);
+  const int W = I.W, H = I.H, RW = W + 2 * PAD, CW = I.cw, RGW = W + 2;
+  const int cx0 = ((G.x0 - 1) >> 4) << 4;  // code box start: 16-byte aligned, <= x0 - 1
+  const int Q = (G.z1 - G.z0) + 2;         // planes z0-1 .. z1
   const bool first = S.phase == PH_START;
   const T beta = (T)S.beta, alpha = (T)S.alpha;
-  const T *__restrict__ r = (const T *)I.r;
-  const T *__restrict__ pold = (const T *)(S.pbuf ? I.p1 : I.p0);
+  const CUtensorMap *m_pold = S.pbuf ? &I.tm_p1 : &I.tm_p0;
+  const CUtensorMap *m_x = SEP ? &I.tm_x0 : (S.xbuf ? &I.tm_x1 : &I.tm_x0);
   T *__restrict__ pnew = (T *)(S.pbuf ? I.p0 : I.p1);
   T *__restrict__ ap = (T *)I.ap;
   T *__restrict__ x = SEP ? (T *)I.d : (T *)(S.xbuf ? I.x64b : I.x64);
+  const size_t px = I.px, plane = (size_t)I.px * I.ny;
 
-  auto pn = [&](size_t e, T &po) -> T {
-    po = pold[e];
-    const T z = zval<T, CM>(I, e, r[e]);
-    return first ? z : z + beta * po;
+  auto issue = [&](int q) {  // thread 0: load plane z0 - 1 + q into its stage
+    const uint32_t st = (seq + q) % NSTAGE;
+    uint8_t *sb = stages + (size_t)st * I.stage_bytes;
+    const int z = G.z0 - 1 + q;
+    mbar_expect_tx(&full[st], (uint32_t)I.tma_bytes);
+    tma_load_3d(sb, &I.tm_r, &full[st], G.x0 - PAD, G.y0 - 1, z);
+    tma_load_3d(sb + I.off_p, m_pold, &full[st], G.x0 - PAD, G.y0 - 1, z);
+    tma_load_3d(sb + I.off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
+    tma_load_3d(sb + I.off_x, m_x, &full[st], G.x0, G.y0, z);
   };
+  if (threadIdx.x == 0)
+    for (int q = 0; q < min(NSTAGE, Q); ++q) issue(q);
 
-  T pm = 0, pc = 0, poc = 0, dummy;
-  if (G.valid && G.z0 > 0) pm = pn((size_t)(G.z0 - 1) * plane + ec0, dummy);
-  if (G.valid) pc = pn((size_t)G.z0 * plane + ec0, poc);
-  sp[0][threadIdx.x / TX + 1][threadIdx.x % TX + 1] = pc;
-  if (H.role) sp[0][H.sy][H.sx] = hvalid ? pn((size_t)G.z0 * plane + eh0, dummy) : (T)0;
-  const int tx = threadIdx.x % TX + 1, ty = threadIdx.x / TX + 1;
-  int cur = 0;
+  // positions of this thread's centre and halo cell in the stage boxes and the ring
+  const int hr = (Hh.hy + 1) * RW + (Hh.hx + PAD);
+  const int hc = (Hh.hy + 1) * CW + (G.x0 + Hh.hx - cx0);
+  const int hg = (Hh.hy + 1) * RGW + (Hh.hx + 1);
+  const int cr = (G.ty + 1) * RW + (G.tx + PAD);
+  const int cc = (G.ty + 1) * CW + (G.x0 + G.tx - cx0);
+  const int cg = (G.ty + 1) * RGW + (G.tx + 1);
+  const size_t ec0 = (size_t)(G.y0 + G.ty) * px + (G.x0 + G.tx);
+  const int hi = G.x0 + Hh.hx, hj = G.y0 + Hh.hy;
+  const bool hin = hi >= 0 && hi < I.nx && hj >= 0 && hj < I.ny;
+  const size_t eh0 = hin ? (size_t)hj * px + hi : 0;
+
+  T pm = 0, pc = 0, po_prev = 0, x_prev = 0;
+  uint32_t code_prev = 0;
   T acc = 0;
-  for (int k = G.z0; k < G.z1; ++k) {
-    const int nxt = cur == 2 ? 0 : cur + 1;
-    T pnx = 0, ponx = 0;
-    if (k + 1 < I.nz) {
-      if (G.valid) pnx = pn((size_t)(k + 1) * plane + ec0, ponx);
-      if (H.role) sp[nxt][H.sy][H.sx] = hvalid ? pn((size_t)(k + 1) * plane + eh0, dummy) : (T)0;
-    } else if (H.role) {
-      sp[nxt][H.sy][H.sx] = 0;
+  for (int q = 0; q < Q; ++q) {
+    const uint32_t st = (seq + q) % NSTAGE, par = ((seq + q) / NSTAGE) & 1u;
+    const bool ok = mbar_wait(&full[st], par);
+    const uint8_t *sb = stages + (size_t)st * I.stage_bytes;
+    const T *sr = (const T *)sb;
+    const T *sp = (const T *)(sb + I.off_p);
+    const uint8_t *sc = sb + I.off_c;
+    const T *sx = (const T *)(sb + I.off_x);
+    T *rg = ring + (size_t)(q % 3) * RGW * (H + 2);
+    const int z = G.z0 - 1 + q;
+    const bool zin = z >= 0 && z < I.nz;
+    T pn = 0, po = 0, xv = 0;
+    uint32_t code = 0;
+    if (ok && G.in_tile) {
+      po = sp[cr];
+      code = sc[cc];
+      xv = sx[G.ty * W + G.tx];
+      if (CM == COEF_PACKED || (G.valid && zin)) {
+        const T zz = zval_code<T, CM>(I, code, sr[cr], (size_t)(zin ? z : 0) * plane + ec0);
+        pn = first ? zz : zz + beta * po;
+      }
+      rg[cg] = pn;
     }
-    sp[nxt][ty][tx] = pnx;
-    __syncthreads();
-    if (G.valid) {
+    if (ok && Hh.role) {
+      T hv = 0;
+      if (CM == COEF_PACKED || (hin && zin)) {
+        const T zz = zval_code<T, CM>(I, sc[hc], sr[hr], (size_t)(zin ? z : 0) * plane + eh0);
+        hv = first ? zz : zz + beta * sp[hr];
+      }
+      rg[hg] = hv;
+    }
+    if (__syncthreads_or(!ok)) {
+      // A wait gave up: let the copies already issued (planes q .. q+NSTAGE-1)
+      // land, each for a bounded time, before the CTA leaves.
+      if (threadIdx.x == 0)
+        for (int u = q; u < min(Q, q + NSTAGE); ++u)
+          mbar_wait(&full[(seq + u) % NSTAGE], ((seq + u) / NSTAGE) & 1u);
+      abort = true;
+      seq += Q;
+      return 0.0;
+    }
+    if (threadIdx.x == 0 && q + NSTAGE < Q) issue(q + NSTAGE);
+    if (q >= 2 && G.valid) {
+      const int k = z - 1;
       const size_t e = (size_t)k * plane + ec0;
-      const NodeCoef<T> c = node_coef<T, CM>(I, e, k);
-      T s = c.exm * sp[cur][ty][tx - 1];
-      s += c.exp * sp[cur][ty][tx + 1];
-      s += c.eym * sp[cur][ty - 1][tx];
-      s += c.eyp * sp[cur][ty + 1][tx];
+      const T *rm = ring + (size_t)((q - 1) % 3) * RGW * (H + 2);
+      NodeCoef<T> c;
+      if (CM == COEF_PACKED) {
+        const T ei = e_in<T>(I), eo = e_out<T>(I);
+        const uint32_t b = code_prev;
+        c.exm = (b & 1u) ? ei : eo; c.exp = (b & 2u) ? ei : eo;
+        c.eym = (b & 4u) ? ei : eo; c.eyp = (b & 8u) ? ei : eo;
+        c.ezm = (b & 16u) ? ei : eo; c.ezp = (b & 32u) ? ei : eo;
+        c.diag = tab_d<T>(I, dtab_index(b));
+      } else {
+        c = node_coef<T, CM>(I, e, k);
+      }
+      T s = c.exm * rm[cg - 1];
+      s += c.exp * rm[cg + 1];
+      s += c.eym * rm[cg - RGW];
+      s += c.eyp * rm[cg + RGW];
       s += c.ezm * pm;
-      s += c.ezp * pnx;
+      s += c.ezp * pn;
       const T a = c.diag * pc - s;
       pnew[e] = pc;
       ap[e] = a;
-      if (SEP) x[e] = first ? (T)0 : x[e] + alpha * poc;
-      else if (!first) x[e] = x[e] + alpha * poc;
+      if (SEP) x[e] = first ? (T)0 : x_prev + alpha * po_prev;
+      else if (!first) x[e] = x_prev + alpha * po_prev;
       acc += pc * a;
     }
-    pm = pc; pc = pnx; poc = ponx; cur = nxt;
+    pm = pc; pc = pn; po_prev = po; x_prev = xv; code_prev = code;
   }
+  seq += Q;
   return (double)acc;
 }
 
-// RESID phase (FP64): fold the deferred update, true residual, new inner rhs.
+// RESID phase (FP64, plain loads): fold the deferred update, true residual,
+// new inner right-hand side.
 template <typename T, int CM>
-__device__ __forceinline__ void resid_tile(const Inst &I, const Scal &S, int tile,
-                                           double (*sq)[TY + 2][TX + 2], double &rr64,
-                                           double &rz) {
+__device__ __forceinline__ void resid_tile(const Inst &I, const Scal &S, int tile, double *ring,
+                                           double &rr64, double &rz) {
   constexpr bool SEP = sizeof(T) == 4;
-  const TileGeo G = tile_geo(I, tile);
-  const Halo H = halo_of(G.x0, G.y0);
-  const bool hvalid = H.role && H.hi >= 0 && H.hi < I.nx && H.hj >= 0 && H.hj < I.ny;
+  const TileG G = tile_g(I, tile);
+  const HaloG Hh = halo_g(I);
+  const int RGW = I.W + 2, H = I.H;
+  const int hi = G.x0 + Hh.hx, hj = G.y0 + Hh.hy;
+  const bool hvalid = Hh.role && hi >= 0 && hi < I.nx && hj >= 0 && hj < I.ny;
   const size_t px = I.px, plane = (size_t)I.px * I.ny;
-  const size_t ec0 = (size_t)G.j * px + G.i, eh0 = (size_t)H.hj * px + H.hi;
+  const size_t ec0 = (size_t)(G.y0 + G.ty) * px + (G.x0 + G.tx);
+  const size_t eh0 = hvalid ? (size_t)hj * px + hi : 0;
+  const int cg = (G.ty + 1) * RGW + (G.tx + 1), hg = (Hh.hy + 1) * RGW + (Hh.hx + 1);
   const double alpha = S.alpha;
   const double *__restrict__ xin = S.xbuf ? I.x64b : I.x64;
   double *__restrict__ xout = S.xbuf ? I.x64 : I.x64b;
   const T *__restrict__ d = (const T *)I.d;
   const T *__restrict__ p = (const T *)(S.pbuf ? I.p1 : I.p0);
   T *__restrict__ r = (T *)I.r;
-
   // Before the first inner solve there is nothing to fold (d and p unset).
   const bool fold = S.outer > 0;
   auto xn = [&](size_t e) -> double {
@@ -155,33 +288,35 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const Scal &S, int til
     if (SEP) v += (double)d[e];
     return v + alpha * (double)p[e];
   };
-
   double xm = 0, xc = 0;
   if (G.valid && G.z0 > 0) xm = xn((size_t)(G.z0 - 1) * plane + ec0);
   if (G.valid) xc = xn((size_t)G.z0 * plane + ec0);
-  const int tx = threadIdx.x % TX + 1, ty = threadIdx.x / TX + 1;
-  sq[0][ty][tx] = xc;
-  if (H.role) sq[0][H.sy][H.sx] = hvalid ? xn((size_t)G.z0 * plane + eh0) : 0.0;
+  if (G.in_tile) ring[cg] = xc;
+  if (Hh.role) ring[hg] = hvalid ? xn((size_t)G.z0 * plane + eh0) : 0.0;
   int cur = 0;
-  rr64 = 0.0; rz = 0.0;
+  rr64 = 0.0;
+  rz = 0.0;
+  const int rsz = RGW * (H + 2);
   for (int k = G.z0; k < G.z1; ++k) {
     const int nxt = cur == 2 ? 0 : cur + 1;
     double xnx = 0;
+    double *rn = ring + (size_t)nxt * rsz;
     if (k + 1 < I.nz) {
       if (G.valid) xnx = xn((size_t)(k + 1) * plane + ec0);
-      if (H.role) sq[nxt][H.sy][H.sx] = hvalid ? xn((size_t)(k + 1) * plane + eh0) : 0.0;
-    } else if (H.role) {
-      sq[nxt][H.sy][H.sx] = 0.0;
+      if (Hh.role) rn[hg] = hvalid ? xn((size_t)(k + 1) * plane + eh0) : 0.0;
+    } else if (Hh.role) {
+      rn[hg] = 0.0;
     }
-    sq[nxt][ty][tx] = xnx;
+    if (G.in_tile) rn[cg] = xnx;
     __syncthreads();
     if (G.valid) {
+      const double *rc = ring + (size_t)cur * rsz;
       const size_t e = (size_t)k * plane + ec0;
       const NodeCoef<double> c = node_coef64<CM>(I, e, k);
-      double s = c.exm * sq[cur][ty][tx - 1];
-      s += c.exp * sq[cur][ty][tx + 1];
-      s += c.eym * sq[cur][ty - 1][tx];
-      s += c.eyp * sq[cur][ty + 1][tx];
+      double s = c.exm * rc[cg - 1];
+      s += c.exp * rc[cg + 1];
+      s += c.eym * rc[cg - RGW];
+      s += c.eyp * rc[cg + RGW];
       s += c.ezm * xm;
       s += c.ezp * xnx;
       const double res = I.b[e] - (c.diag * xc - s);
@@ -203,7 +338,8 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum two values over the CTA; thread 0 gets the result.
+// Sum two values over the CTA of NTH threads; thread 0 gets the result.
+template <int NTH>
 __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
   a = warp_sum(a);
   b = warp_sum(b);
@@ -212,21 +348,22 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
   __syncthreads();
   if (threadIdx.x == 0) {
     double sa = 0, sb = 0;
-    for (int u = 0; u < NT / 32; u++) { sa += red[2 * u]; sb += red[2 * u + 1]; }
+    for (int u = 0; u < NTH / 32; u++) { sa += red[2 * u]; sb += red[2 * u + 1]; }
     a = sa; b = sb;
   }
   __syncthreads();
 }
 
-// Sum column c of n partials (stride 2) with the whole CTA in a fixed order.
+// Sum the two columns of n partials with the whole CTA in a fixed order.
+template <int NTH>
 __device__ __forceinline__ void sum_partials(const double *part, int n, double &s0, double &s1,
                                              double *red) {
   double a = 0, b = 0;
-  for (int t = threadIdx.x; t < n; t += NT) {
+  for (int t = threadIdx.x; t < n; t += NTH) {
     a += __ldcg(part + 2 * t);
     b += __ldcg(part + 2 * t + 1);
   }
-  block_sum2(a, b, red);
+  block_sum2<NTH>(a, b, red);
   s0 = a; s1 = b;
 }
 
@@ -304,11 +441,23 @@ __device__ void fin_resid(const Inst &I, Scal *S, double rr64, double rz) {
 // ---------------------------------------------------------------------------
 // Phase kernels.
 
+constexpr size_t RING_BYTES = ((size_t)3 * (WMAX + 2) * (HMAX + 2) * sizeof(double) + 127) / 128 * 128;
+
 template <typename T, int CM>
 __global__ void __launch_bounds__(NT) k_stencil(Batch B) {
-  __shared__ __align__(16) double smem[3][TY + 2][TX + 2];
+  extern __shared__ __align__(128) uint8_t dyn[];
+  __shared__ __align__(8) uint64_t full[NSTAGE];
   __shared__ double red[2 * (NT / 32)];
   __shared__ int s_phase, s_last;
+  double *ring = (double *)dyn;  // 3 planes with halo (FP64 view; FP32 view for the CG pass)
+  uint8_t *stages = dyn + RING_BYTES;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; s++) mbar_init(&full[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t seq = 0;
+  bool abort = false;
   for (int it = blockIdx.x; it < B.n_st_items; it += gridDim.x) {
     const Item item = B.st_items[it];
     const Inst &I = B.inst[item.inst];
@@ -319,9 +468,13 @@ __global__ void __launch_bounds__(NT) k_stencil(Batch B) {
     if (ph == PH_INNER || ph == PH_START || ph == PH_RESID) {
       const Scal S = *Sp;
       double v0 = 0, v1 = 0;
-      if (ph != PH_RESID) v0 = cg_tile<T, CM>(I, S, item.tile, (T(*)[TY + 2][TX + 2])smem);
-      else resid_tile<T, CM>(I, S, item.tile, smem, v0, v1);
-      block_sum2(v0, v1, red);
+      if (ph != PH_RESID) v0 = cg_tile<T, CM>(I, S, item.tile, stages, (T *)ring, full, seq, abort);
+      else resid_tile<T, CM>(I, S, item.tile, ring, v0, v1);
+      if (abort) {
+        if (threadIdx.x == 0) atomicOr(B.error, 2);  // a pipeline wait timed out
+        break;
+      }
+      block_sum2<NT>(v0, v1, red);
       if (threadIdx.x == 0) {
         double *part = B.st_part + 2 * (size_t)(I.st_base + item.tile);
         part[0] = v0;
@@ -334,7 +487,7 @@ __global__ void __launch_bounds__(NT) k_stencil(Batch B) {
       if (s_last) {
         __threadfence();
         double s0, s1;
-        sum_partials(B.st_part + 2 * (size_t)I.st_base, I.n_st, s0, s1, red);
+        sum_partials<NT>(B.st_part + 2 * (size_t)I.st_base, I.n_st, s0, s1, red);
         if (threadIdx.x == 0) {
           if (ph == PH_RESID) fin_resid(I, Sp, s0, s1);
           else fin_cg(I, Sp, s0);
@@ -346,10 +499,10 @@ __global__ void __launch_bounds__(NT) k_stencil(Batch B) {
 }
 
 template <typename T, int CM>
-__global__ void __launch_bounds__(NT) k_update(Batch B) {
+__global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
   constexpr int V = 16 / sizeof(T);
   typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type VT;
-  __shared__ double red[2 * (NT / 32)];
+  __shared__ double red[2 * (NT_UPD / 32)];
   __shared__ int s_phase, s_last;
   for (int it = blockIdx.x; it < B.n_ch_items; it += gridDim.x) {
     const Item item = B.ch_items[it];
@@ -359,27 +512,36 @@ __global__ void __launch_bounds__(NT) k_update(Batch B) {
     __syncthreads();
     if (s_phase == PH_INNER) {
       const T alpha = (T)Sp->alpha;
-      const size_t lo = (size_t)item.tile * CH;
-      const size_t hi = min(lo + (size_t)CH, I.n_pad);
+      const int vx = (I.nx + V - 1) / V;  // vectors per row (pads beyond nx are zero)
+      const int row0 = item.tile * I.rows_per_chunk;
+      const int nrows = min(I.rows_per_chunk, I.ny * I.nz - row0);
+      const int nvec = nrows * vx;
+      const size_t px = I.px;
       T *__restrict__ r = (T *)I.r;
       const T *__restrict__ ap = (const T *)I.ap;
       T rz = 0, rr = 0;
-      for (size_t e = lo + (size_t)threadIdx.x * V; e < hi; e += (size_t)NT * V) {
+#pragma unroll 2
+      for (int f = threadIdx.x; f < nvec; f += NT_UPD) {
+        const int row = f / vx, v = f - row * vx;
+        const size_t e = (size_t)(row0 + row) * px + (size_t)v * V;
         VT rv = *(const VT *)(r + e);
-        const VT av = *(const VT *)(ap + e);
+        const VT av = __ldcs((const VT *)(ap + e));
+        uint32_t codes;
+        if (V == 4) codes = *(const uint32_t *)(I.code + e);
+        else codes = *(const uint16_t *)(I.code + e);
         T *rp = (T *)&rv;
         const T *apv = (const T *)&av;
 #pragma unroll
         for (int u = 0; u < V; u++) {
           rp[u] = rp[u] - alpha * apv[u];
-          const T z = zval<T, CM>(I, e + u, rp[u]);
+          const T z = zval_code<T, CM>(I, (codes >> (8 * u)) & 0xffu, rp[u], e + u);
           rz += rp[u] * z;
           rr += rp[u] * rp[u];
         }
         *(VT *)(r + e) = rv;
       }
       double a = (double)rz, b = (double)rr;
-      block_sum2(a, b, red);
+      block_sum2<NT_UPD>(a, b, red);
       if (threadIdx.x == 0) {
         double *part = B.ch_part + 2 * (size_t)(I.ch_base + item.tile);
         part[0] = a;
@@ -392,7 +554,7 @@ __global__ void __launch_bounds__(NT) k_update(Batch B) {
       if (s_last) {
         __threadfence();
         double s0, s1;
-        sum_partials(B.ch_part + 2 * (size_t)I.ch_base, I.n_ch, s0, s1, red);
+        sum_partials<NT_UPD>(B.ch_part + 2 * (size_t)I.ch_base, I.n_ch, s0, s1, red);
         if (threadIdx.x == 0) fin_update(I, Sp, s0, s1);
       }
     }
@@ -403,10 +565,15 @@ __global__ void __launch_bounds__(NT) k_update(Batch B) {
 // ---------------------------------------------------------------------------
 // Host side
 
+size_t stencil_smem_bytes(int elem_size) {
+  return RING_BYTES + (size_t)NSTAGE * max_stage_bytes(elem_size);
+}
+
 template <typename T, int CM>
 static cudaError_t phase_impl(const Batch &B, const KernelGrid &kg, int which, cudaStream_t st) {
-  if (which & 1) k_stencil<T, CM><<<kg.stencil_blocks, NT, 0, st>>>(B);
-  if (which & 2) k_update<T, CM><<<kg.update_blocks, NT, 0, st>>>(B);
+  if (which & 1)
+    k_stencil<T, CM><<<kg.stencil_blocks, NT, stencil_smem_bytes(sizeof(T)), st>>>(B);
+  if (which & 2) k_update<T, CM><<<kg.update_blocks, NT_UPD, 0, st>>>(B);
   return cudaGetLastError();
 }
 
@@ -427,8 +594,10 @@ cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg
 
 template <typename T, int CM>
 static void occ(int &s, int &u) {
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM>, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&u, k_update<T, CM>, NT, 0);
+  const size_t sm = stencil_smem_bytes(sizeof(T));
+  cudaFuncSetAttribute(k_stencil<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM>, NT, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&u, k_update<T, CM>, NT_UPD, 0);
 }
 
 KernelGrid kernel_grid(int mode, int coef, int num_sms) {
@@ -440,8 +609,10 @@ KernelGrid kernel_grid(int mode, int coef, int num_sms) {
   else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u);
   else occ<float, COEF_PACKED>(s, u);
   KernelGrid kg;
-  kg.stencil_blocks = num_sms * (s > 0 ? s : 1);
-  kg.update_blocks = num_sms * (u > 0 ? u : 1);
+  kg.stencil_per_sm = s > 0 ? s : 1;
+  kg.update_per_sm = u > 0 ? u : 1;
+  kg.stencil_blocks = num_sms * kg.stencil_per_sm;
+  kg.update_blocks = num_sms * kg.update_per_sm;
   return kg;
 }
 

@@ -7,7 +7,40 @@ namespace pb {
 
 struct KernelGrid {  // persistent grid sizes of the phase kernels
   int stencil_blocks, update_blocks;
+  int stencil_per_sm, update_per_sm;  // resident CTAs per SM
 };
+
+// Shared-memory layout of one TMA stage of the stencil pass for a W x H tile
+// of elements of `es` bytes: r and p_old boxes (W + 2*16/es) x (H + 2), the
+// code box cw x (H + 2) bytes, the x box W x H; every box 128-byte aligned.
+struct StageLayout {
+  int rw, cw, rows, off_p, off_c, off_x, stage_bytes, tma_bytes;
+};
+inline StageLayout stage_layout(int W, int H, int es) {
+  StageLayout L;
+  const int pad = 16 / es;
+  L.rw = W + 2 * pad;
+  L.rows = H + 2;
+  L.cw = round_up(W + 17, 16);  // covers x0-1 .. x0+W from a 16-aligned start
+  const int rbytes = L.rw * L.rows * es, cbytes = L.cw * L.rows, xbytes = W * H * es;
+  L.off_p = round_up(rbytes, 128);
+  L.off_c = L.off_p + round_up(rbytes, 128);
+  L.off_x = L.off_c + round_up(cbytes, 128);
+  L.stage_bytes = L.off_x + round_up(xbytes, 128);
+  L.tma_bytes = 2 * rbytes + cbytes + xbytes;
+  return L;
+}
+// Largest stage over every tile the planner may choose (W <= WMAX, H <= HMAX, W*H <= NT).
+inline int max_stage_bytes(int es) {
+  int m = 0;
+  for (int W = 4; W <= WMAX; W += 4)
+    for (int H = 1; H <= HMAX && W * H <= NT; H++) {
+      const int b = stage_layout(W, H, es).stage_bytes;
+      m = b > m ? b : m;
+    }
+  return m;
+}
+size_t stencil_smem_bytes(int elem_size);
 
 // One tick: the stencil pass then the update pass over every instance.
 cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg, cudaStream_t st);

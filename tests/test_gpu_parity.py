@@ -189,6 +189,18 @@ def test_pcg_f64_parity_129(pbm, ctx, globule129):
         assert abs(info.iterations - ref.iters) <= max(1, 0.02 * ref.iters)
 
 
+def test_pcg_f64_parity_129_fp32_boundary(pbm, ctx, globule129):
+    # the FP32 Debye-Hueckel sum moves phi and E far less than the FP64 tolerances
+    p, s, ref, e_ref = globule129
+    spec = p.grid.replace(dh="f32")
+    with pbm.Grid(ctx, spec, p.atoms) as g:
+        phi, info = solve(pbm, g, spec, precision="f64", tol=1e-10)
+        assert info.status == 0
+        assert rel_max(phi, ref.phi) <= 1e-8
+        assert abs(g.energy(dev(phi)) - e_ref) <= 1e-8 * abs(e_ref)
+        assert abs(info.iterations - ref.iters) <= max(1, 0.02 * ref.iters)
+
+
 @pytest.mark.parametrize("coef", ["packed", "f32", "bf16"])
 def test_fp32_and_refinement_129(pbm, ctx, globule129, coef):
     p, s, ref, e_ref = globule129
