@@ -449,8 +449,10 @@ __global__ void __launch_bounds__(NT) k_stencil(Batch B) {
   __shared__ __align__(8) uint64_t full[NSTAGE];
   __shared__ double red[2 * (NT / 32)];
   __shared__ int s_phase, s_last;
-  double *ring = (double *)dyn;  // 3 planes with halo (FP64 view; FP32 view for the CG pass)
-  uint8_t *stages = dyn + RING_BYTES;
+  // TMA destinations must be 16-byte aligned; align the whole region to 128.
+  uint8_t *base = (uint8_t *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
+  double *ring = (double *)base;  // 3 planes with halo (FP64 view; FP32 view for the CG pass)
+  uint8_t *stages = base + RING_BYTES;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; s++) mbar_init(&full[s], 1);
     mbar_fence_init();
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
 // Host side
 
 size_t stencil_smem_bytes(int elem_size) {
-  return RING_BYTES + (size_t)NSTAGE * max_stage_bytes(elem_size);
+  return 128 + RING_BYTES + (size_t)NSTAGE * max_stage_bytes(elem_size);  // + alignment slack
 }
 
 template <typename T, int CM>
