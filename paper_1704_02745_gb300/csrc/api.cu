@@ -161,22 +161,27 @@ extern "C" pb_status pb_free_grid(pb_grid *g) {
 }
 
 // Stencil tiles: the fewest x tiles of width <= WMAX, then the tallest H with
-// W*H <= NT, then z chunks so that all tiles fit in one wave of resident CTAs.
-static void tile_plan(pb_grid *g, int resident) {
+// W*H <= NV*NT, then z chunks so that all tiles fit in one wave of resident CTAs.
+static void tile_plan(pb_grid *g, const KernelGrid &kg) {
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
   g->tiles_x = (nx + WMAX - 1) / WMAX;
-  g->W = round_up((nx + g->tiles_x - 1) / g->tiles_x, 4);
-  const int hmax = std::min(HMAX, NT / g->W);
+  g->W = round_up((nx + g->tiles_x - 1) / g->tiles_x, NV);
+  const int hmax = std::min(HMAX, NV * NT / g->W);
   g->tiles_y = (ny + hmax - 1) / hmax;
   g->H = (ny + g->tiles_y - 1) / g->tiles_y;
   const int cols = g->tiles_x * g->tiles_y;
+  const int resident = std::max(kg.stencil_blocks, 2 * g->ctx->num_sms);
   int zc = std::max(1, resident / cols);
   zc = std::min(zc, std::max(1, nz / 4));
   g->tz = (nz + zc - 1) / zc;
   g->tiles_z = (nz + g->tz - 1) / g->tz;
   g->n_st = cols * g->tiles_z;
-  g->rows_per_chunk = std::max(1, CH / nx);
-  g->n_ch = (int)(((long)ny * nz + g->rows_per_chunk - 1) / g->rows_per_chunk);
+  // update chunks: one wave of resident update CTAs on large grids, never
+  // fewer than CH elements per chunk
+  const long rows = (long)ny * nz;
+  const long by_count = (rows + kg.update_blocks - 1) / kg.update_blocks;
+  g->rows_per_chunk = (int)std::max<long>(std::max(1, CH / nx), by_count);
+  g->n_ch = (int)((rows + g->rows_per_chunk - 1) / g->rows_per_chunk);
 }
 
 // (Re)run the setup kernels of a grid for the given host atoms.
@@ -319,7 +324,7 @@ extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_
     pb_grid_release(g);
     return st;
   }
-  tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms).stencil_blocks);
+  tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms));
   *out = g;
   return PB_OK;
 #undef ALLOC
@@ -426,6 +431,10 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   I.W = g->W; I.H = g->H;
   I.tiles_x = g->tiles_x; I.tiles_y = g->tiles_y; I.tiles_z = g->tiles_z; I.tz = g->tz;
   I.n_st = g->n_st; I.n_ch = g->n_ch; I.rows_per_chunk = g->rows_per_chunk;
+  {
+    const uint64_t vx = (uint64_t)(g->d.nx + (mode == MODE_F64 ? 2 : 4) - 1) / (mode == MODE_F64 ? 2 : 4);
+    I.vx_magic = vx > 1 ? (uint32_t)(((1ull << 32) + vx - 1) / vx) : 0u;
+  }
   I.st_base = 0; I.ch_base = 0;
   I.mode = mode;
   I.precond = o ? (o->precond == PB_PRECOND_JACOBI) : 1;

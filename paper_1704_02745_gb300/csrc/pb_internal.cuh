@@ -6,7 +6,8 @@
 // and the (nx+1)-th x-edge fits in the row):
 //   code   uint8  [nz][ny][px]   packed coefficients, one byte per node:
 //                                bit 0/1 x-/x+ edge inside (eps_in), bit 2/3 y-/y+,
-//                                bit 4/5 z-/z+, bit 6 lambda (1 = ion accessible);
+//                                bit 4/5 z-/z+, bit 6 node inside an atom (lambda = 0
+//                                when the ion-exclusion mask is on);
 //                                pad bytes are 0
 //   b      f64    [nz][ny][px]   right-hand side of Eq. (4) with the boundary folded in
 //   x64    f64    [nz][ny][px]   solution (FP64)
@@ -28,14 +29,15 @@ struct __align__(32) dbl4 {  // four doubles, 32-byte aligned (atoms: x, y, z, q
   double x, y, z, w;
 };
 
-// Stencil tiles: W x H columns (W a multiple of 4, W <= 64, W*H <= NT) marching
-// over a z range; one CTA of NT threads per tile, one column per thread.
-constexpr int NT = 512;        // threads per stencil CTA
+// Stencil tiles: W x H columns (W a multiple of NV, W <= WMAX, H <= HMAX,
+// W*H <= NV*NT) marching over a z range; one CTA of NT threads per tile, each
+// thread owning NV consecutive x columns.
+constexpr int NT = 256;        // threads per stencil CTA
+constexpr int NV = 4;          // x columns per thread (16-byte vectors of FP32)
 constexpr int WMAX = 64;       // widest tile
-constexpr int HMAX = 16;       // tallest tile
-constexpr int NSTAGE = 4;      // TMA pipeline depth (z planes in flight per CTA)
+constexpr int HMAX = 24;       // tallest tile
 constexpr int NT_UPD = 256;    // threads per update CTA
-constexpr int CH = 8192;       // elements per chunk of the update pass
+constexpr int CH = 2048;       // fewest elements per chunk of the update pass
 constexpr int NDTAB = 14;      // diagonal table entries: (#inside edges 0..6) x (lambda 0/1)
 constexpr int PITCH_ALIGN = 16;  // node-array pitch in elements (TMA: 16-byte strides for bytes)
 
@@ -70,6 +72,7 @@ struct alignas(64) Inst {
   int cw;                             // width of the code box (bytes, multiple of 16)
   int stage_bytes, off_p, off_c, off_x, tma_bytes;  // TMA stage layout and bytes per stage
   int rows_per_chunk;                 // update-pass chunk
+  uint32_t vx_magic;                  // ceil(2^32 / vectors per row), for row = f*magic >> 32
   int nx, ny, nz, px;
   int tiles_x, tiles_y, tiles_z, tz;  // stencil tile decomposition
   int n_st, n_ch;                     // stencil tiles, elementwise chunks
@@ -104,11 +107,12 @@ struct Batch {  // device pointers describing a batch of instances
   int *error;            // device error word
 };
 
+// Index of a code byte in the diagonal tables: 2 * (#edges inside) + lambda.
 __host__ __device__ inline int dtab_index(uint32_t c) {
 #ifdef __CUDA_ARCH__
-  return 2 * __popc(c & 63u) + ((c >> 6) & 1u);
+  return 2 * __popc(c & 63u) + (((c >> 6) & 1u) ^ 1u);
 #else
-  return 2 * __builtin_popcount(c & 63u) + ((c >> 6) & 1u);
+  return 2 * __builtin_popcount(c & 63u) + (((c >> 6) & 1u) ^ 1u);
 #endif
 }
 

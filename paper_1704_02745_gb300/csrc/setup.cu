@@ -12,17 +12,10 @@
 namespace pb {
 
 // ---------------------------------------------------------------------------
-// Packed codes: start with every edge outside (eps_out) and lambda = 1.
-__global__ void k_init_code(uint8_t *code, int nx, int px, size_t n_pad, uint8_t init) {
+// Packed codes start at 0: every edge outside (eps_out), every node outside.
+__global__ void k_init_code(uint8_t *code, size_t n_pad) {
   size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  for (; e < n_pad; e += (size_t)gridDim.x * blockDim.x) code[e] = ((int)(e % px) < nx) ? init : 0;
-}
-
-__device__ __forceinline__ void set_bits(uint32_t *code32, size_t e, uint32_t bits) {
-  atomicOr(code32 + (e >> 2), bits << ((e & 3) * 8));
-}
-__device__ __forceinline__ void clear_bits(uint32_t *code32, size_t e, uint32_t bits) {
-  atomicAnd(code32 + (e >> 2), ~(bits << ((e & 3) * 8)));
+  for (; e < n_pad; e += (size_t)gridDim.x * blockDim.x) code[e] = 0;
 }
 
 __device__ __forceinline__ bool inside_sphere(double mx, double my, double mz, double ax, double ay,
@@ -40,50 +33,70 @@ __device__ __forceinline__ double mid_coord(double o, long i, double h) {
   return __dadd_rn(o, __dmul_rn(__dadd_rn((double)i, 0.5), h));
 }
 
-// One CTA per atom: every x/y/z edge and node of the atom's bounding box (one
-// spacing of margin) is tested; an inside edge sets the matching bit of both
-// nodes it joins, an inside node clears its lambda bit.  Writes are OR/AND of
-// the same bits, so the result does not depend on atom order.
+// One CTA per atom, one thread per node of the atom's bounding box (one
+// spacing of margin): the node and the midpoints of its six edges are tested
+// against the sphere, and the result is OR-ed into the node's code byte with
+// one atomic (bits 0-5: edges x-, x+, y-, y+, z-, z+ inside; bit 6: node
+// inside).  Each edge is tested by both of its nodes with the same exact rule,
+// so the two copies of its bit agree.  The test runs in FP32 with a wide
+// margin; points within the margin of the sphere surface are decided by the
+// exact FP64 test, so the map is the one the FP64 definition gives.
+constexpr float INSIDE_MARGIN = 1e-3f;  // relative to r^2 + 1; the FP32 error of d^2 is < 1e-5 A^2
 __global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *code32,
                               int kappa_mask) {
   const int a = blockIdx.x;
   if (a >= n_atoms) return;
   const dbl4 A = atoms[a];  // x, y, z, radius
   const double r2 = __dmul_rn(A.w, A.w);
-  const long i0 = (long)floor(__ddiv_rn(A.x - A.w - g.ox, g.h)) - 1;
-  const long i1 = (long)ceil(__ddiv_rn(A.x + A.w - g.ox, g.h)) + 1;
-  const long j0 = (long)floor(__ddiv_rn(A.y - A.w - g.oy, g.h)) - 1;
-  const long j1 = (long)ceil(__ddiv_rn(A.y + A.w - g.oy, g.h)) + 1;
-  const long k0 = (long)floor(__ddiv_rn(A.z - A.w - g.oz, g.h)) - 1;
-  const long k1 = (long)ceil(__ddiv_rn(A.z + A.w - g.oz, g.h)) + 1;
+  const float r2f = (float)r2, margin = INSIDE_MARGIN * (r2f + 1.0f);
+  const long i0 = max((long)floor(__ddiv_rn(A.x - A.w - g.ox, g.h)) - 1, 0L);
+  const long i1 = min((long)ceil(__ddiv_rn(A.x + A.w - g.ox, g.h)) + 1, (long)g.nx - 1);
+  const long j0 = max((long)floor(__ddiv_rn(A.y - A.w - g.oy, g.h)) - 1, 0L);
+  const long j1 = min((long)ceil(__ddiv_rn(A.y + A.w - g.oy, g.h)) + 1, (long)g.ny - 1);
+  const long k0 = max((long)floor(__ddiv_rn(A.z - A.w - g.oz, g.h)) - 1, 0L);
+  const long k1 = min((long)ceil(__ddiv_rn(A.z + A.w - g.oz, g.h)) + 1, (long)g.nz - 1);
+  if (i0 > i1 || j0 > j1 || k0 > k1) return;
+  const long ni = i1 - i0 + 1, nj = j1 - j0 + 1, cnt = ni * nj * (k1 - k0 + 1);
+  // FP32 offsets from the atom of the box's first node (exact up to one FP32
+  // rounding), then steps of h: a few hundred ulp of a few A at most
+  const float bx = (float)(node_coord(g.ox, i0, g.h) - A.x);
+  const float by = (float)(node_coord(g.oy, j0, g.h) - A.y);
+  const float bz = (float)(node_coord(g.oz, k0, g.h) - A.z);
+  const float hf = (float)g.h;
   const size_t rowp = (size_t)g.px, plane = (size_t)g.px * g.ny;
-  for (int kind = 0; kind < 4; kind++) {
-    // kind 0: x-edges (i from -1), 1: y-edges (j from -1), 2: z-edges (k from -1), 3: nodes
-    if (kind == 3 && !kappa_mask) break;
-    long ia = max(i0, kind == 0 ? -1L : 0L), ib = min(i1, (long)g.nx - 1);
-    long ja = max(j0, kind == 1 ? -1L : 0L), jb = min(j1, (long)g.ny - 1);
-    long ka = max(k0, kind == 2 ? -1L : 0L), kb = min(k1, (long)g.nz - 1);
-    if (ia > ib || ja > jb || ka > kb) continue;
-    const long ni = ib - ia + 1, nj = jb - ja + 1, nk = kb - ka + 1;
-    const long cnt = ni * nj * nk;
-    for (long t = threadIdx.x; t < cnt; t += blockDim.x) {
-      const long i = ia + t % ni, j = ja + (t / ni) % nj, k = ka + t / (ni * nj);
-      double mx = kind == 0 ? mid_coord(g.ox, i, g.h) : node_coord(g.ox, i, g.h);
-      double my = kind == 1 ? mid_coord(g.oy, j, g.h) : node_coord(g.oy, j, g.h);
-      double mz = kind == 2 ? mid_coord(g.oz, k, g.h) : node_coord(g.oz, k, g.h);
-      if (!inside_sphere(mx, my, mz, A.x, A.y, A.z, r2)) continue;
-      if (kind == 0) {
-        if (i >= 0) set_bits(code32, k * plane + j * rowp + i, 2u);            // x+ of node i
-        if (i + 1 < g.nx) set_bits(code32, k * plane + j * rowp + i + 1, 1u);  // x- of node i+1
-      } else if (kind == 1) {
-        if (j >= 0) set_bits(code32, k * plane + j * rowp + i, 8u);
-        if (j + 1 < g.ny) set_bits(code32, k * plane + (j + 1) * rowp + i, 4u);
-      } else if (kind == 2) {
-        if (k >= 0) set_bits(code32, k * plane + j * rowp + i, 32u);
-        if (k + 1 < g.nz) set_bits(code32, (k + 1) * plane + j * rowp + i, 16u);
-      } else {
-        clear_bits(code32, k * plane + j * rowp + i, 64u);
+  for (long t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const long i = i0 + t % ni, j = j0 + (t / ni) % nj, k = k0 + t / (ni * nj);
+    const float dx = bx + (float)(i - i0) * hf, dy = by + (float)(j - j0) * hf;
+    const float dz = bz + (float)(k - k0) * hf;
+    const float hh = 0.5f * hf;
+    // squared distances of the 7 test points: node, x-, x+, y-, y+, z-, z+ midpoints
+    const float yz = dy * dy + dz * dz, xz = dx * dx + dz * dz, xy = dx * dx + dy * dy;
+    float d2[7];
+    d2[0] = dx * dx + yz;
+    d2[1] = (dx - hh) * (dx - hh) + yz;
+    d2[2] = (dx + hh) * (dx + hh) + yz;
+    d2[3] = (dy - hh) * (dy - hh) + xz;
+    d2[4] = (dy + hh) * (dy + hh) + xz;
+    d2[5] = (dz - hh) * (dz - hh) + xy;
+    d2[6] = (dz + hh) * (dz + hh) + xy;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int p = 0; p < 7; p++) {
+      bool in;
+      if (d2[p] < r2f - margin) in = true;
+      else if (d2[p] > r2f + margin) in = false;
+      else {  // close to the surface: the exact FP64 test of the definition
+        const long ii = p == 1 ? i - 1 : i, jj = p == 3 ? j - 1 : j, kk = p == 5 ? k - 1 : k;
+        const double mx = (p == 1 || p == 2) ? mid_coord(g.ox, ii, g.h) : node_coord(g.ox, i, g.h);
+        const double my = (p == 3 || p == 4) ? mid_coord(g.oy, jj, g.h) : node_coord(g.oy, j, g.h);
+        const double mz = (p == 5 || p == 6) ? mid_coord(g.oz, kk, g.h) : node_coord(g.oz, k, g.h);
+        in = inside_sphere(mx, my, mz, A.x, A.y, A.z, r2);
       }
+      if (in) bits |= p == 0 ? (kappa_mask ? 64u : 0u) : (1u << (p - 1));
+    }
+    if (bits) {
+      const size_t e = k * plane + j * rowp + i;
+      atomicOr(code32 + (e >> 2), bits << ((e & 3) * 8));
     }
   }
 }
@@ -173,8 +186,20 @@ __global__ void __launch_bounds__(DH_NT) k_dh_f64(const dbl4 *xyzq, int n_atoms,
   if (t < n_ghost) ghost[t] = s;
 }
 
-// Same sum in FP32 arithmetic with a compensated (Kahan) FP32 accumulator;
-// the ghost value is stored as FP64.
+// Same sum in FP32 arithmetic: hardware reciprocal square root and base-2
+// exponential (rsqrt.approx, ex2.approx: a few ulp), FP32 partial sums over
+// blocks of DH_NT atoms added into an FP64 accumulator.  The ghost value is
+// stored as FP64.
+__device__ __forceinline__ float fast_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __global__ void __launch_bounds__(DH_NT) k_dh_f32(const dbl4 *xyzq, int n_atoms, Geom g,
                                                   double kappa, double eps_out, double *ghost,
                                                   long n_ghost) {
@@ -184,30 +209,29 @@ __global__ void __launch_bounds__(DH_NT) k_dh_f32(const dbl4 *xyzq, int n_atoms,
   if (t < n_ghost) ghost_pos(g, t, px, py, pz);
   // positions relative to the grid origin keep FP32 rounding small
   const float fx = (float)(px - g.ox), fy = (float)(py - g.oy), fz = (float)(pz - g.oz);
-  const float kf = (float)kappa, inv_eps = (float)(1.0 / eps_out);
-  float s = 0.f, comp = 0.f;
+  const float k2 = (float)(kappa * 1.4426950408889634);  // kappa / ln 2
+  const float inv_eps = (float)(1.0 / eps_out);
+  double s = 0.0;
   for (int base = 0; base < n_atoms; base += DH_NT) {
     __syncthreads();
     if (base + threadIdx.x < n_atoms) {
-      dbl4 A = xyzq[base + threadIdx.x];
+      const dbl4 A = xyzq[base + threadIdx.x];
       sa[threadIdx.x] = make_float4((float)(A.x - g.ox), (float)(A.y - g.oy), (float)(A.z - g.oz),
                                     (float)A.w * inv_eps);
     }
     __syncthreads();
     const int m = min(DH_NT, n_atoms - base);
+    float part = 0.f;
     for (int u = 0; u < m; u++) {
       const float4 A = sa[u];
-      float dx = fx - A.x, dy = fy - A.y, dz = fz - A.z;
-      float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      float rinv = rsqrtf(d2);
-      float term = A.w * expf(-kf * (d2 * rinv)) * rinv;
-      float y = term - comp;
-      float tt = s + y;
-      comp = (tt - s) - y;
-      s = tt;
+      const float dx = fx - A.x, dy = fy - A.y, dz = fz - A.z;
+      const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const float rinv = fast_rsqrt(d2);
+      part = fmaf(A.w * rinv, fast_exp2(-k2 * (d2 * rinv)), part);
     }
+    s += (double)part;
   }
-  if (t < n_ghost) ghost[t] = (double)s;
+  if (t < n_ghost) ghost[t] = s;
 }
 
 // b = (4 pi / h) q_node, then every boundary row adds eps_edge * phi_ghost for
@@ -284,7 +308,7 @@ __global__ void k_expand_coef(const uint8_t *code, Geom g, double ein, double eo
         s = s + (D)((c & 8u) ? ein : eout);
         s = s + (D)((c & 16u) ? ein : eout);
         s = s + (D)((c & 32u) ? ein : eout);
-        s = s + (D)kbh2 * (D)((c >> 6) & 1u);
+        s = s + (D)kbh2 * (D)(((c >> 6) & 1u) ^ 1u);
         dv = s;
       }
       diag[e] = dv;
@@ -298,7 +322,7 @@ __global__ void k_export_lambda(const uint8_t *code, Geom g, uint8_t *lam) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x) {
     const size_t i = t % g.nx, row = t / g.nx;
-    lam[t] = (code[row * g.px + i] >> 6) & 1u;
+    lam[t] = ((code[row * g.px + i] >> 6) & 1u) ^ 1u;
   }
 }
 
@@ -341,7 +365,7 @@ static int grid_for(size_t n, int nt) {
 cudaError_t launch_setup(const SetupArgs &a, cudaStream_t st) {
   const Geom &g = a.g;
   const size_t n_pad = (size_t)g.px * g.ny * g.nz;
-  k_init_code<<<grid_for(n_pad, 256), 256, 0, st>>>(a.code, g.nx, g.px, n_pad, 0x40);
+  k_init_code<<<grid_for(n_pad, 256), 256, 0, st>>>(a.code, n_pad);
   if (a.n_atoms > 0) {
     k_eps_scatter<<<a.n_atoms, 128, 0, st>>>(a.atoms_xyzr, a.n_atoms, g, (uint32_t *)a.code,
                                              a.kappa_mask);

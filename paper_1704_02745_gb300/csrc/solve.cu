@@ -87,37 +87,54 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start
+// launching now, and wait until the previous kernel's results are visible.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
-// Tile geometry.
+// Tile geometry.  A CTA owns a W x H column tile; thread t owns NV consecutive
+// x columns (a "group"), so all shared and global accesses of the centre
+// nodes are 16-byte vectors.
 
 struct TileG {
-  int x0, y0, z0, z1, tx, ty;
-  bool in_tile;  // thread owns a column of the W x H tile
-  bool valid;    // ... and that column is inside the grid
+  int x0, y0, z0, z1, tx, ty;  // tile origin and z range; group origin in the tile
+  bool in_tile;                // thread owns a group of the tile
+  bool row_ok;                 // ... whose row is inside the grid
+  uint32_t vmask;              // bit u: node tx+u is inside the grid
 };
 __device__ __forceinline__ TileG tile_g(const Inst &I, int tile) {
   TileG g;
   const int bx = tile % I.tiles_x, rest = tile / I.tiles_x;
   const int by = rest % I.tiles_y, bz = rest / I.tiles_y;
+  const int gw = I.W / NV;
   g.x0 = bx * I.W;
   g.y0 = by * I.H;
   g.z0 = bz * I.tz;
   g.z1 = min(g.z0 + I.tz, I.nz);
-  g.tx = threadIdx.x % I.W;
-  g.ty = threadIdx.x / I.W;
-  g.in_tile = threadIdx.x < I.W * I.H;
-  g.valid = g.in_tile && g.x0 + g.tx < I.nx && g.y0 + g.ty < I.ny;
+  g.tx = (threadIdx.x % gw) * NV;
+  g.ty = threadIdx.x / gw;
+  g.in_tile = (int)threadIdx.x < gw * I.H;
+  g.row_ok = g.in_tile && g.y0 + g.ty < I.ny;
+  g.vmask = 0;
+  if (g.row_ok)
+    for (int u = 0; u < NV; u++)
+      if (g.x0 + g.tx + u < I.nx) g.vmask |= 1u << u;
   return g;
 }
 
-// Halo cell owned by this thread: left/right columns then bottom/top rows.
+// Halo cell owned by this thread: cell h = lane * (NT/32) + warp, so every warp
+// gets the same share; cells are the left and right columns, then the bottom
+// and top rows.
 struct HaloG {
   int hx, hy;  // tile-relative position, -1 .. W / -1 .. H
   bool role;
 };
 __device__ __forceinline__ HaloG halo_g(const Inst &I) {
   HaloG h{0, 0, false};
-  const int t = threadIdx.x, W = I.W, H = I.H;
+  const int t = (threadIdx.x % 32) * (NT / 32) + threadIdx.x / 32, W = I.W, H = I.H;
   if (t < H) { h.hx = -1; h.hy = t; h.role = true; }
   else if (t < 2 * H) { h.hx = W; h.hy = t - H; h.role = true; }
   else if (t < 2 * H + W) { h.hx = t - 2 * H; h.hy = -1; h.role = true; }
@@ -133,147 +150,239 @@ __device__ __forceinline__ T zval_code(const Inst &I, uint32_t code, T r, size_t
   return r / ((const T *)I.diag)[e];
 }
 
+// NV-element vectors in 16-byte pieces.
+template <typename T> struct Vec { T v[NV]; };
+template <typename T>
+__device__ __forceinline__ Vec<T> ldv(const T *p) {
+  Vec<T> r;
+  if (sizeof(T) == 4) {
+    const float4 a = *(const float4 *)p;
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
+  } else {
+    const double2 a = ((const double2 *)p)[0], b = ((const double2 *)p)[1];
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void stv(T *p, const Vec<T> &r) {
+  if (sizeof(T) == 4) {
+    *(float4 *)p = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else {
+    ((double2 *)p)[0] = make_double2(r.v[0], r.v[1]);
+    ((double2 *)p)[1] = make_double2(r.v[2], r.v[3]);
+  }
+}
+
+// The scalars a tile reads (a copy of the full Scal would hold ~20 registers).
+struct TileScal {
+  double alpha, beta;
+  int phase, pbuf, xbuf, outer;
+};
+__device__ __forceinline__ TileScal tile_scal(const Scal *S) {
+  TileScal t;
+  t.alpha = S->alpha;
+  t.beta = S->beta;
+  t.phase = S->phase;
+  t.pbuf = S->pbuf;
+  t.xbuf = S->xbuf;
+  t.outer = S->outer;
+  return t;
+}
+
+template <typename T> struct Pair { T d, i; };
+
+// Stage ring of the TMA pipeline: stage index and the phase parity of every
+// stage, advanced one plane at a time.
+struct StageRing {
+  uint32_t st;     // stage of the next plane to consume
+  uint32_t phase;  // bit s: parity of the next completion of stage s
+};
+
 // ---------------------------------------------------------------------------
 // INNER phase, stencil pass of one tile (TMA pipeline).  Returns this
 // thread's p.Ap; sets `abort` if a pipeline wait timed out.
-template <typename T, int CM>
-__device__ __forceinline__ double cg_tile(const Inst &I, const Scal &S, int tile, uint8_t *stages,
-                                          T *ring, uint64_t *full, uint32_t &seq, bool &abort) {
+//
+// tab: {diag, 1/diag} of the FP32/FP64 operator for every code byte (1/diag
+// replaced by 1 without preconditioner), built in shared memory per item.
+template <typename T, int CM, int NS>
+__device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int tile,
+                                          uint8_t *stages, T *ring, const Pair<T> *tab,
+                                          uint64_t *full, StageRing &SR, bool &abort) {
   constexpr bool SEP = sizeof(T) == 4;  // FP32 inner solves accumulate into d
-  constexpr int PAD = 16 / (int)sizeof(T);
   const TileG G = tile_g(I, tile);
   const HaloG Hh = halo_g(I);
-  const int W = I.W, H = I.H, RW = W + 2 * PAD, CW = I.cw, RGW = W + 2;
+  const int W = I.W, H = I.H, RW = W + 2 * NV, CW = I.cw, RGW = W + 2 * NV;
+  const int ring_plane = RGW * (H + 2);
   const int cx0 = ((G.x0 - 1) >> 4) << 4;  // code box start: 16-byte aligned, <= x0 - 1
   const int Q = (G.z1 - G.z0) + 2;         // planes z0-1 .. z1
   const bool first = S.phase == PH_START;
-  const T beta = (T)S.beta, alpha = (T)S.alpha;
+  const T beta = first ? (T)0 : (T)S.beta, alpha = (T)S.alpha;
+  const T ei = e_in<T>(I), eo = e_out<T>(I);
   const CUtensorMap *m_pold = S.pbuf ? &I.tm_p1 : &I.tm_p0;
   const CUtensorMap *m_x = SEP ? &I.tm_x0 : (S.xbuf ? &I.tm_x1 : &I.tm_x0);
-  T *__restrict__ pnew = (T *)(S.pbuf ? I.p0 : I.p1);
-  T *__restrict__ ap = (T *)I.ap;
-  T *__restrict__ x = SEP ? (T *)I.d : (T *)(S.xbuf ? I.x64b : I.x64);
-  const size_t px = I.px, plane = (size_t)I.px * I.ny;
+  const size_t plane = (size_t)I.px * I.ny;
+  const size_t ec0 = (size_t)(G.y0 + G.ty) * I.px + (G.x0 + G.tx);
+  // output pointers walk plane by plane (first written plane: z0)
+  T *pnew = (T *)(S.pbuf ? I.p0 : I.p1) + (size_t)G.z0 * plane + ec0;
+  T *ap = (T *)I.ap + (size_t)G.z0 * plane + ec0;
+  T *x = (SEP ? (T *)I.d : (T *)(S.xbuf ? I.x64b : I.x64)) + (size_t)G.z0 * plane + ec0;
 
-  auto issue = [&](int q) {  // thread 0: load plane z0 - 1 + q into its stage
-    const uint32_t st = (seq + q) % NSTAGE;
-    uint8_t *sb = stages + (size_t)st * I.stage_bytes;
+  // thread 0 issues plane z0-1+q into stage st
+  auto issue = [&](int q, uint32_t st) {
+    uint8_t *sb = stages + st * (uint32_t)I.stage_bytes;
     const int z = G.z0 - 1 + q;
     mbar_expect_tx(&full[st], (uint32_t)I.tma_bytes);
-    tma_load_3d(sb, &I.tm_r, &full[st], G.x0 - PAD, G.y0 - 1, z);
-    tma_load_3d(sb + I.off_p, m_pold, &full[st], G.x0 - PAD, G.y0 - 1, z);
+    tma_load_3d(sb, &I.tm_r, &full[st], G.x0 - NV, G.y0 - 1, z);
+    tma_load_3d(sb + I.off_p, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
     tma_load_3d(sb + I.off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
     tma_load_3d(sb + I.off_x, m_x, &full[st], G.x0, G.y0, z);
   };
-  if (threadIdx.x == 0)
-    for (int q = 0; q < min(NSTAGE, Q); ++q) issue(q);
+  if (threadIdx.x == 0) {
+    uint32_t st = SR.st;
+    for (int q = 0; q < min(NS, Q); ++q) {
+      issue(q, st);
+      st = st + 1 == NS ? 0 : st + 1;
+    }
+  }
 
-  // positions of this thread's centre and halo cell in the stage boxes and the ring
-  const int hr = (Hh.hy + 1) * RW + (Hh.hx + PAD);
-  const int hc = (Hh.hy + 1) * CW + (G.x0 + Hh.hx - cx0);
-  const int hg = (Hh.hy + 1) * RGW + (Hh.hx + 1);
-  const int cr = (G.ty + 1) * RW + (G.tx + PAD);
+  // this thread's group and halo cell in the stage boxes and the ring
+  const int cr = (G.ty + 1) * RW + NV + G.tx;
   const int cc = (G.ty + 1) * CW + (G.x0 + G.tx - cx0);
-  const int cg = (G.ty + 1) * RGW + (G.tx + 1);
-  const size_t ec0 = (size_t)(G.y0 + G.ty) * px + (G.x0 + G.tx);
+  const int cg = (G.ty + 1) * RGW + NV + G.tx;
+  const int cx = G.ty * W + G.tx;
+  const int hr = (Hh.hy + 1) * RW + NV + Hh.hx;
+  const int hc = (Hh.hy + 1) * CW + (G.x0 + Hh.hx - cx0);
+  const int hg = (Hh.hy + 1) * RGW + NV + Hh.hx;
   const int hi = G.x0 + Hh.hx, hj = G.y0 + Hh.hy;
   const bool hin = hi >= 0 && hi < I.nx && hj >= 0 && hj < I.ny;
-  const size_t eh0 = hin ? (size_t)hj * px + hi : 0;
+  const size_t eh0 = hin ? (size_t)hj * I.px + hi : 0;
 
-  T pm = 0, pc = 0, po_prev = 0, x_prev = 0;
+  Vec<T> pm = {}, pc = {}, po_prev = {}, x_prev = {};
   uint32_t code_prev = 0;
   T acc = 0;
+  int rq = 0, rq1 = 2;  // ring plane of q and of q-1
+  uint32_t st_issue = SR.st;
+  for (int u = 0; u < min(NS, Q); ++u) st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
   for (int q = 0; q < Q; ++q) {
-    const uint32_t st = (seq + q) % NSTAGE, par = ((seq + q) / NSTAGE) & 1u;
-    const bool ok = mbar_wait(&full[st], par);
-    const uint8_t *sb = stages + (size_t)st * I.stage_bytes;
+    const uint32_t st = SR.st;
+    const bool ok = mbar_wait(&full[st], (SR.phase >> st) & 1u);
+    SR.phase ^= 1u << st;
+    SR.st = st + 1 == NS ? 0 : st + 1;
+    const uint8_t *sb = stages + st * (uint32_t)I.stage_bytes;
     const T *sr = (const T *)sb;
     const T *sp = (const T *)(sb + I.off_p);
     const uint8_t *sc = sb + I.off_c;
     const T *sx = (const T *)(sb + I.off_x);
-    T *rg = ring + (size_t)(q % 3) * RGW * (H + 2);
+    T *rg = ring + rq * ring_plane;
     const int z = G.z0 - 1 + q;
     const bool zin = z >= 0 && z < I.nz;
-    T pn = 0, po = 0, xv = 0;
-    uint32_t code = 0;
+    Vec<T> pn = {}, po = {}, xv = {};
+    uint32_t codes = 0;
     if (ok && G.in_tile) {
-      po = sp[cr];
-      code = sc[cc];
-      xv = sx[G.ty * W + G.tx];
-      if (CM == COEF_PACKED || (G.valid && zin)) {
-        const T zz = zval_code<T, CM>(I, code, sr[cr], (size_t)(zin ? z : 0) * plane + ec0);
-        pn = first ? zz : zz + beta * po;
+      const Vec<T> rv = ldv(sr + cr);
+      po = ldv(sp + cr);
+      xv = ldv(sx + cx);
+      codes = *(const uint32_t *)(sc + cc);
+#pragma unroll
+      for (int u = 0; u < NV; u++) {
+        if (CM == COEF_PACKED) {
+          pn.v[u] = rv.v[u] * tab[(codes >> (8 * u)) & 127u].i + beta * po.v[u];
+        } else if (zin && ((G.vmask >> u) & 1u)) {
+          pn.v[u] = zval_code<T, CM>(I, 0, rv.v[u], (size_t)z * plane + ec0 + u) + beta * po.v[u];
+        }
       }
-      rg[cg] = pn;
+      stv(rg + cg, pn);
     }
     if (ok && Hh.role) {
       T hv = 0;
-      if (CM == COEF_PACKED || (hin && zin)) {
-        const T zz = zval_code<T, CM>(I, sc[hc], sr[hr], (size_t)(zin ? z : 0) * plane + eh0);
-        hv = first ? zz : zz + beta * sp[hr];
+      if (CM == COEF_PACKED) {
+        hv = sr[hr] * tab[sc[hc] & 127u].i + beta * sp[hr];
+      } else if (hin && zin) {
+        hv = zval_code<T, CM>(I, 0, sr[hr], (size_t)z * plane + eh0) + beta * sp[hr];
       }
       rg[hg] = hv;
     }
     if (__syncthreads_or(!ok)) {
-      // A wait gave up: let the copies already issued (planes q .. q+NSTAGE-1)
-      // land, each for a bounded time, before the CTA leaves.
-      if (threadIdx.x == 0)
-        for (int u = q; u < min(Q, q + NSTAGE); ++u)
-          mbar_wait(&full[(seq + u) % NSTAGE], ((seq + u) / NSTAGE) & 1u);
+      // A wait gave up: let the copies already issued land, each for a
+      // bounded time, before the CTA leaves.
+      if (threadIdx.x == 0) {
+        uint32_t s2 = SR.st, ph = SR.phase;
+        for (int u = q + 1; u < min(Q, q + NS); ++u) {
+          mbar_wait(&full[s2], (ph >> s2) & 1u);
+          ph ^= 1u << s2;
+          s2 = s2 + 1 == NS ? 0 : s2 + 1;
+        }
+        SR.phase = ph;
+        SR.st = s2;
+      }
       abort = true;
-      seq += Q;
       return 0.0;
     }
-    if (threadIdx.x == 0 && q + NSTAGE < Q) issue(q + NSTAGE);
-    if (q >= 2 && G.valid) {
-      const int k = z - 1;
-      const size_t e = (size_t)k * plane + ec0;
-      const T *rm = ring + (size_t)((q - 1) % 3) * RGW * (H + 2);
-      NodeCoef<T> c;
-      if (CM == COEF_PACKED) {
-        const T ei = e_in<T>(I), eo = e_out<T>(I);
-        const uint32_t b = code_prev;
-        c.exm = (b & 1u) ? ei : eo; c.exp = (b & 2u) ? ei : eo;
-        c.eym = (b & 4u) ? ei : eo; c.eyp = (b & 8u) ? ei : eo;
-        c.ezm = (b & 16u) ? ei : eo; c.ezp = (b & 32u) ? ei : eo;
-        c.diag = tab_d<T>(I, dtab_index(b));
-      } else {
-        c = node_coef<T, CM>(I, e, k);
-      }
-      T s = c.exm * rm[cg - 1];
-      s += c.exp * rm[cg + 1];
-      s += c.eym * rm[cg - RGW];
-      s += c.eyp * rm[cg + RGW];
-      s += c.ezm * pm;
-      s += c.ezp * pn;
-      const T a = c.diag * pc - s;
-      pnew[e] = pc;
-      ap[e] = a;
-      if (SEP) x[e] = first ? (T)0 : x_prev + alpha * po_prev;
-      else if (!first) x[e] = x_prev + alpha * po_prev;
-      acc += pc * a;
+    if (threadIdx.x == 0 && q + NS < Q) {
+      issue(q + NS, st_issue);
+      st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
     }
-    pm = pc; pc = pn; po_prev = po; x_prev = xv; code_prev = code;
+    if (q >= 2) {
+      if (G.row_ok) {
+        const T *rm = ring + rq1 * ring_plane;
+        const Vec<T> ym = ldv(rm + cg - RGW), yp = ldv(rm + cg + RGW);
+        const T xl = rm[cg - 1], xr = rm[cg + NV];
+        Vec<T> a, xn;
+#pragma unroll
+        for (int u = 0; u < NV; u++) {
+          NodeCoef<T> c;
+          if (CM == COEF_PACKED) {
+            const uint32_t b = (code_prev >> (8 * u)) & 0xffu;
+            c.exm = (b & 1u) ? ei : eo; c.exp = (b & 2u) ? ei : eo;
+            c.eym = (b & 4u) ? ei : eo; c.eyp = (b & 8u) ? ei : eo;
+            c.ezm = (b & 16u) ? ei : eo; c.ezp = (b & 32u) ? ei : eo;
+            c.diag = tab[b & 127u].d;
+          } else if ((G.vmask >> u) & 1u) {
+            c = node_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0 + u, z - 1);
+          } else {
+            c = NodeCoef<T>{0, 0, 0, 0, 0, 0, 0};
+          }
+          T s = c.exm * (u == 0 ? xl : pc.v[u - 1]);
+          s += c.exp * (u == NV - 1 ? xr : pc.v[u + 1]);
+          s += c.eym * ym.v[u];
+          s += c.eyp * yp.v[u];
+          s += c.ezm * pm.v[u];
+          s += c.ezp * pn.v[u];
+          T av = c.diag * pc.v[u] - s;
+          if (!((G.vmask >> u) & 1u)) av = 0;  // pad columns keep Ap = 0
+          a.v[u] = av;
+          acc += pc.v[u] * av;
+          xn.v[u] = first ? (T)0 : x_prev.v[u] + alpha * po_prev.v[u];
+        }
+        stv(pnew, pc);
+        stv(ap, a);
+        if (SEP || !first) stv(x, xn);
+      }
+      pnew += plane; ap += plane; x += plane;
+    }
+    pm = pc; pc = pn; po_prev = po; x_prev = xv; code_prev = codes;
+    rq1 = rq;
+    rq = rq == 2 ? 0 : rq + 1;
   }
-  seq += Q;
   return (double)acc;
 }
 
 // RESID phase (FP64, plain loads): fold the deferred update, true residual,
-// new inner right-hand side.
+// new inner right-hand side.  Same groups of NV nodes per thread.
 template <typename T, int CM>
-__device__ __forceinline__ void resid_tile(const Inst &I, const Scal &S, int tile, double *ring,
+__device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int tile, double *ring,
                                            double &rr64, double &rz) {
   constexpr bool SEP = sizeof(T) == 4;
   const TileG G = tile_g(I, tile);
   const HaloG Hh = halo_g(I);
-  const int RGW = I.W + 2, H = I.H;
+  const int RGW = I.W + 2 * NV, H = I.H;
   const int hi = G.x0 + Hh.hx, hj = G.y0 + Hh.hy;
   const bool hvalid = Hh.role && hi >= 0 && hi < I.nx && hj >= 0 && hj < I.ny;
   const size_t px = I.px, plane = (size_t)I.px * I.ny;
   const size_t ec0 = (size_t)(G.y0 + G.ty) * px + (G.x0 + G.tx);
   const size_t eh0 = hvalid ? (size_t)hj * px + hi : 0;
-  const int cg = (G.ty + 1) * RGW + (G.tx + 1), hg = (Hh.hy + 1) * RGW + (Hh.hx + 1);
+  const int cg = (G.ty + 1) * RGW + NV + G.tx, hg = (Hh.hy + 1) * RGW + NV + Hh.hx;
   const double alpha = S.alpha;
   const double *__restrict__ xin = S.xbuf ? I.x64b : I.x64;
   double *__restrict__ xout = S.xbuf ? I.x64 : I.x64b;
@@ -288,45 +397,51 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const Scal &S, int til
     if (SEP) v += (double)d[e];
     return v + alpha * (double)p[e];
   };
-  double xm = 0, xc = 0;
-  if (G.valid && G.z0 > 0) xm = xn((size_t)(G.z0 - 1) * plane + ec0);
-  if (G.valid) xc = xn((size_t)G.z0 * plane + ec0);
-  if (G.in_tile) ring[cg] = xc;
+  auto group = [&](int k, double *out) {  // x_new of this thread's nodes in plane k
+#pragma unroll
+    for (int u = 0; u < NV; u++)
+      out[u] = ((G.vmask >> u) & 1u) && k >= 0 && k < I.nz ? xn((size_t)k * plane + ec0 + u) : 0.0;
+  };
+  double xm[NV], xc[NV], xnx[NV];
+  group(G.z0 - 1, xm);
+  group(G.z0, xc);
+  const int rsz = RGW * (H + 2);
+  if (G.in_tile)
+    for (int u = 0; u < NV; u++) ring[cg + u] = xc[u];
   if (Hh.role) ring[hg] = hvalid ? xn((size_t)G.z0 * plane + eh0) : 0.0;
   int cur = 0;
   rr64 = 0.0;
   rz = 0.0;
-  const int rsz = RGW * (H + 2);
   for (int k = G.z0; k < G.z1; ++k) {
     const int nxt = cur == 2 ? 0 : cur + 1;
-    double xnx = 0;
     double *rn = ring + (size_t)nxt * rsz;
-    if (k + 1 < I.nz) {
-      if (G.valid) xnx = xn((size_t)(k + 1) * plane + ec0);
-      if (Hh.role) rn[hg] = hvalid ? xn((size_t)(k + 1) * plane + eh0) : 0.0;
-    } else if (Hh.role) {
-      rn[hg] = 0.0;
-    }
-    if (G.in_tile) rn[cg] = xnx;
+    group(k + 1, xnx);
+    if (G.in_tile)
+      for (int u = 0; u < NV; u++) rn[cg + u] = xnx[u];
+    if (Hh.role) rn[hg] = hvalid && k + 1 < I.nz ? xn((size_t)(k + 1) * plane + eh0) : 0.0;
     __syncthreads();
-    if (G.valid) {
-      const double *rc = ring + (size_t)cur * rsz;
-      const size_t e = (size_t)k * plane + ec0;
+    const double *rc = ring + (size_t)cur * rsz;
+#pragma unroll
+    for (int u = 0; u < NV; u++) {
+      if (!((G.vmask >> u) & 1u)) continue;
+      const size_t e = (size_t)k * plane + ec0 + u;
       const NodeCoef<double> c = node_coef64<CM>(I, e, k);
-      double s = c.exm * rc[cg - 1];
-      s += c.exp * rc[cg + 1];
-      s += c.eym * rc[cg - RGW];
-      s += c.eyp * rc[cg + RGW];
-      s += c.ezm * xm;
-      s += c.ezp * xnx;
-      const double res = I.b[e] - (c.diag * xc - s);
-      xout[e] = xc;
+      double s = c.exm * rc[cg + u - 1];
+      s += c.exp * rc[cg + u + 1];
+      s += c.eym * rc[cg + u - RGW];
+      s += c.eyp * rc[cg + u + RGW];
+      s += c.ezm * xm[u];
+      s += c.ezp * xnx[u];
+      const double res = I.b[e] - (c.diag * xc[u] - s);
+      xout[e] = xc[u];
       const T rt = (T)res;
       r[e] = rt;
       rr64 += res * res;
       rz += (double)(rt * zval<T, CM>(I, e, rt));
     }
-    xm = xc; xc = xnx; cur = nxt;
+#pragma unroll
+    for (int u = 0; u < NV; u++) { xm[u] = xc[u]; xc[u] = xnx[u]; }
+    cur = nxt;
   }
 }
 
@@ -441,37 +556,79 @@ __device__ void fin_resid(const Inst &I, Scal *S, double rr64, double rz) {
 // ---------------------------------------------------------------------------
 // Phase kernels.
 
-constexpr size_t RING_BYTES = ((size_t)3 * (WMAX + 2) * (HMAX + 2) * sizeof(double) + 127) / 128 * 128;
+// Ring of three planes with halo, sized for the largest tile in FP64 (the
+// RESID pass).
+constexpr int RING_CELLS = max_ring_cells();
+__host__ __device__ constexpr size_t ring_bytes(size_t es) {
+  return ((size_t)3 * RING_CELLS * es + 127) / 128 * 128;
+}
+#ifndef PB_STAGES_F32
+#define PB_STAGES_F32 4  // TMA pipeline depth in z planes, FP32 inner solves
+#endif
+#ifndef PB_STAGES_F64
+#define PB_STAGES_F64 3  // ... FP64 solves (larger stages)
+#endif
+#ifndef PB_STENCIL_MINB
+#define PB_STENCIL_MINB 2  // resident stencil CTAs per SM the register budget targets
+#endif
+template <typename T> struct Stages {
+  static constexpr int n = sizeof(T) == 4 ? PB_STAGES_F32 : PB_STAGES_F64;
+};
+
+// {diag, 1/diag} by code byte for the operator of precision T (shared memory).
+template <typename T>
+__device__ __forceinline__ void build_tab(const Inst &I, Pair<T> *tab) {
+  if (threadIdx.x < 128) {
+    const int k = dtab_index(threadIdx.x);
+    tab[threadIdx.x].d = tab_d<T>(I, k);
+    tab[threadIdx.x].i = I.precond ? tab_i<T>(I, k) : (T)1;
+  }
+}
 
 template <typename T, int CM>
-__global__ void __launch_bounds__(NT) k_stencil(Batch B) {
+__global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
+  constexpr int NS = Stages<T>::n;
   extern __shared__ __align__(128) uint8_t dyn[];
-  __shared__ __align__(8) uint64_t full[NSTAGE];
+  __shared__ __align__(8) uint64_t full[NS];
   __shared__ double red[2 * (NT / 32)];
-  __shared__ int s_phase, s_last;
+  __shared__ Pair<T> tab[128];
+  __shared__ int s_phase, s_last, s_inst;
   // TMA destinations must be 16-byte aligned; align the whole region to 128.
+  // CG pass: ring of T planes, then the stages.  RESID pass (no TMA): an FP64
+  // ring over the same bytes.
   uint8_t *base = (uint8_t *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
-  double *ring = (double *)base;  // 3 planes with halo (FP64 view; FP32 view for the CG pass)
-  uint8_t *stages = base + RING_BYTES;
+  double *ring = (double *)base;
+  uint8_t *stages = base + ring_bytes(sizeof(T));
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; s++) mbar_init(&full[s], 1);
+    for (int s = 0; s < NS; s++) mbar_init(&full[s], 1);
     mbar_fence_init();
+    s_inst = -1;
   }
+  pdl_launch_dependents();
+  pdl_wait();
   __syncthreads();
-  uint32_t seq = 0;
+  StageRing SR{0u, 0u};
   bool abort = false;
   for (int it = blockIdx.x; it < B.n_st_items; it += gridDim.x) {
     const Item item = B.st_items[it];
     const Inst &I = B.inst[item.inst];
     Scal *Sp = I.s;
-    if (threadIdx.x == 0) s_phase = *(volatile int *)&Sp->phase;
+    const bool new_inst = s_inst != item.inst;
+    __syncthreads();  // everyone has read s_inst
+    if (threadIdx.x == 0) {
+      s_phase = *(volatile int *)&Sp->phase;
+      s_inst = item.inst;
+    }
+    if (new_inst) build_tab<T>(I, tab);
     __syncthreads();
     const int ph = s_phase;
     if (ph == PH_INNER || ph == PH_START || ph == PH_RESID) {
-      const Scal S = *Sp;
+      const TileScal S = tile_scal(Sp);
       double v0 = 0, v1 = 0;
-      if (ph != PH_RESID) v0 = cg_tile<T, CM>(I, S, item.tile, stages, (T *)ring, full, seq, abort);
-      else resid_tile<T, CM>(I, S, item.tile, ring, v0, v1);
+      if (ph != PH_RESID)
+        v0 = cg_tile<T, CM, NS>(I, S, item.tile, stages, (T *)ring, tab, full, SR, abort);
+      else
+        resid_tile<T, CM>(I, S, item.tile, ring, v0, v1);
       if (abort) {
         if (threadIdx.x == 0) atomicOr(B.error, 2);  // a pipeline wait timed out
         break;
@@ -503,44 +660,70 @@ __global__ void __launch_bounds__(NT) k_stencil(Batch B) {
 template <typename T, int CM>
 __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
   constexpr int V = 16 / sizeof(T);
+  constexpr int U = 4;  // vectors loaded before any is stored (loads in flight per thread)
   typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type VT;
   __shared__ double red[2 * (NT_UPD / 32)];
-  __shared__ int s_phase, s_last;
+  __shared__ Pair<T> tab[128];
+  __shared__ int s_phase, s_last, s_inst;
+  if (threadIdx.x == 0) s_inst = -1;
+  pdl_launch_dependents();
+  pdl_wait();
+  __syncthreads();
   for (int it = blockIdx.x; it < B.n_ch_items; it += gridDim.x) {
     const Item item = B.ch_items[it];
     const Inst &I = B.inst[item.inst];
     Scal *Sp = I.s;
-    if (threadIdx.x == 0) s_phase = *(volatile int *)&Sp->phase;
+    const bool new_inst = s_inst != item.inst;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_phase = *(volatile int *)&Sp->phase;
+      s_inst = item.inst;
+    }
+    if (new_inst) build_tab<T>(I, tab);
     __syncthreads();
     if (s_phase == PH_INNER) {
       const T alpha = (T)Sp->alpha;
-      const int vx = (I.nx + V - 1) / V;  // vectors per row (pads beyond nx are zero)
+      const uint32_t vx = (uint32_t)(I.nx + V - 1) / V;  // vectors per row; pads are zero
+      const uint32_t magic = I.vx_magic;                  // ceil(2^32 / vx): row = f * magic >> 32
       const int row0 = item.tile * I.rows_per_chunk;
-      const int nrows = min(I.rows_per_chunk, I.ny * I.nz - row0);
-      const int nvec = nrows * vx;
-      const size_t px = I.px;
-      T *__restrict__ r = (T *)I.r;
-      const T *__restrict__ ap = (const T *)I.ap;
+      const uint32_t nrows = (uint32_t)min(I.rows_per_chunk, I.ny * I.nz - row0);
+      const uint32_t nvec = nrows * vx;
+      T *__restrict__ r = (T *)I.r + (size_t)row0 * I.px;
+      const T *__restrict__ ap = (const T *)I.ap + (size_t)row0 * I.px;
+      const uint8_t *__restrict__ code = I.code + (size_t)row0 * I.px;
+      const uint32_t px = I.px;
       T rz = 0, rr = 0;
-#pragma unroll 2
-      for (int f = threadIdx.x; f < nvec; f += NT_UPD) {
-        const int row = f / vx, v = f - row * vx;
-        const size_t e = (size_t)(row0 + row) * px + (size_t)v * V;
-        VT rv = *(const VT *)(r + e);
-        const VT av = __ldcs((const VT *)(ap + e));
-        uint32_t codes;
-        if (V == 4) codes = *(const uint32_t *)(I.code + e);
-        else codes = *(const uint16_t *)(I.code + e);
-        T *rp = (T *)&rv;
-        const T *apv = (const T *)&av;
+      for (uint32_t f0 = threadIdx.x; f0 < nvec; f0 += U * NT_UPD) {
+        uint32_t e[U];
+        VT rv[U], av[U];
+        uint32_t codes[U];
 #pragma unroll
-        for (int u = 0; u < V; u++) {
-          rp[u] = rp[u] - alpha * apv[u];
-          const T z = zval_code<T, CM>(I, (codes >> (8 * u)) & 0xffu, rp[u], e + u);
-          rz += rp[u] * z;
-          rr += rp[u] * rp[u];
+        for (int k = 0; k < U; k++) {
+          const uint32_t f = f0 + k * NT_UPD;
+          const uint32_t row = vx == 1 ? f : __umulhi(f, magic);
+          e[k] = row * px + (f - row * vx) * V;
+          if (f < nvec) {
+            rv[k] = *(const VT *)(r + e[k]);
+            av[k] = __ldcs((const VT *)(ap + e[k]));
+            codes[k] = V == 4 ? *(const uint32_t *)(code + e[k]) : *(const uint16_t *)(code + e[k]);
+          }
         }
-        *(VT *)(r + e) = rv;
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+          if (f0 + k * NT_UPD >= nvec) break;
+          T *rp = (T *)&rv[k];
+          const T *apv = (const T *)&av[k];
+#pragma unroll
+          for (int u = 0; u < V; u++) {
+            rp[u] = rp[u] - alpha * apv[u];
+            T z;
+            if (CM == COEF_PACKED) z = rp[u] * tab[(codes[k] >> (8 * u)) & 127u].i;
+            else z = zval_code<T, CM>(I, 0, rp[u], (size_t)row0 * px + e[k] + u);
+            rz += rp[u] * z;
+            rr += rp[u] * rp[u];
+          }
+          *(VT *)(r + e[k]) = rv[k];
+        }
       }
       double a = (double)rz, b = (double)rr;
       block_sum2<NT_UPD>(a, b, red);
@@ -568,15 +751,38 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
 // Host side
 
 size_t stencil_smem_bytes(int elem_size) {
-  return 128 + RING_BYTES + (size_t)NSTAGE * max_stage_bytes(elem_size);  // + alignment slack
+  const int ns = elem_size == 4 ? Stages<float>::n : Stages<double>::n;
+  const size_t cg = ring_bytes(elem_size) + (size_t)ns * max_stage_bytes(elem_size);
+  const size_t resid = ring_bytes(sizeof(double));
+  return 128 + (cg > resid ? cg : resid);  // + alignment slack
+}
+
+// Launch with the programmatic-stream-serialization attribute, so a kernel
+// may be scheduled while its predecessor drains (each waits with
+// griddepcontrol.wait before touching the predecessor's results).
+template <typename... Args>
+static cudaError_t launch_pdl(void (*k)(Args...), int blocks, int threads, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 template <typename T, int CM>
 static cudaError_t phase_impl(const Batch &B, const KernelGrid &kg, int which, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
   if (which & 1)
-    k_stencil<T, CM><<<kg.stencil_blocks, NT, stencil_smem_bytes(sizeof(T)), st>>>(B);
-  if (which & 2) k_update<T, CM><<<kg.update_blocks, NT_UPD, 0, st>>>(B);
-  return cudaGetLastError();
+    e = launch_pdl(k_stencil<T, CM>, kg.stencil_blocks, NT, stencil_smem_bytes(sizeof(T)), st, B);
+  if (e == cudaSuccess && (which & 2)) e = launch_pdl(k_update<T, CM>, kg.update_blocks, NT_UPD, 0, st, B);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_phase(const Batch &B, int mode, int coef, const KernelGrid &kg, int which,

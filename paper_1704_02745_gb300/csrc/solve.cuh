@@ -11,15 +11,15 @@ struct KernelGrid {  // persistent grid sizes of the phase kernels
 };
 
 // Shared-memory layout of one TMA stage of the stencil pass for a W x H tile
-// of elements of `es` bytes: r and p_old boxes (W + 2*16/es) x (H + 2), the
-// code box cw x (H + 2) bytes, the x box W x H; every box 128-byte aligned.
+// of elements of `es` bytes: r and p_old boxes (W + 2*NV) x (H + 2) starting
+// NV columns left of the tile (16-byte aligned for FP32 and FP64), the code box
+// cw x (H + 2) bytes, the x box W x H; every box 128-byte aligned.
 struct StageLayout {
   int rw, cw, rows, off_p, off_c, off_x, stage_bytes, tma_bytes;
 };
 inline StageLayout stage_layout(int W, int H, int es) {
   StageLayout L;
-  const int pad = 16 / es;
-  L.rw = W + 2 * pad;
+  L.rw = W + 2 * NV;
   L.rows = H + 2;
   L.cw = round_up(W + 17, 16);  // covers x0-1 .. x0+W from a 16-aligned start
   const int rbytes = L.rw * L.rows * es, cbytes = L.cw * L.rows, xbytes = W * H * es;
@@ -30,13 +30,23 @@ inline StageLayout stage_layout(int W, int H, int es) {
   L.tma_bytes = 2 * rbytes + cbytes + xbytes;
   return L;
 }
-// Largest stage over every tile the planner may choose (W <= WMAX, H <= HMAX, W*H <= NT).
+// Largest stage over every tile the planner may choose.
 inline int max_stage_bytes(int es) {
   int m = 0;
-  for (int W = 4; W <= WMAX; W += 4)
-    for (int H = 1; H <= HMAX && W * H <= NT; H++) {
+  for (int W = NV; W <= WMAX; W += NV)
+    for (int H = 1; H <= HMAX && W * H <= NV * NT; H++) {
       const int b = stage_layout(W, H, es).stage_bytes;
       m = b > m ? b : m;
+    }
+  return m;
+}
+// Largest ring plane ((W + 2*NV) x (H + 2) cells) over the same tiles.
+constexpr int max_ring_cells() {
+  int m = 0;
+  for (int W = NV; W <= WMAX; W += NV)
+    for (int H = 1; H <= HMAX && W * H <= NV * NT; H++) {
+      const int c = (W + 2 * NV) * (H + 2);
+      m = c > m ? c : m;
     }
   return m;
 }

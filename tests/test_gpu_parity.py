@@ -66,6 +66,33 @@ def test_setup_arrays(pbm, ctx, maker, mask):
         assert rel_max(g.export("b"), s.b) < 1e-13
 
 
+def test_setup_surface_ties(pbm, ctx):
+    # radii equal (to the last bit, or one ulp either side) to the distance of
+    # a chosen edge midpoint or node: the exact FP64 rule decides those cases
+    rng = np.random.default_rng(77)
+    g = inputs.GridSpec(20, 18, 16, 0.45, (-4.1, -3.7, -3.3))
+    ox, oy, oz = g.origin
+    xyz, q, r = [], [], []
+    for t in range(60):
+        a = np.array([ox, oy, oz]) + rng.uniform(2.0, 5.5, 3)
+        i, j, k = rng.integers(2, 12, 3)
+        kind = t % 4
+        mx = ox + ((i + 0.5) if kind == 1 else i) * g.h
+        my = oy + ((j + 0.5) if kind == 2 else j) * g.h
+        mz = oz + ((k + 0.5) if kind == 3 else k) * g.h
+        dx, dy, dz = mx - a[0], my - a[1], mz - a[2]
+        d2 = dx * dx + dy * dy
+        d2 = d2 + dz * dz
+        rad = float(np.sqrt(d2))
+        rad = [rad, np.nextafter(rad, 0.0), np.nextafter(rad, 9.0)][t % 3]
+        xyz.append(a); q.append(rng.uniform(-1, 1)); r.append(rad)
+    atoms = inputs.Atoms(np.array(xyz), np.array(q), np.array(r))
+    s = oracle.setup(g, atoms)
+    with pbm.Grid(ctx, g, atoms) as grid:
+        for name, want in (("eps_x", s.ex), ("eps_y", s.ey), ("eps_z", s.ez), ("lambda", s.lam)):
+            assert np.array_equal(grid.export(name), want), name
+
+
 def test_setup_dh_f32(pbm, ctx):
     p = inputs.small_33()
     s = oracle.setup(p.grid, p.atoms)
