@@ -187,6 +187,74 @@ pb_status pb_grid_export(pb_grid *grid, int what, void *host_dst, size_t bytes);
  * `precision` (the admission model of the server). */
 size_t pb_grid_bytes(const pb_grid_desc *desc, int precision);
 
+/* ------------------------------------------------------------------------ */
+/* Continuous-batching server.  The paper's motivation is PB on thousands to
+ * millions of MD snapshots (Sec. 1); the server solves many snapshots at once:
+ * requests are admitted as device memory allows, each snapshot's grid stays
+ * resident per trajectory (the next snapshot warm-starts from the last
+ * solution), and all active grids advance together through the same
+ * persistent phase kernels, each under its own convergence mask.  A result
+ * does not depend on which other requests share the device (each grid's
+ * reductions are summed in its own fixed order). */
+
+typedef struct {
+    int64_t trajectory_id;   /* snapshots of one trajectory share a resident grid; -1: none */
+    pb_grid_desc desc;       /* grid of this snapshot (a trajectory keeps one desc) */
+    int n_atoms;
+    const double *xyz, *q, *radius; /* HOST arrays, copied by pb_batch_submit */
+    double *phi_out;         /* optional HOST buffer of nx*ny*nz doubles that receives phi;
+                                borrowed until pb_batch_poll returns the result */
+} pb_request;
+
+typedef struct {
+    int status;              /* pb_status of the request */
+    double energy;           /* kcal/mol, as pb_energy */
+    pb_solve_info info;
+    double seconds;          /* submit -> result ready (host clock) */
+    int warm_started;        /* 1 if the solve started from the trajectory's last solution */
+} pb_result;
+
+/* Server on ctx's device with a device-memory budget (bytes; grids are
+ * admitted while the sum of pb_grid_bytes stays within it) and the solve
+ * options applied to every request (precision, preconditioner, tolerances;
+ * warm_start = 1: later snapshots of a trajectory start from its last
+ * solution).  NULL opts: FP32 + FP64 refinement, Jacobi, rel_tol 1e-6.  The
+ * server runs a worker thread; pb_server_destroy stops it and frees all. */
+pb_status pb_server_create(pb_ctx *ctx, size_t hbm_budget_bytes, const pb_solve_opts *opts,
+                           pb_server **out);
+pb_status pb_server_destroy(pb_server *server);
+/* Queue a request (inputs copied).  PB_ERR_BUSY when the queue is full;
+ * PB_ERR_ARG for a bad request (checked on the host before queueing). */
+pb_status pb_batch_submit(pb_server *server, const pb_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (0: do not wait; < 0: wait until ready) for a
+ * ticket.  PB_ERR_TIMEOUT if not ready (the ticket stays valid);
+ * PB_ERR_NOT_FOUND for an unknown or already returned ticket.  Never blocks
+ * forever when timeout_ms >= 0. */
+pb_status pb_batch_poll(pb_server *server, uint64_t ticket, int timeout_ms, pb_result *result);
+/* Counters: requests queued, active on the device, grids resident, bytes
+ * resident, solves completed.  Any pointer may be NULL. */
+pb_status pb_server_stats(pb_server *server, int *queued, int *active, int *resident,
+                          size_t *bytes_resident, uint64_t *completed);
+
+/* Admission decision of the server, exposed for testing.  Requests are
+ * considered in queue order.  A request whose trajectory has an idle
+ * resident grid of the same dims reuses it; a request whose trajectory is
+ * busy waits; any other request needs req_bytes[i] new bytes, for which idle
+ * grids are evicted least recently used first.  The first request that does
+ * not fit stops admission of requests that need new memory (no overtaking).
+ * Outputs: admit[i] = index of the reused slot, -1 for a new slot, -2 not
+ * admitted; evict[j] = 1 for slots to evict.  Returns the number admitted. */
+typedef struct {
+    int64_t trajectory_id;
+    int nx, ny, nz;
+    size_t bytes;
+    int busy;                /* 1 while a request of this grid is on the device */
+    uint64_t last_used;      /* larger = more recent */
+} pb_slot_state;
+int pb_plan_admission(size_t budget, const pb_slot_state *slots, int n_slots,
+                      const int64_t *req_traj, const int *req_dims /* 3 per request */,
+                      const size_t *req_bytes, int n_reqs, int *admit, int *evict);
+
 #ifdef __cplusplus
 }
 #endif

@@ -123,7 +123,7 @@ static bool finite_all(const double *a, size_t n) {
   return true;
 }
 
-static pb_status check_desc(const pb_grid_desc *d) {
+pb_status pb_check_desc(const pb_grid_desc *d) {
   if (!d) return pb_fail(PB_ERR_ARG, "grid desc is NULL");
   if (d->nx < 1 || d->ny < 1 || d->nz < 1) return pb_fail(PB_ERR_ARG, "empty grid");
   if ((double)d->nx * d->ny * d->nz > 2.0e9) return pb_fail(PB_ERR_ARG, "grid too large");
@@ -144,10 +144,11 @@ static pb_status check_desc(const pb_grid_desc *d) {
 void pb_grid_release(pb_grid *g) {
   if (!g) return;
   if (g->graph) cudaGraphExecDestroy(g->graph);
-  void *ptrs[] = {g->code, g->b, g->ghost, g->xyzq, g->xyzr, g->err, g->scratch, g->ex, g->ey,
+  void *ptrs[] = {g->code, g->b, g->ghost, g->xyzq, g->xyzr, g->err, g->counts, g->scratch, g->ex, g->ey,
                   g->ez, g->diag, g->ex64, g->ey64, g->ez64, g->diag64, g->x64, g->x64b, g->d32,
-                  g->r32, g->p032, g->p132, g->ap32, g->r64, g->p064, g->p164, g->ap64, g->scal,
-                  g->dinst, g->st_items, g->ch_items, g->st_part, g->ch_part};
+                  g->r32, g->p032, g->p132, g->ap32, g->r64, g->p064, g->p164, g->ap64,
+                  g->own_scal ? (void *)g->scal : nullptr, g->dinst, g->st_items, g->ch_items, g->st_part,
+                  g->ch_part};
   for (void *p : ptrs) dfree(p);
   delete g;
 }
@@ -162,7 +163,9 @@ extern "C" pb_status pb_free_grid(pb_grid *g) {
 
 // Stencil tiles: the fewest x tiles of width <= WMAX, then the tallest H with
 // W*H <= NV*NT, then z chunks so that all tiles fit in one wave of resident CTAs.
-static void tile_plan(pb_grid *g, const KernelGrid &kg) {
+// batch = true (grids of a server): z chunks of at least 32 planes and update
+// chunks of at least 4*CH elements, since many grids share each launch.
+void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
   g->tiles_x = (nx + WMAX - 1) / WMAX;
   g->W = round_up((nx + g->tiles_x - 1) / g->tiles_x, NV);
@@ -172,7 +175,7 @@ static void tile_plan(pb_grid *g, const KernelGrid &kg) {
   const int cols = g->tiles_x * g->tiles_y;
   const int resident = std::max(kg.stencil_blocks, 2 * g->ctx->num_sms);
   int zc = std::max(1, resident / cols);
-  zc = std::min(zc, std::max(1, nz / 4));
+  zc = std::min(zc, std::max(1, nz / (batch ? 32 : 4)));
   g->tz = (nz + zc - 1) / zc;
   g->tiles_z = (nz + g->tz - 1) / g->tz;
   g->n_st = cols * g->tiles_z;
@@ -180,13 +183,13 @@ static void tile_plan(pb_grid *g, const KernelGrid &kg) {
   // fewer than CH elements per chunk
   const long rows = (long)ny * nz;
   const long by_count = (rows + kg.update_blocks - 1) / kg.update_blocks;
-  g->rows_per_chunk = (int)std::max<long>(std::max(1, CH / nx), by_count);
+  g->rows_per_chunk = (int)std::max<long>(std::max(1, (batch ? 4 * CH : CH) / nx), by_count);
   g->n_ch = (int)((rows + g->rows_per_chunk - 1) / g->rows_per_chunk);
 }
 
 // (Re)run the setup kernels of a grid for the given host atoms.
-static pb_status run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
-                           const double *radius) {
+pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
+                       const double *radius, bool sync) {
   cudaStream_t s = g->ctx->stream;
   const pb_grid_desc *desc = &g->d;
   if (!g->scratch || n_atoms > g->atom_cap) {  // first call (also with no atoms) or growth
@@ -199,7 +202,8 @@ static pb_status run_setup(pb_grid *g, int n_atoms, const double *xyz, const dou
     pb_status st;
     if ((st = pb_dalloc((void **)&g->xyzq, (size_t)(n_atoms + 1) * sizeof(dbl4)))) return st;
     if ((st = pb_dalloc((void **)&g->xyzr, (size_t)(n_atoms + 1) * sizeof(dbl4)))) return st;
-    if ((st = pb_dalloc((void **)&g->scratch, (264 + (size_t)n_atoms / 256 + 1) * sizeof(double))))
+    if ((st = pb_dalloc((void **)&g->scratch,
+                        (SCR_ENERGY_PART + (size_t)n_atoms / 256 + 1) * sizeof(double))))
       return st;
     g->atom_cap = n_atoms;
   }
@@ -222,8 +226,8 @@ static pb_status run_setup(pb_grid *g, int n_atoms, const double *xyz, const dou
   a.code = g->code;
   a.b = g->b;
   a.ghost = g->ghost;
-  a.scratch = g->scratch;
-  a.bnorm2 = g->scratch + 256;  // slot after the 256 partials
+  a.scratch = g->scratch + SCR_SETUP;  // 256 partials of ||b||^2
+  a.bnorm2 = g->scratch + SCR_BNORM2;
   a.err = g->err;
   a.kappa = g->kappa;
   a.ein = desc->eps_in;
@@ -239,25 +243,26 @@ static pb_status run_setup(pb_grid *g, int n_atoms, const double *xyz, const dou
   a.kappa_mask = desc->kappa_mask ? 1 : 0;
   a.dh_f32 = desc->dh_precision == PB_F32;
   CK(launch_setup(a, s));
-  g->ctx->launches += 5 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
-  g->ctx->h2d += 2 * (unsigned long long)n_atoms * sizeof(dbl4);
-  g->ctx->d2h += sizeof(int) + sizeof(double);
   if (desc->coef == PB_COEF_F64)
     CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, COEF_F64, g->ex64,
                      g->ey64, g->ez64, g->diag64, s));
   else if (desc->coef != PB_COEF_PACKED)
     CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, desc->coef, g->ex, g->ey,
                      g->ez, g->diag, s));
+  g->ctx->launches += 5 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
+  g->ctx->h2d += 2 * (unsigned long long)n_atoms * sizeof(dbl4);
+  if (!sync) return PB_OK;  // the error word and ||b||^2 stay on the device
   int *hbuf = (int *)g->ctx->host_scal;  // pinned staging: error word, then ||b||^2
   CK(cudaMemcpyAsync(hbuf, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync((double *)hbuf + 1, a.bnorm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  g->ctx->d2h += sizeof(int) + sizeof(double);
   CK(cudaStreamSynchronize(s));
   if (hbuf[0]) return pb_fail(PB_ERR_ARG, "an atom's trilinear cell leaves the grid");
   g->bnorm = std::sqrt(((double *)hbuf)[1]);
   return PB_OK;
 }
 
-static pb_status check_atoms(int n_atoms, const double *xyz, const double *q, const double *radius) {
+pb_status pb_check_atoms(int n_atoms, const double *xyz, const double *q, const double *radius) {
   if (n_atoms < 0) return pb_fail(PB_ERR_ARG, "n_atoms < 0");
   if (n_atoms > 0 && (!xyz || !q || !radius)) return pb_fail(PB_ERR_ARG, "atom arrays are NULL");
   if (n_atoms > 0 && (!finite_all(xyz, 3 * (size_t)n_atoms) || !finite_all(q, n_atoms) ||
@@ -269,26 +274,21 @@ static pb_status check_atoms(int n_atoms, const double *xyz, const double *q, co
 extern "C" pb_status pb_grid_update_atoms(pb_grid *g, int n_atoms, const double *xyz,
                                           const double *q, const double *radius) {
   if (!g) return pb_fail(PB_ERR_ARG, "pb_grid_update_atoms: NULL grid");
-  pb_status st = check_atoms(n_atoms, xyz, q, radius);
+  pb_status st = pb_check_atoms(n_atoms, xyz, q, radius);
   if (st) return st;
   CK(cudaSetDevice(g->ctx->device));
-  return run_setup(g, n_atoms, xyz, q, radius);
+  return pb_run_setup(g, n_atoms, xyz, q, radius, true);
 }
 
-extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_atoms,
-                                   const double *xyz, const double *q, const double *radius,
-                                   pb_grid **out) {
-  if (!ctx || !out) return pb_fail(PB_ERR_ARG, "pb_setup_grid: NULL ctx or out");
+// Allocate a grid and plan its tiles (no atoms yet).
+pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_grid **out) {
   *out = nullptr;
-  pb_status st = check_desc(desc);
+  pb_status st = pb_check_desc(desc);
   if (st) return st;
-  if ((st = check_atoms(n_atoms, xyz, q, radius))) return st;
   CK(cudaSetDevice(ctx->device));
-
   pb_grid *g = new pb_grid();
   g->ctx = ctx;
   g->d = *desc;
-  g->n_atoms = n_atoms;
   const int px = pitch_of(desc->nx);
   g->g = Geom{desc->nx, desc->ny, desc->nz, px, desc->h, desc->origin[0], desc->origin[1],
               desc->origin[2]};
@@ -297,7 +297,6 @@ extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_
   g->kappa = std::sqrt(kd2);
   g->kbh2 = desc->eps_out * kd2 * desc->h * desc->h;
   g->n_ghost = 2L * ((long)desc->ny * desc->nz + (long)desc->nx * desc->nz + (long)desc->nx * desc->ny);
-
 #define ALLOC(ptr, bytes)                                  \
   do {                                                     \
     pb_status a_ = pb_dalloc((void **)&(ptr), (bytes));    \
@@ -307,6 +306,7 @@ extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_
   ALLOC(g->b, g->n_pad * sizeof(double));
   ALLOC(g->ghost, g->n_ghost * sizeof(double));
   ALLOC(g->err, sizeof(int) * 4);
+  ALLOC(g->counts, sizeof(int) * 2);
   if (desc->coef != PB_COEF_PACKED) {
     const size_t nc = (size_t)px * (desc->ny + 1) * (desc->nz + 1);
     if (desc->coef == PB_COEF_F64) {
@@ -318,16 +318,28 @@ extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_
       ALLOC(g->diag, g->n_pad * 4);
     }
   }
+#undef ALLOC
+  pb_tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms), batch);
+  *out = g;
+  return PB_OK;
+}
 
-  st = run_setup(g, n_atoms, xyz, q, radius);
-  if (st) {
+extern "C" pb_status pb_setup_grid(pb_ctx *ctx, const pb_grid_desc *desc, int n_atoms,
+                                   const double *xyz, const double *q, const double *radius,
+                                   pb_grid **out) {
+  if (!ctx || !out) return pb_fail(PB_ERR_ARG, "pb_setup_grid: NULL ctx or out");
+  *out = nullptr;
+  pb_status st = pb_check_desc(desc);
+  if (st) return st;
+  if ((st = pb_check_atoms(n_atoms, xyz, q, radius))) return st;
+  pb_grid *g = nullptr;
+  if ((st = pb_grid_create(ctx, desc, false, &g))) return st;
+  if ((st = pb_run_setup(g, n_atoms, xyz, q, radius, true))) {
     pb_grid_release(g);
     return st;
   }
-  tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms));
   *out = g;
   return PB_OK;
-#undef ALLOC
 }
 
 extern "C" size_t pb_grid_bytes(const pb_grid_desc *d, int precision) {
@@ -388,8 +400,10 @@ pb_status pb_ensure_workspace(pb_grid *g, int mode) {
     if ((st = pb_dalloc((void **)&g->ch_items, ci.size() * sizeof(Item)))) return st;
     if ((st = pb_dalloc((void **)&g->st_part, 2 * sizeof(double) * g->n_st))) return st;
     if ((st = pb_dalloc((void **)&g->ch_part, 2 * sizeof(double) * g->n_ch))) return st;
+    const int counts[2] = {g->n_st, g->n_ch};
     if (cudaMemcpy(g->st_items, si.data(), si.size() * sizeof(Item), cudaMemcpyHostToDevice) ||
-        cudaMemcpy(g->ch_items, ci.data(), ci.size() * sizeof(Item), cudaMemcpyHostToDevice))
+        cudaMemcpy(g->ch_items, ci.data(), ci.size() * sizeof(Item), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(g->counts, counts, sizeof(counts), cudaMemcpyHostToDevice))
       return pb_fail(PB_ERR_CUDA, "copy work items");
   }
   return PB_OK;
@@ -444,6 +458,8 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   I.tol = o ? o->rel_tol : 0;
   I.inner_tol = o ? o->inner_tol : 0;
   I.bnorm = g->bnorm;
+  I.err = g->err;
+  I.bnorm2 = g->scratch + SCR_BNORM2;
   I.n_pad = g->n_pad;
   I.code = g->code;
   if (coef == COEF_F64) {
@@ -501,9 +517,10 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   return PB_OK;
 }
 
-Scal pb_initial_scal() {
+Scal pb_initial_scal(double bnorm) {
   Scal S;
   memset(&S, 0, sizeof(S));
+  S.bnorm = bnorm;
   S.phase = PH_RESID;
   S.ref_norm = 1.0;
   S.rz_old = 1.0;
@@ -547,8 +564,7 @@ Batch pb_single_batch(pb_grid *g) {
   B.inst = g->dinst;
   B.st_items = g->st_items;
   B.ch_items = g->ch_items;
-  B.n_st_items = g->n_st;
-  B.n_ch_items = g->n_ch;
+  B.n_items = g->counts;
   B.st_part = g->st_part;
   B.ch_part = g->ch_part;
   B.error = g->err;
@@ -672,7 +688,7 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   if (mode != MODE_F32_REFINE) oo.max_outer = 1;
   Inst I;
   if ((st = pb_make_inst(g, &oo, mode, coef, I))) return st;
-  Scal S0 = pb_initial_scal();
+  Scal S0 = pb_initial_scal(g->bnorm);
   CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(g->scal, &S0, sizeof(Scal), cudaMemcpyHostToDevice, s));
@@ -735,10 +751,10 @@ extern "C" pb_status pb_energy(pb_grid *g, const double *phi, double *energy) {
   if (!g || !phi || !energy) return pb_fail(PB_ERR_ARG, "pb_energy: NULL argument");
   CK(cudaSetDevice(g->ctx->device));
   cudaStream_t s = g->ctx->stream;
-  // scratch[0] receives the energy, scratch[8..] the per-CTA partials
   CK(launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.h, g->d.origin[0],
-                   g->d.origin[1], g->d.origin[2], phi, g->scratch + 8, g->scratch, s));
-  CK(cudaMemcpyAsync(energy, g->scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+                   g->d.origin[1], g->d.origin[2], phi, g->scratch + SCR_ENERGY_PART,
+                   g->scratch + SCR_ENERGY, s));
+  CK(cudaMemcpyAsync(energy, g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost, s));
   g->ctx->launches += g->n_atoms > 0 ? 2 : 1;
   g->ctx->d2h += sizeof(double);
   CK(cudaStreamSynchronize(s));

@@ -37,7 +37,9 @@ struct pb_grid {
   double *x64 = nullptr, *x64b = nullptr;
   void *d32 = nullptr, *r32 = nullptr, *p032 = nullptr, *p132 = nullptr, *ap32 = nullptr;
   double *r64 = nullptr, *p064 = nullptr, *p164 = nullptr, *ap64 = nullptr;
-  pb::Scal *scal = nullptr;
+  pb::Scal *scal = nullptr;  // own allocation, or a slot of a server's scalar array
+  bool own_scal = true;
+  int *counts = nullptr;     // device: stencil and update item counts of the single-grid batch
   pb::Inst *dinst = nullptr;
   pb::Item *st_items = nullptr, *ch_items = nullptr;
   double *st_part = nullptr, *ch_part = nullptr;
@@ -54,4 +56,18 @@ void pb_grid_release(pb_grid *g);
 int pb_inner_coef(const pb_grid *g, int mode);
 pb_status pb_ensure_workspace(pb_grid *g, int mode);
 pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int coef, pb::Inst &I);
-pb::Scal pb_initial_scal();
+pb::Scal pb_initial_scal(double bnorm);
+pb_status pb_check_desc(const pb_grid_desc *d);
+pb_status pb_check_atoms(int n_atoms, const double *xyz, const double *q, const double *radius);
+pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_grid **out);
+pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
+                       const double *radius, bool sync);
+pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks);
+
+// Layout of a grid's FP64 scratch buffer.
+enum : size_t {
+  SCR_ENERGY = 0,        // energy result
+  SCR_BNORM2 = 1,        // ||b||^2 from the setup
+  SCR_SETUP = 8,         // 256 partials of the setup's norm reduction
+  SCR_ENERGY_PART = 264  // per-CTA partials of the energy (one per 256 atoms)
+};

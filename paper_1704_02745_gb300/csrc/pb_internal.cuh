@@ -54,6 +54,7 @@ struct Scal {
   double ref_norm;     // ||rhs|| of the current inner solve
   double relres;       // recursive residual / ref_norm
   double relres_true;  // ||b - A x|| / ||b|| (FP64)
+  double bnorm;        // ||b||
   int phase;           // Phase
   int pbuf;            // index of the buffer holding the latest direction p
   int iter;            // iterations of the current inner solve
@@ -86,6 +87,8 @@ struct alignas(64) Inst {
   const double *b;
   void *d, *r, *p0, *p1, *ap;         // inner work vectors
   Scal *s;
+  const int *err;                     // the grid's setup error word
+  const double *bnorm2;               // ||b||^2 as the setup left it
   double ein, eout, kbh2;
   double dtab[NDTAB], idtab[NDTAB];   // FP64 diagonal and its inverse by (n_in, lambda)
   float dtab32[NDTAB], idtab32[NDTAB];
@@ -101,7 +104,8 @@ struct Batch {  // device pointers describing a batch of instances
   const Inst *inst;
   const Item *st_items;  // stencil tiles of all instances
   const Item *ch_items;  // elementwise chunks of all instances
-  int n_st_items, n_ch_items;
+  const int *n_items;    // [0]: stencil items, [1]: update items (device memory, so a
+                         // captured device graph serves any active set)
   double *st_part;       // 3 doubles per stencil tile
   double *ch_part;       // 2 doubles per chunk
   int *error;            // device error word

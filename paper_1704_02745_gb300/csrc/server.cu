@@ -1,0 +1,670 @@
+// server.cu -- continuous-batching solve server of libpb (pb_server_*,
+// pb_batch_*): many MD snapshots (arXiv:1704.02745 Sec. 1: PB over thousands
+// to millions of snapshots) solved together on one GPU.
+//
+// A worker thread owns the server's CUDA work.  Each loop it
+//   1. admits queued requests (pb_plan_admission) into resident grids --
+//      one per trajectory, reused snapshot after snapshot, so a solve starts
+//      from the trajectory's last solution -- evicting idle grids LRU when the
+//      device-memory budget requires;
+//   2. runs the setup kernels of the admitted snapshots and starts their
+//      solves on the device (no host round trip);
+//   3. rebuilds the batch's work list when the active set changed: stencil
+//      tiles and update chunks of every active grid, each grid's partial sums
+//      at its own offset, so its reductions are summed in a fixed order
+//      whatever else runs;
+//   4. launches a captured device graph of `ticks` phase ticks over the whole
+//      batch (finished grids are skipped by their convergence mask);
+//   5. reads all grids' scalars and completes the finished requests (energy,
+//      optional copy of phi to the caller).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "pb.h"
+#include "pb_host.h"
+#include "pb_internal.cuh"
+#include "solve.cuh"
+
+using namespace pb;
+
+// ---------------------------------------------------------------------------
+// Admission planner (pure host logic).
+
+extern "C" int pb_plan_admission(size_t budget, const pb_slot_state *slots, int n_slots,
+                                 const int64_t *req_traj, const int *req_dims,
+                                 const size_t *req_bytes, int n_reqs, int *admit, int *evict) {
+  std::vector<char> busy(n_slots), gone(n_slots, 0);
+  size_t used = 0;
+  for (int j = 0; j < n_slots; j++) {
+    busy[j] = slots[j].busy != 0;
+    used += slots[j].bytes;
+    evict[j] = 0;
+  }
+  int n_admit = 0;
+  bool blocked = false;  // a request needing new memory did not fit: no overtaking
+  std::vector<int64_t> waiting;  // trajectories with an earlier request not admitted
+  for (int i = 0; i < n_reqs; i++) {
+    admit[i] = -2;
+    const int64_t tr = req_traj[i];
+    const bool has_traj = tr >= 0;
+    if (has_traj && std::find(waiting.begin(), waiting.end(), tr) != waiting.end()) continue;
+    // a resident grid of this trajectory
+    int own = -1;
+    if (has_traj)
+      for (int j = 0; j < n_slots; j++)
+        if (!gone[j] && slots[j].trajectory_id == tr) { own = j; break; }
+    if (own >= 0 && busy[own]) {  // the previous snapshot is still on the device
+      waiting.push_back(tr);
+      continue;
+    }
+    if (own >= 0 && slots[own].nx == req_dims[3 * i] && slots[own].ny == req_dims[3 * i + 1] &&
+        slots[own].nz == req_dims[3 * i + 2]) {
+      admit[i] = own;
+      busy[own] = 1;
+      n_admit++;
+      continue;
+    }
+    if (blocked) {
+      if (has_traj) waiting.push_back(tr);
+      continue;
+    }
+    // new memory: a stale grid of this trajectory goes first, then LRU idle grids
+    size_t need = req_bytes[i];
+    if (own >= 0) {
+      gone[own] = 1;
+      evict[own] = 1;
+      used -= slots[own].bytes;
+    }
+    while (used + need > budget) {
+      int lru = -1;
+      for (int j = 0; j < n_slots; j++)
+        if (!gone[j] && !busy[j] && (lru < 0 || slots[j].last_used < slots[lru].last_used)) lru = j;
+      if (lru < 0) break;
+      gone[lru] = 1;
+      evict[lru] = 1;
+      used -= slots[lru].bytes;
+    }
+    if (used + need > budget) {
+      blocked = true;
+      if (has_traj) waiting.push_back(tr);
+      continue;
+    }
+    used += need;
+    admit[i] = -1;
+    n_admit++;
+  }
+  return n_admit;
+}
+
+// ---------------------------------------------------------------------------
+// Server state.
+
+namespace {
+
+constexpr int MAX_SLOTS = 1024;  // resident grids (device scalar / descriptor arrays)
+constexpr int MAX_QUEUE = 1 << 20;
+
+struct Request {
+  uint64_t ticket;
+  int64_t traj;
+  pb_grid_desc desc;
+  std::vector<double> xyz, q, r;
+  double *phi_out;
+  std::chrono::steady_clock::time_point t_submit;
+  size_t bytes;
+};
+
+struct Slot {
+  pb_grid *g = nullptr;
+  int64_t traj = -1;
+  size_t bytes = 0;
+  bool busy = false;
+  bool has_solution = false;  // x64 holds this trajectory's last solution
+  uint64_t last_used = 0;
+  Request req;
+  bool warm = false;
+};
+
+}  // namespace
+
+struct pb_server {
+  pb_ctx *ctx = nullptr;
+  size_t budget = 0;
+  pb_solve_opts opts{};
+  int mode = MODE_F32_REFINE, coef = COEF_PACKED;
+  // host side
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::deque<Request> queue;
+  std::unordered_map<uint64_t, pb_result> done;
+  std::unordered_set<uint64_t> outstanding;  // submitted, result not yet returned by a poll
+  uint64_t next_ticket = 1, completed = 0, clock = 0;
+  int n_active = 0, n_resident = 0;
+  size_t bytes_resident = 0;
+  // worker-only state
+  cudaStream_t stream = nullptr;
+  std::vector<Slot> slots;  // index = device slot
+  std::vector<int> free_slots;
+  Scal *d_scal = nullptr, *h_scal = nullptr;
+  Inst *d_inst = nullptr;
+  int *d_counts = nullptr, *d_list = nullptr, *d_err = nullptr;
+  Item *d_st = nullptr, *d_ch = nullptr;
+  double *d_st_part = nullptr, *d_ch_part = nullptr;
+  size_t cap_st = 0, cap_ch = 0;
+  double *d_dense = nullptr;
+  size_t cap_dense = 0;
+  cudaGraphExec_t graph = nullptr;
+  int ticks = 8;
+  KernelGrid kg{};
+  std::string worker_error;
+};
+
+namespace {
+
+double since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+bool cuda_ok(cudaError_t e, pb_server *s, const char *what) {
+  if (e == cudaSuccess) return true;
+  s->worker_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+// Grow a device array (contents not kept).
+template <typename T>
+bool grow(T **p, size_t *cap, size_t need) {
+  if (need <= *cap) return true;
+  size_t n = std::max(need, *cap * 2);
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (pb_dalloc((void **)p, n * sizeof(T))) {
+    *cap = 0;
+    return false;
+  }
+  *cap = n;
+  return true;
+}
+
+void fail_request(pb_server *s, const Request &rq, int status) {
+  pb_result r;
+  memset(&r, 0, sizeof(r));
+  r.status = status;
+  r.info.status = status;
+  r.seconds = since(rq.t_submit);
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->done[rq.ticket] = r;
+  s->completed++;
+  s->cv_done.notify_all();
+}
+
+// Release the grid of a slot.
+void evict_slot(pb_server *s, int j) {
+  Slot &sl = s->slots[j];
+  if (sl.g) {
+    sl.g->scal = nullptr;  // a slot of the server's array, not the grid's own
+    pb_grid_release(sl.g);
+  }
+  sl = Slot();
+  s->free_slots.push_back(j);
+}
+
+// Admit queued requests; returns the slots whose solves start now.
+std::vector<int> admit(pb_server *s) {
+  std::vector<Request> cand;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t look = std::min<size_t>(s->queue.size(), 4096);
+    for (size_t i = 0; i < look; i++) cand.push_back(s->queue[i]);
+  }
+  std::vector<int> started;
+  if (cand.empty()) return started;
+  std::vector<int> idx;  // occupied slot indices
+  std::vector<pb_slot_state> st;
+  for (int j = 0; j < (int)s->slots.size(); j++)
+    if (s->slots[j].g) {
+      idx.push_back(j);
+      const Slot &sl = s->slots[j];
+      st.push_back(pb_slot_state{sl.traj, sl.g->d.nx, sl.g->d.ny, sl.g->d.nz, sl.bytes,
+                                 sl.busy ? 1 : 0, sl.last_used});
+    }
+  std::vector<int64_t> traj(cand.size());
+  std::vector<int> dims(3 * cand.size());
+  std::vector<size_t> bytes(cand.size());
+  for (size_t i = 0; i < cand.size(); i++) {
+    traj[i] = cand[i].traj;
+    dims[3 * i] = cand[i].desc.nx;
+    dims[3 * i + 1] = cand[i].desc.ny;
+    dims[3 * i + 2] = cand[i].desc.nz;
+    bytes[i] = cand[i].bytes;
+  }
+  std::vector<int> adm(cand.size()), ev(st.size());
+  pb_plan_admission(s->budget, st.data(), (int)st.size(), traj.data(), dims.data(), bytes.data(),
+                    (int)cand.size(), adm.data(), ev.data());
+  for (size_t k = 0; k < st.size(); k++)
+    if (ev[k]) evict_slot(s, idx[k]);
+  std::vector<uint64_t> taken;
+  for (size_t i = 0; i < cand.size(); i++) {
+    if (adm[i] == -2) continue;
+    Request &rq = cand[i];
+    int j;
+    if (adm[i] >= 0) {
+      j = idx[adm[i]];
+    } else {
+      if (s->free_slots.empty()) continue;  // all slots in use: stays queued
+      j = s->free_slots.back();
+      pb_grid *g = nullptr;
+      if (pb_grid_create(s->ctx, &rq.desc, true, &g) || pb_ensure_workspace(g, s->mode)) {
+        if (g) pb_grid_release(g);
+        continue;  // device memory short of the model: retry later
+      }
+      s->free_slots.pop_back();
+      if (g->scal) cudaFree(g->scal);
+      g->scal = s->d_scal + j;
+      g->own_scal = false;
+      Slot &sl = s->slots[j];
+      sl.g = g;
+      sl.traj = rq.traj;
+      sl.bytes = rq.bytes;
+      sl.has_solution = false;
+    }
+    Slot &sl = s->slots[j];
+    sl.busy = true;
+    sl.last_used = ++s->clock;
+    sl.warm = s->opts.warm_start && sl.has_solution;
+    if (pb_run_setup(sl.g, (int)rq.q.size(), rq.xyz.data(), rq.q.data(), rq.r.data(), false)) {
+      sl.busy = false;
+      fail_request(s, rq, PB_ERR_CUDA);
+      taken.push_back(rq.ticket);
+      continue;
+    }
+    if (!sl.warm) {  // cold start: phi0 = 0 in both solution buffers
+      cudaMemsetAsync(sl.g->x64, 0, sl.g->n_pad * sizeof(double), s->stream);
+      cudaMemsetAsync(sl.g->x64b, 0, sl.g->n_pad * sizeof(double), s->stream);
+    }
+    sl.req = std::move(rq);
+    taken.push_back(sl.req.ticket);
+    started.push_back(j);
+  }
+  if (!taken.empty()) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::deque<Request> rest;
+    for (auto &r : s->queue)
+      if (std::find(taken.begin(), taken.end(), r.ticket) == taken.end()) rest.push_back(std::move(r));
+    s->queue.swap(rest);
+  }
+  return started;
+}
+
+// Upload the descriptors, work lists and partial offsets of the active grids.
+bool rebuild_batch(pb_server *s, bool *graph_stale) {
+  std::vector<Item> st, ch;
+  std::vector<int> active;
+  for (int j = 0; j < (int)s->slots.size(); j++)
+    if (s->slots[j].g && s->slots[j].busy) active.push_back(j);
+  int st_off = 0, ch_off = 0;
+  for (int j : active) {
+    pb_grid *g = s->slots[j].g;
+    Inst I;
+    if (pb_make_inst(g, &s->opts, s->mode, s->coef, I)) return false;
+    I.s = s->d_scal + j;
+    I.st_base = st_off;
+    I.ch_base = ch_off;
+    for (int t = 0; t < g->n_st; t++) st.push_back(Item{j, t});
+    for (int t = 0; t < g->n_ch; t++) ch.push_back(Item{j, t});
+    st_off += g->n_st;
+    ch_off += g->n_ch;
+    if (!cuda_ok(cudaMemcpyAsync(s->d_inst + j, &I, sizeof(Inst), cudaMemcpyHostToDevice, s->stream),
+                 s, "upload descriptor"))
+      return false;
+    s->ctx->h2d += sizeof(Inst);
+  }
+  const size_t old_st = s->cap_st, old_ch = s->cap_ch;
+  Item *ost = s->d_st, *och = s->d_ch;
+  if (!grow(&s->d_st, &s->cap_st, std::max<size_t>(st.size(), 1)) ||
+      !grow(&s->d_ch, &s->cap_ch, std::max<size_t>(ch.size(), 1))) {
+    s->worker_error = "out of device memory for the work lists";
+    return false;
+  }
+  size_t cst = old_st, cch = old_ch;
+  // partials follow the item capacity
+  if (s->cap_st != old_st || s->d_st != ost) {
+    cudaFree(s->d_st_part);
+    s->d_st_part = nullptr;
+    pb_dalloc((void **)&s->d_st_part, 2 * sizeof(double) * s->cap_st);
+    *graph_stale = true;
+  }
+  if (s->cap_ch != old_ch || s->d_ch != och) {
+    cudaFree(s->d_ch_part);
+    s->d_ch_part = nullptr;
+    pb_dalloc((void **)&s->d_ch_part, 2 * sizeof(double) * s->cap_ch);
+    *graph_stale = true;
+  }
+  (void)cst; (void)cch;
+  if (!s->d_st_part || !s->d_ch_part) {
+    s->worker_error = "out of device memory for the partial sums";
+    return false;
+  }
+  const int counts[2] = {(int)st.size(), (int)ch.size()};
+  if (!st.empty() && !cuda_ok(cudaMemcpyAsync(s->d_st, st.data(), st.size() * sizeof(Item),
+                                              cudaMemcpyHostToDevice, s->stream), s, "items"))
+    return false;
+  if (!ch.empty() && !cuda_ok(cudaMemcpyAsync(s->d_ch, ch.data(), ch.size() * sizeof(Item),
+                                              cudaMemcpyHostToDevice, s->stream), s, "items"))
+    return false;
+  if (!cuda_ok(cudaMemcpyAsync(s->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s->stream),
+               s, "counts"))
+    return false;
+  s->ctx->h2d += (st.size() + ch.size()) * sizeof(Item) + sizeof(counts);
+  // the copies read host vectors that go out of scope: wait for them
+  return cuda_ok(cudaStreamSynchronize(s->stream), s, "upload");
+}
+
+bool run_graph(pb_server *s, bool stale) {
+  if (stale && s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  if (!s->graph) {
+    Batch B;
+    B.inst = s->d_inst;
+    B.st_items = s->d_st;
+    B.ch_items = s->d_ch;
+    B.n_items = s->d_counts;
+    B.st_part = s->d_st_part;
+    B.ch_part = s->d_ch_part;
+    B.error = s->d_err;
+    cudaGraph_t g;
+    if (!cuda_ok(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), s, "capture"))
+      return false;
+    for (int t = 0; t < s->ticks; t++) launch_tick(B, s->mode, s->coef, s->kg, s->stream);
+    if (!cuda_ok(cudaStreamEndCapture(s->stream, &g), s, "capture")) return false;
+    const cudaError_t e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (!cuda_ok(e, s, "instantiate")) return false;
+  }
+  if (!cuda_ok(cudaGraphLaunch(s->graph, s->stream), s, "graph launch")) return false;
+  s->ctx->launches += 2ull * s->ticks;
+  return true;
+}
+
+// Complete the finished solves among the active slots.
+void complete(pb_server *s, const std::vector<int> &fin) {
+  if (fin.empty()) return;
+  std::vector<double> energy(fin.size(), 0.0);
+  for (size_t k = 0; k < fin.size(); k++) {
+    Slot &sl = s->slots[fin[k]];
+    pb_grid *g = sl.g;
+    const Scal &S = s->h_scal[fin[k]];
+    if (S.status == PB_ERR_ARG) continue;
+    const double *x = S.xbuf ? g->x64b : g->x64;
+    const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
+    if (!grow(&s->d_dense, &s->cap_dense, n)) continue;
+    if (S.outer == -1) cudaMemsetAsync(s->d_dense, 0, n * sizeof(double), s->stream);
+    else launch_unpack(x, s->d_dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->stream);
+    launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.h, g->d.origin[0],
+                  g->d.origin[1], g->d.origin[2], s->d_dense, g->scratch + SCR_ENERGY_PART,
+                  g->scratch + SCR_ENERGY, s->stream);
+    cudaMemcpyAsync(&energy[k], g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost,
+                    s->stream);
+    s->ctx->launches += 1 + (g->n_atoms > 0 ? 2 : 1);
+    s->ctx->d2h += sizeof(double);
+    if (sl.req.phi_out) {
+      cudaMemcpyAsync(sl.req.phi_out, s->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost,
+                      s->stream);
+      s->ctx->d2h += n * sizeof(double);
+    }
+  }
+  cudaStreamSynchronize(s->stream);
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (size_t k = 0; k < fin.size(); k++) {
+    Slot &sl = s->slots[fin[k]];
+    const Scal &S = s->h_scal[fin[k]];
+    pb_result r;
+    memset(&r, 0, sizeof(r));
+    r.status = S.status;
+    r.energy = S.status == PB_ERR_ARG ? 0.0 : energy[k];
+    r.info.status = S.status;
+    r.info.iterations = S.total_iter;
+    r.info.outer_steps = S.outer < 0 ? 0 : S.outer;
+    r.info.relres = S.relres;
+    r.info.relres_true = S.outer == -1 ? 0.0 : S.relres_true;
+    r.seconds = since(sl.req.t_submit);
+    r.warm_started = sl.warm ? 1 : 0;
+    s->done[sl.req.ticket] = r;
+    s->completed++;
+    sl.busy = false;
+    sl.has_solution = S.status == PB_OK;
+    sl.last_used = ++s->clock;
+    sl.req = Request();
+  }
+  s->cv_done.notify_all();
+}
+
+void worker_main(pb_server *s) {
+  cudaSetDevice(s->ctx->device);
+  bool active_changed = true, graph_stale = true;
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      const bool any_busy = std::any_of(s->slots.begin(), s->slots.end(),
+                                        [](const Slot &x) { return x.g && x.busy; });
+      if (!any_busy && s->queue.empty())
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                            [&] { return s->stop || !s->queue.empty(); });
+      if (s->stop) break;
+    }
+    const std::vector<int> started = admit(s);
+    if (!started.empty()) active_changed = true;
+    if (active_changed) {
+      // descriptors first: the start kernel reads each grid's error word and
+      // ||b||^2 through its descriptor
+      if (!rebuild_batch(s, &graph_stale)) break;
+      if (!started.empty()) {
+        cudaMemcpyAsync(s->d_list, started.data(), started.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, s->stream);
+        launch_start(s->d_inst, s->d_list, (int)started.size(), s->stream);
+        s->ctx->launches += 1;
+      }
+      active_changed = false;
+    }
+    std::vector<int> active;
+    for (int j = 0; j < (int)s->slots.size(); j++)
+      if (s->slots[j].g && s->slots[j].busy) active.push_back(j);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->n_active = (int)active.size();
+      s->n_resident = 0;
+      s->bytes_resident = 0;
+      for (auto &x : s->slots)
+        if (x.g) { s->n_resident++; s->bytes_resident += x.bytes; }
+    }
+    if (active.empty()) continue;
+    if (!run_graph(s, graph_stale)) break;
+    graph_stale = false;
+    const int hi = *std::max_element(active.begin(), active.end()) + 1;
+    cudaMemcpyAsync(s->h_scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
+    s->ctx->d2h += hi * sizeof(Scal);
+    if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "tick")) break;
+    std::vector<int> fin;
+    for (int j : active)
+      if (s->h_scal[j].phase == PH_DONE) fin.push_back(j);
+    if (!fin.empty()) {
+      complete(s, fin);
+      active_changed = true;
+    }
+  }
+  // fail what is left
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto &rq : s->queue) {
+    pb_result r;
+    memset(&r, 0, sizeof(r));
+    r.status = r.info.status = s->stop ? PB_ERR_BUSY : PB_ERR_CUDA;
+    s->done[rq.ticket] = r;
+  }
+  s->queue.clear();
+  for (auto &sl : s->slots)
+    if (sl.g && sl.busy) {
+      pb_result r;
+      memset(&r, 0, sizeof(r));
+      r.status = r.info.status = s->stop ? PB_ERR_BUSY : PB_ERR_CUDA;
+      s->done[sl.req.ticket] = r;
+      sl.busy = false;
+    }
+  s->stop = true;
+  s->cv_done.notify_all();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve_opts *opts,
+                                      pb_server **out) {
+  if (!ctx || !out) return pb_fail(PB_ERR_ARG, "pb_server_create: NULL argument");
+  *out = nullptr;
+  pb_solve_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    memset(&o, 0, sizeof(o));
+    o.precond = PB_PRECOND_JACOBI;
+    o.precision = PB_PREC_F32_REFINE;
+    o.rel_tol = 1e-6;
+    o.max_iter = 100000;
+    o.inner_tol = 1e-3;
+    o.max_outer = 20;
+    o.warm_start = 1;
+  }
+  if (o.precision < PB_PREC_F64 || o.precision > PB_PREC_F32_REFINE || !(o.rel_tol > 0) ||
+      (o.precision == PB_PREC_F32_REFINE && (!(o.inner_tol > 0) || o.max_outer < 1)))
+    return pb_fail(PB_ERR_ARG, "pb_server_create: bad solve options");
+  if (o.precision != PB_PREC_F32_REFINE) o.max_outer = 1;
+  if (o.max_iter <= 0) o.max_iter = 100000;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return pb_fail(PB_ERR_CUDA, "cudaSetDevice");
+  pb_server *s = new pb_server();
+  s->ctx = ctx;
+  s->budget = budget;
+  s->opts = o;
+  s->mode = o.precision == PB_PREC_F64 ? MODE_F64 : o.precision == PB_PREC_F32 ? MODE_F32
+                                                                                : MODE_F32_REFINE;
+  s->coef = COEF_PACKED;
+  s->kg = kernel_grid(s->mode, s->coef, ctx->num_sms);
+  s->slots.resize(MAX_SLOTS);
+  for (int j = MAX_SLOTS - 1; j >= 0; j--) s->free_slots.push_back(j);
+  bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && !pb_dalloc((void **)&s->d_scal, MAX_SLOTS * sizeof(Scal));
+  ok = ok && !pb_dalloc((void **)&s->d_inst, MAX_SLOTS * sizeof(Inst));
+  ok = ok && !pb_dalloc((void **)&s->d_counts, 2 * sizeof(int));
+  ok = ok && !pb_dalloc((void **)&s->d_list, MAX_SLOTS * sizeof(int));
+  ok = ok && !pb_dalloc((void **)&s->d_err, 4 * sizeof(int));
+  ok = ok && cudaMallocHost((void **)&s->h_scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
+  ok = ok && cudaMemset(s->d_scal, 0, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
+  ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    pb_server_destroy(s);
+    return pb_fail(PB_ERR_OOM, "pb_server_create: device allocation failed");
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return PB_OK;
+}
+
+extern "C" pb_status pb_server_destroy(pb_server *s) {
+  if (!s) return PB_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->ctx->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (int j = 0; j < (int)s->slots.size(); j++)
+    if (s->slots[j].g) {
+      s->slots[j].g->scal = nullptr;
+      pb_grid_release(s->slots[j].g);
+      s->slots[j].g = nullptr;
+    }
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  void *ptrs[] = {s->d_scal, s->d_inst, s->d_counts, s->d_list, s->d_err, s->d_st, s->d_ch,
+                  s->d_st_part, s->d_ch_part, s->d_dense};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (s->h_scal) cudaFreeHost(s->h_scal);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return PB_OK;
+}
+
+extern "C" pb_status pb_batch_submit(pb_server *s, const pb_request *req, uint64_t *ticket) {
+  if (!s || !req || !ticket) return pb_fail(PB_ERR_ARG, "pb_batch_submit: NULL argument");
+  pb_status st = pb_check_desc(&req->desc);
+  if (st) return st;
+  if ((st = pb_check_atoms(req->n_atoms, req->xyz, req->q, req->radius))) return st;
+  Request rq;
+  rq.traj = req->trajectory_id < 0 ? -1 : req->trajectory_id;
+  rq.desc = req->desc;
+  rq.desc.coef = PB_COEF_PACKED;
+  rq.xyz.assign(req->xyz, req->xyz + 3 * (size_t)req->n_atoms);
+  rq.q.assign(req->q, req->q + req->n_atoms);
+  rq.r.assign(req->radius, req->radius + req->n_atoms);
+  rq.phi_out = req->phi_out;
+  rq.t_submit = std::chrono::steady_clock::now();
+  rq.bytes = pb_grid_bytes(&rq.desc, s->opts.precision);
+  if (rq.bytes > s->budget) return pb_fail(PB_ERR_ARG, "request larger than the memory budget");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return pb_fail(PB_ERR_BUSY, "server stopped: " + s->worker_error);
+  if (s->queue.size() >= MAX_QUEUE) return pb_fail(PB_ERR_BUSY, "queue full");
+  rq.ticket = s->next_ticket++;
+  *ticket = rq.ticket;
+  s->outstanding.insert(rq.ticket);
+  s->queue.push_back(std::move(rq));
+  s->cv_work.notify_all();
+  return PB_OK;
+}
+
+extern "C" pb_status pb_batch_poll(pb_server *s, uint64_t ticket, int timeout_ms, pb_result *res) {
+  if (!s || !res) return pb_fail(PB_ERR_ARG, "pb_batch_poll: NULL argument");
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (!s->outstanding.count(ticket)) return pb_fail(PB_ERR_NOT_FOUND, "unknown or returned ticket");
+  auto ready = [&] { return s->done.count(ticket) > 0; };
+  if (!ready()) {
+    if (timeout_ms == 0) return pb_fail(PB_ERR_TIMEOUT, "not ready");
+    if (timeout_ms < 0) s->cv_done.wait(lk, [&] { return ready() || s->stop; });
+    else
+      s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                          [&] { return ready() || s->stop; });
+    if (!ready()) {
+      if (s->stop) return pb_fail(PB_ERR_CUDA, "server stopped: " + s->worker_error);
+      return pb_fail(PB_ERR_TIMEOUT, "not ready");
+    }
+  }
+  *res = s->done[ticket];
+  s->done.erase(ticket);
+  s->outstanding.erase(ticket);
+  return res->status == PB_OK ? PB_OK : res->status;
+}
+
+extern "C" pb_status pb_server_stats(pb_server *s, int *queued, int *active, int *resident,
+                                     size_t *bytes, uint64_t *completed) {
+  if (!s) return pb_fail(PB_ERR_ARG, "pb_server_stats: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (queued) *queued = (int)s->queue.size();
+  if (active) *active = s->n_active;
+  if (resident) *resident = s->n_resident;
+  if (bytes) *bytes = s->bytes_resident;
+  if (completed) *completed = s->completed;
+  return PB_OK;
+}

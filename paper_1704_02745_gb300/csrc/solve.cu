@@ -214,6 +214,11 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
   const HaloG Hh = halo_g(I);
   const int W = I.W, H = I.H, RW = W + 2 * NV, CW = I.cw, RGW = W + 2 * NV;
   const int ring_plane = RGW * (H + 2);
+  // descriptor fields used in the plane loop, held in registers (the asm
+  // statements of the pipeline clobber memory, which would force reloads)
+  const uint32_t stage_bytes = I.stage_bytes, off_p = I.off_p, off_c = I.off_c, off_x = I.off_x;
+  const uint32_t tma_bytes = I.tma_bytes;
+  const int nzg = I.nz;
   const int cx0 = ((G.x0 - 1) >> 4) << 4;  // code box start: 16-byte aligned, <= x0 - 1
   const int Q = (G.z1 - G.z0) + 2;         // planes z0-1 .. z1
   const bool first = S.phase == PH_START;
@@ -230,13 +235,13 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
 
   // thread 0 issues plane z0-1+q into stage st
   auto issue = [&](int q, uint32_t st) {
-    uint8_t *sb = stages + st * (uint32_t)I.stage_bytes;
+    uint8_t *sb = stages + st * stage_bytes;
     const int z = G.z0 - 1 + q;
-    mbar_expect_tx(&full[st], (uint32_t)I.tma_bytes);
+    mbar_expect_tx(&full[st], tma_bytes);
     tma_load_3d(sb, &I.tm_r, &full[st], G.x0 - NV, G.y0 - 1, z);
-    tma_load_3d(sb + I.off_p, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
-    tma_load_3d(sb + I.off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
-    tma_load_3d(sb + I.off_x, m_x, &full[st], G.x0, G.y0, z);
+    tma_load_3d(sb + off_p, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
+    tma_load_3d(sb + off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
+    tma_load_3d(sb + off_x, m_x, &full[st], G.x0, G.y0, z);
   };
   if (threadIdx.x == 0) {
     uint32_t st = SR.st;
@@ -269,14 +274,14 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
     const bool ok = mbar_wait(&full[st], (SR.phase >> st) & 1u);
     SR.phase ^= 1u << st;
     SR.st = st + 1 == NS ? 0 : st + 1;
-    const uint8_t *sb = stages + st * (uint32_t)I.stage_bytes;
+    const uint8_t *sb = stages + st * stage_bytes;
     const T *sr = (const T *)sb;
-    const T *sp = (const T *)(sb + I.off_p);
-    const uint8_t *sc = sb + I.off_c;
-    const T *sx = (const T *)(sb + I.off_x);
+    const T *sp = (const T *)(sb + off_p);
+    const uint8_t *sc = sb + off_c;
+    const T *sx = (const T *)(sb + off_x);
     T *rg = ring + rq * ring_plane;
     const int z = G.z0 - 1 + q;
-    const bool zin = z >= 0 && z < I.nz;
+    const bool zin = z >= 0 && z < nzg;
     Vec<T> pn = {}, po = {}, xv = {};
     uint32_t codes = 0;
     if (ok && G.in_tile) {
@@ -522,7 +527,7 @@ __device__ void fin_update(const Inst &I, Scal *S, double rz, double rr) {
 __device__ void fin_resid(const Inst &I, Scal *S, double rr64, double rz) {
   S->cnt2 = 0;
   S->xbuf ^= 1;  // the new solution now sits in the other x buffer
-  const double rel = sqrt(rr64) / I.bnorm;
+  const double rel = sqrt(rr64) / S->bnorm;
   S->relres_true = rel;
   if (!isfinite(rel)) {
     S->status = 6;
@@ -548,7 +553,7 @@ __device__ void fin_resid(const Inst &I, Scal *S, double rr64, double rz) {
   S->alpha = 0.0;
   S->beta = 0.0;
   S->rz_old = rz;
-  S->ref_norm = I.mode == MODE_F32_REFINE ? sqrt(rr64) : I.bnorm;
+  S->ref_norm = I.mode == MODE_F32_REFINE ? sqrt(rr64) : S->bnorm;
   S->relres = I.mode == MODE_F32_REFINE ? 1.0 : rel;
   S->phase = PH_START;
 }
@@ -609,7 +614,8 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
   __syncthreads();
   StageRing SR{0u, 0u};
   bool abort = false;
-  for (int it = blockIdx.x; it < B.n_st_items; it += gridDim.x) {
+  const int n_items = B.n_items[0];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const Item item = B.st_items[it];
     const Inst &I = B.inst[item.inst];
     Scal *Sp = I.s;
@@ -669,7 +675,8 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
   pdl_launch_dependents();
   pdl_wait();
   __syncthreads();
-  for (int it = blockIdx.x; it < B.n_ch_items; it += gridDim.x) {
+  const int n_items = B.n_items[1];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const Item item = B.ch_items[it];
     const Inst &I = B.inst[item.inst];
     Scal *Sp = I.s;
@@ -745,6 +752,42 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Start a solve on each listed instance from the state its setup left on the
+// device (no host round trip): an atom outside the grid ends the solve with
+// PB_ERR_ARG; b = 0 ends it at once (the solution is phi = 0); otherwise
+// the FP64 residual pass comes next, from the instance's current x (warm
+// start) or from zero.
+__global__ void k_start(const Inst *inst, const int *list, int n, int cold) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const Inst &I = inst[list[t]];
+  Scal *S = I.s;
+  const int xbuf = S->xbuf;
+  Scal z = {};
+  z.xbuf = xbuf;
+  z.ref_norm = 1.0;
+  z.rz_old = 1.0;
+  z.bnorm = sqrt(*I.bnorm2);
+  if (*I.err) {
+    z.status = 1;  // PB_ERR_ARG
+    z.phase = PH_DONE;
+  } else if (z.bnorm == 0.0) {
+    z.phase = PH_DONE;
+    z.outer = -1;  // marks "phi = 0"
+  } else {
+    z.phase = PH_RESID;
+  }
+  *S = z;
+  (void)cold;
+}
+
+cudaError_t launch_start(const Inst *inst, const int *list, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_start<<<(n + 127) / 128, 128, 0, st>>>(inst, list, n, 0);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

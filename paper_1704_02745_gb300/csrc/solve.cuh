@@ -58,6 +58,8 @@ cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg
 cudaError_t launch_phase(const Batch &B, int mode, int coef, const KernelGrid &kg, int which,
                          cudaStream_t st);
 KernelGrid kernel_grid(int mode, int coef, int num_sms);
+// Start solves on the listed instances from their device-side setup state.
+cudaError_t launch_start(const Inst *inst, const int *list, int n, cudaStream_t st);
 
 // ops.cu
 cudaError_t launch_pack(const double *dense, double *padded, int nx, int ny, int nz, int px,

@@ -70,6 +70,23 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("trajectory_id", ctypes.c_int64), ("desc", GridDesc), ("n_atoms", ctypes.c_int),
+                ("xyz", ctypes.c_void_p), ("q", ctypes.c_void_p), ("radius", ctypes.c_void_p),
+                ("phi_out", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("energy", ctypes.c_double), ("info", SolveInfo),
+                ("seconds", ctypes.c_double), ("warm_started", ctypes.c_int)]
+
+
+class SlotState(ctypes.Structure):
+    _fields_ = [("trajectory_id", ctypes.c_int64), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("bytes", ctypes.c_size_t), ("busy", ctypes.c_int),
+                ("last_used", ctypes.c_uint64)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 
@@ -98,9 +115,19 @@ def load(path: str = LIB_PATH):
     lib.pb_grid_export.argtypes = [_P, ctypes.c_int, _P, ctypes.c_size_t]
     lib.pb_grid_bytes.restype = ctypes.c_size_t
     lib.pb_grid_bytes.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int]
+    lib.pb_server_create.argtypes = [_P, ctypes.c_size_t, ctypes.POINTER(SolveOpts), ctypes.POINTER(_P)]
+    lib.pb_server_destroy.argtypes = [_P]
+    lib.pb_batch_submit.argtypes = [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.pb_batch_poll.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result)]
+    lib.pb_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
+                                    ctypes.POINTER(ctypes.c_uint64)]
+    lib.pb_plan_admission.restype = ctypes.c_int
+    lib.pb_plan_admission.argtypes = [ctypes.c_size_t, ctypes.POINTER(SlotState), ctypes.c_int,
+                                      _P, _P, _P, ctypes.c_int, _P, _P]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype if name in (
-            "pb_last_error", "pb_grid_bytes") else ctypes.c_int
+            "pb_last_error", "pb_grid_bytes", "pb_plan_admission") else ctypes.c_int
     _lib = lib
     return lib
 
@@ -278,3 +305,109 @@ class Grid:
 
     def energy(self, phi) -> float:
         return pb_energy(self.handle, phi)
+
+
+# --- continuous-batching server ---------------------------------------------
+
+def pb_server_create(ctx: int, budget_bytes: int, opts: Optional[SolveOpts] = None) -> int:
+    h = _P()
+    _check(load().pb_server_create(_P(ctx), budget_bytes, ctypes.byref(opts) if opts else None,
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def pb_server_destroy(server: int):
+    _check(load().pb_server_destroy(_P(server)))
+
+
+def pb_batch_submit(server: int, trajectory_id: int, spec, atoms, phi_out: Optional[np.ndarray] = None):
+    """Queue one snapshot; returns (ticket, keepalive) -- keep `keepalive` (the
+    output buffer) alive until the result is polled."""
+    r = Request()
+    r.trajectory_id = trajectory_id
+    r.desc = grid_desc(spec)
+    xyz = np.ascontiguousarray(atoms.xyz, dtype=np.float64)
+    q = np.ascontiguousarray(atoms.q, dtype=np.float64)
+    rad = np.ascontiguousarray(atoms.r, dtype=np.float64)
+    r.n_atoms = int(q.shape[0])
+    r.xyz, r.q, r.radius = xyz.ctypes.data, q.ctypes.data, rad.ctypes.data
+    r.phi_out = phi_out.ctypes.data if phi_out is not None else None
+    t = ctypes.c_uint64(0)
+    _check(load().pb_batch_submit(_P(server), ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def pb_batch_poll(server: int, ticket: int, timeout_ms: int = -1, check: bool = False):
+    """(status, Result).  Status PB_ERR_TIMEOUT when not ready."""
+    res = Result()
+    st = load().pb_batch_poll(_P(server), ticket, timeout_ms, ctypes.byref(res))
+    if check:
+        _check(st)
+    return st, res
+
+
+def pb_server_stats(server: int):
+    q, a, r = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    b, c = ctypes.c_size_t(0), ctypes.c_uint64(0)
+    _check(load().pb_server_stats(_P(server), ctypes.byref(q), ctypes.byref(a), ctypes.byref(r),
+                                  ctypes.byref(b), ctypes.byref(c)))
+    return {"queued": q.value, "active": a.value, "resident": r.value, "bytes": b.value,
+            "completed": c.value}
+
+
+def pb_plan_admission(budget: int, slots, reqs):
+    """slots: list of dicts (trajectory_id, dims, bytes, busy, last_used);
+    reqs: list of (trajectory_id, dims, bytes).  Returns (admit, evict)."""
+    ns, nr = len(slots), len(reqs)
+    arr = (SlotState * max(ns, 1))()
+    for j, sl in enumerate(slots):
+        arr[j].trajectory_id = sl["trajectory_id"]
+        arr[j].nx, arr[j].ny, arr[j].nz = sl["dims"]
+        arr[j].bytes = sl["bytes"]
+        arr[j].busy = 1 if sl["busy"] else 0
+        arr[j].last_used = sl["last_used"]
+    traj = np.array([r[0] for r in reqs] or [0], dtype=np.int64)
+    dims = np.array([d for r in reqs for d in r[1]] or [0, 0, 0], dtype=np.int32)
+    nbytes = np.array([r[2] for r in reqs] or [0], dtype=np.uint64)
+    admit = np.zeros(max(nr, 1), dtype=np.int32)
+    evict = np.zeros(max(ns, 1), dtype=np.int32)
+    load().pb_plan_admission(budget, arr, ns, traj.ctypes.data, dims.ctypes.data, nbytes.ctypes.data,
+                             nr, admit.ctypes.data, evict.ctypes.data)
+    return admit[:nr].tolist(), evict[:ns].tolist()
+
+
+class Server:
+    """pb_server_create / pb_server_destroy around submit and poll."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, **opts):
+        o = solve_opts(**{"precision": "f32_refine", "tol": 1e-6, "inner_tol": 1e-3,
+                          "warm_start": True, **opts})
+        self.handle = pb_server_create(ctx.handle, int(budget_bytes), o)
+        self._keep = {}
+
+    def submit(self, trajectory_id: int, spec, atoms, want_phi: bool = False) -> int:
+        out = np.empty(spec.shape, dtype=np.float64) if want_phi else None
+        t = pb_batch_submit(self.handle, trajectory_id, spec, atoms, out)
+        self._keep[t] = out
+        return t
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        st, res = pb_batch_poll(self.handle, ticket, timeout_ms)
+        if st == PB_ERR_TIMEOUT:
+            return None
+        phi = self._keep.pop(ticket, None)
+        return res, phi
+
+    def stats(self):
+        return pb_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            pb_server_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
