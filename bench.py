@@ -1,13 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the FDPB Jacobi-PCG hot path on GB300.
 
-One step = one MD-like snapshot of the workload: grid setup on the device
-(dielectric map, charges, Debye-Hueckel boundary), the FP32 + FP64-refined
-Jacobi-PCG solve to a 1e-6 true relative residual, and the energy read back to
-the host.  Prints one JSON line (rank 0).  Multi-GPU runs are independent
-replicas (each rank solves its own snapshots; no collective on the data path).
+Default workload ("serving"): 16 MD-like trajectories (300-8,000 atoms, grids
+33^3-193^3 at fill ratio 1.5, snapshots a 0.2 A random walk).  One step = a
+batch of 64 snapshot requests submitted at once to the continuous-batching
+server (grid setup, FP32 Jacobi-PCG with FP64 iterative refinement to a 1e-6
+true relative residual, warm start along each trajectory, energy back to the
+host).  The same requests are also solved one at a time with plain FP64 PCG,
+and a Poisson request stream at 0.8x the measured plain-FP64 capacity gives
+p50/p99 latency for both.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload globule129]
+Single-grid workloads (globule33/129/257): one step = one snapshot solved with
+pb_pcg_solve (setup, FP32 + FP64 refinement to 1e-6, energy).
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (each
+rank solves its own requests; no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload serving]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 """
 from __future__ import annotations
@@ -29,7 +38,9 @@ import numpy as np  # noqa: E402
 from paper_1704_02745_gb300 import inputs  # noqa: E402
 
 METRIC = "solves/s, p50/p99 @1e-6 rel resid: served FP32+refine vs plain FP64 PCG"
+SERVING = "serving"
 WORKLOADS = {
+    SERVING: None,
     "globule33": inputs.small_33,
     "globule129": inputs.globule_129,
     "globule257": inputs.globule_257,
@@ -154,6 +165,249 @@ def run_loop(g, phi, snaps, steps, warmup, stream, flush, solve_kw, ctx=None, ma
         torch.cuda.synchronize()
         marks.append(ctx.stats())
     return dev_ms, wall_ms, iters, energies
+
+
+# --------------------------------------------------------------------------- serving
+
+class Stream:
+    """Snapshot requests of the serving workload: request i is the next
+    snapshot of a random trajectory (seeded)."""
+
+    def __init__(self, seed=5, n_traj=16, sigma=0.2, req_seed=99):
+        self.trajs = inputs.trajectories(seed=seed, count=n_traj, sigma=sigma)
+        self.rng = np.random.default_rng([seed, req_seed])
+        self.cur = [t.base.copy() for t in self.trajs]
+        self.walk = [np.random.default_rng([seed, 1000 + k]) for k in range(n_traj)]
+
+    def next(self):
+        k = int(self.rng.integers(0, len(self.trajs)))
+        a = self.cur[k].copy()
+        a.xyz = a.xyz + self.walk[k].normal(0.0, self.trajs[k].sigma, a.xyz.shape)
+        self.cur[k] = a
+        return k, self.trajs[k].grid, a
+
+    def take(self, n):
+        return [self.next() for _ in range(n)]
+
+
+def serve_batch(srv, reqs, want_phi=False):
+    """Submit all requests, wait for all; (wall seconds, latencies s, results)."""
+    t0 = time.perf_counter()
+    tickets = [srv.submit(k, g, a, want_phi=want_phi) for k, g, a in reqs]
+    res = []
+    for t in tickets:
+        r, _ = srv.poll(t, 600000)
+        res.append(r)
+    return time.perf_counter() - t0, [r.seconds for r in res], res
+
+
+class PlainFP64:
+    """One request at a time: per-trajectory grid, setup, FP64 Jacobi-PCG from
+    phi0 = 0, energy (pb_pcg_solve)."""
+
+    def __init__(self, pb, ctx, torch):
+        self.pb, self.ctx, self.torch = pb, ctx, torch
+        self.grids, self.phis = {}, {}
+
+    def solve(self, k, g, a, tol):
+        if k not in self.grids:
+            self.grids[k] = self.pb.Grid(self.ctx, g.replace(dh="f32"), a)
+            self.phis[k] = self.torch.zeros(g.shape, dtype=self.torch.float64, device="cuda")
+        else:
+            self.grids[k].update_atoms(a)
+        info = self.grids[k].solve(self.phis[k], precision="f64", tol=tol)
+        return self.grids[k].energy(self.phis[k]), info
+
+    def close(self):
+        for gr in self.grids.values():
+            gr.close()
+
+
+def poisson_run(submit_fn, reqs, rate, seed=17):
+    """Open-loop stream: request i arrives at its Poisson time; returns
+    (makespan s, latencies s = completion - arrival)."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    arrivals -= arrivals[0]
+    return submit_fn(reqs, arrivals)
+
+
+def run_serving(args):
+    import torch
+    from paper_1704_02745_gb300 import pb
+    from paper_1704_02745_gb300 import build as pbbuild
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    pbbuild.build()
+    torch.cuda.set_device(local)
+    stream = Stream(seed=5, req_seed=99 + 1000 * rank)
+    per_step = args.batch
+    ctx = pb.Context(local)
+    budget = int(args.budget_gb * (1 << 30))
+    srv = pb.Server(ctx, budget, precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol,
+                    warm_start=True)
+    # warm-up steps, then the timed steps
+    for _ in range(args.warmup):
+        serve_batch(srv, [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)])
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    walls, lats, iters = [], [], []
+    for _ in range(args.steps):
+        reqs = [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
+        w, l, res = serve_batch(srv, reqs)
+        walls.append(w)
+        lats += l
+        iters += [r.info.iterations for r in res]
+        bad = [r.status for r in res if r.status != 0]
+        if bad:
+            raise RuntimeError(f"served requests failed: {bad[:5]}")
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    st1 = ctx.stats()
+    total = sum(walls)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t[0])
+    # end to end: the same steps with phi copied back to the host per request
+    e2e_walls, e2e0 = [], ctx.stats()
+    for _ in range(max(1, args.steps // 2)):
+        reqs = [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
+        w, _, _ = serve_batch(srv, reqs, want_phi=True)
+        e2e_walls.append(w)
+    e2e1 = ctx.stats()
+    e2e_steps = len(e2e_walls)
+    # plain FP64, one at a time, on the same kind of requests (fresh trajectories)
+    plain = PlainFP64(pb, ctx, torch)
+    pstream = Stream(seed=5, req_seed=98 + 1000 * rank)
+    p_lat = []
+    plain.solve(*pstream.next(), args.tol)  # warm-up
+    t0 = time.perf_counter()
+    n_plain = max(8, per_step // 2)
+    for _ in range(n_plain):
+        t1 = time.perf_counter()
+        plain.solve(*pstream.next(), args.tol)
+        p_lat.append(time.perf_counter() - t1)
+    plain_rate = n_plain / (time.perf_counter() - t0)
+    # Poisson stream at 0.8x the plain-FP64 capacity, both arms
+    rate = 0.8 * plain_rate
+    n_pois = args.stream_requests
+
+    def served_stream_lat(reqs, arrivals):
+        t_start = time.perf_counter()
+        tickets = []
+        for (k, g, a), ta in zip(reqs, arrivals):
+            d = t_start + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(k, g.replace(dh="f32"), a))
+        lat = []
+        for t in tickets:
+            r, _ = srv.poll(t, 600000)
+            lat.append(r.seconds)
+        return time.perf_counter() - t_start, lat
+
+    def plain_stream(reqs, arrivals):
+        t_start = time.perf_counter()
+        lat = []
+        for (k, g, a), ta in zip(reqs, arrivals):
+            now = time.perf_counter() - t_start
+            if now < ta:
+                time.sleep(ta - now)
+            plain.solve(k, g, a, args.tol)
+            lat.append(time.perf_counter() - t_start - ta)  # queueing + service
+        return time.perf_counter() - t_start, lat
+
+    s_make, s_lat = poisson_run(served_stream_lat, Stream(seed=5, req_seed=77 + rank).take(n_pois), rate)
+    p_make, p_lat_stream = poisson_run(plain_stream, Stream(seed=5, req_seed=77 + rank).take(n_pois),
+                                       rate)
+    plain.close()
+    # per-kernel device time of one 129^3 solve (kernels launched one by one between events)
+    prob = inputs.globule_129()
+    spec = prob.grid.replace(dh="f32")
+    with pb.Grid(ctx, spec, prob.atoms) as g:
+        phi = torch.zeros(spec.shape, dtype=torch.float64, device="cuda")
+        g.solve(phi, precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol)
+        prof = g.solve(phi, precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol,
+                       profile=True)
+    srv.close()
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    n_req = args.steps * per_step
+    hbm, peak_kind = peaks()
+    n129 = spec.n
+    t_st = prof.ms_stencil / max(prof.n_stencil, 1) / 1e3
+    t_up = prof.ms_update / max(prof.n_update, 1) / 1e3
+    ach_st = BYTES_PER_NODE["stencil"] * n129 / t_st / 1e9
+    ach_up = BYTES_PER_NODE["update"] * n129 / t_up / 1e9
+    trf = NCU_TRAFFIC_PER_NODE["stencil"]
+    out = {
+        "metric": METRIC,
+        "value": world * n_req / total,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "serving stream: 16 trajectories, 300-8000 atoms, grids 33^3-193^3",
+                   "requests_per_step": per_step, "tol": args.tol,
+                   "solver": "continuous-batching FP32 Jacobi-PCG + FP64 refinement, warm start",
+                   "inner_tol": args.inner_tol, "budget_gb": args.budget_gb,
+                   "debye_hueckel_sum": "f32", "snapshot_sigma_A": 0.2,
+                   "l2": "inputs larger than L2 (2.1 M nodes mean per request, 64 per step)",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": pct([1e3 * x for x in lats], 50), "p99": pct([1e3 * x for x in lats], 99),
+                       "note": "closed loop: 64 requests submitted at once, submit -> result"},
+        "iterations_mean": float(np.mean(iters)),
+        "fp64_plain": {"value": plain_rate, "unit": "solves/s",
+                       "latency_ms": {"p50": pct([1e3 * x for x in p_lat], 50),
+                                      "p99": pct([1e3 * x for x in p_lat], 99)},
+                       "requests": n_plain, "note": "one at a time, phi0 = 0"},
+        "poisson_stream": {"rate_per_s": rate, "requests": n_pois,
+                           "served": {"solves_per_s": n_pois / s_make,
+                                      "p50_ms": pct([1e3 * x for x in s_lat], 50),
+                                      "p99_ms": pct([1e3 * x for x in s_lat], 99)},
+                           "fp64_plain": {"solves_per_s": n_pois / p_make,
+                                          "p50_ms": pct([1e3 * x for x in p_lat_stream], 50),
+                                          "p99_ms": pct([1e3 * x for x in p_lat_stream], 99)}},
+        "roofline": {"bound": "hbm", "kernel": "k_stencil<float,packed> (CG stencil pass), 129^3 grid",
+                     "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
+                     "peak_kind": peak_kind,
+                     "traffic": None if trf is None else trf * n129,
+                     "bytes_per_node": BYTES_PER_NODE["stencil"], "launch_ms": t_st * 1e3,
+                     "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
+                                     "bytes_per_node": BYTES_PER_NODE["update"],
+                                     "launch_ms": t_up * 1e3}},
+        "e2e": {"value": world * e2e_steps * per_step / sum(e2e_walls), "unit": "solves/s",
+                "h2d_bytes_per_step": int((e2e1[1] - e2e0[1]) / e2e_steps),
+                "d2h_bytes_per_step": int((e2e1[2] - e2e0[2]) / e2e_steps),
+                "note": "same steps with phi copied to host memory per request"},
+        "gpu_launches": int(st1[0] - st0[0]),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        k, g, a = Stream(seed=5, req_seed=99).next()
+        out["cpu_baseline"] = cpu_baseline(inputs.Problem("serving-request", g, a), a,
+                                           float(np.mean(iters)), args)
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_ours(args):
@@ -317,18 +571,26 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    problem = WORKLOADS[args.workload]()
-    snaps = snapshots(problem, 8, seed=100)
+    if args.workload == SERVING:
+        reqs = Stream(seed=5, req_seed=99).take(8)
+        problem = inputs.Problem("serving-request", reqs[0][1], reqs[0][2])
+        snaps = [a for _, _, a in reqs]
+        mixed = [inputs.Problem("serving-request", g, a) for _, g, a in reqs]
+    else:
+        problem = WORKLOADS[args.workload]()
+        snaps = snapshots(problem, 8, seed=100)
+        mixed = None
     # calibrate the full iteration count once (untimed)
     s = oracle.setup(problem.grid, snaps[0])
     full = oracle.pcg(s, tol=args.tol, max_iter=args.cpu_sample_iters if problem.grid.n > 5e6 else 100000)
     full_iters = full.iters
     times = []
     for i in range(args.warmup + args.steps):
-        t_fixed, t_iter, _ = oracle_solve_sample(problem, snaps[i % len(snaps)], args.tol,
-                                                 args.cpu_sample_iters)
+        pr = mixed[i % len(mixed)] if mixed else problem
+        t_fixed, t_iter, _ = oracle_solve_sample(pr, pr.atoms if mixed else snaps[i % len(snaps)],
+                                                 args.tol, args.cpu_sample_iters)
         if i >= args.warmup:
-            times.append(t_fixed + t_iter * full_iters)
+            times.append(t_fixed + t_iter * full_iters * (pr.grid.n / problem.grid.n) ** (1 / 3))
     total = sum(times)
     val = args.steps / total
     print(json.dumps({
@@ -336,8 +598,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": problem.name, "grid": f"{problem.grid.nx}^3",
-                   "atoms": problem.atoms.n, "tol": args.tol, "solver": "oracle FP64 Jacobi-PCG"},
+        "config": {"workload": (SERVING if mixed else problem.name), "tol": args.tol,
+                   "solver": "oracle FP64 Jacobi-PCG"},
         "latency_ms": {"p50": pct([t * 1e3 for t in times], 50),
                        "p99": pct([t * 1e3 for t in times], 99)},
         "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -355,7 +617,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="globule129", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=SERVING, choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=64, help="serving: requests per step")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device-memory budget")
+    ap.add_argument("--stream-requests", type=int, default=200,
+                    help="serving: requests of the Poisson stream (each arm)")
     ap.add_argument("--coef", default="packed", choices=["packed", "f32", "bf16"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
@@ -370,6 +636,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == SERVING:
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -98,9 +98,9 @@ extern "C" pb_status pb_destroy(pb_ctx *c) {
 
 extern "C" pb_status pb_ctx_stats(pb_ctx *c, uint64_t *launches, uint64_t *h2d, uint64_t *d2h) {
   if (!c) return pb_fail(PB_ERR_ARG, "pb_ctx_stats: NULL ctx");
-  if (launches) *launches = c->launches;
-  if (h2d) *h2d = c->h2d;
-  if (d2h) *d2h = c->d2h;
+  if (launches) *launches = c->launches.load();
+  if (h2d) *h2d = c->h2d.load();
+  if (d2h) *d2h = c->d2h.load();
   return PB_OK;
 }
 
@@ -249,13 +249,13 @@ pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double 
   else if (desc->coef != PB_COEF_PACKED)
     CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, desc->coef, g->ex, g->ey,
                      g->ez, g->diag, s));
-  g->ctx->launches += 5 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
-  g->ctx->h2d += 2 * (unsigned long long)n_atoms * sizeof(dbl4);
+  g->ctx->stats->launches += 5 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
+  g->ctx->stats->h2d += 2 * (unsigned long long)n_atoms * sizeof(dbl4);
   if (!sync) return PB_OK;  // the error word and ||b||^2 stay on the device
   int *hbuf = (int *)g->ctx->host_scal;  // pinned staging: error word, then ||b||^2
   CK(cudaMemcpyAsync(hbuf, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync((double *)hbuf + 1, a.bnorm2, sizeof(double), cudaMemcpyDeviceToHost, s));
-  g->ctx->d2h += sizeof(int) + sizeof(double);
+  g->ctx->stats->d2h += sizeof(int) + sizeof(double);
   CK(cudaStreamSynchronize(s));
   if (hbuf[0]) return pb_fail(PB_ERR_ARG, "an atom's trilinear cell leaves the grid");
   g->bnorm = std::sqrt(((double *)hbuf)[1]);
@@ -542,7 +542,7 @@ extern "C" pb_status pb_apply_operator(pb_grid *g, const void *u, void *au, int 
   cudaStream_t s = g->ctx->stream;
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
   CK(launch_apply(I, g->dinst, u, au, dtype == PB_F64 ? 0 : 1, s));
-  g->ctx->launches += 1;
+  g->ctx->stats->launches += 1;
   CK(cudaStreamSynchronize(s));
   return PB_OK;
 }
@@ -609,7 +609,7 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
     g->graph_ticks = ticks;
   }
   CK(cudaGraphLaunch(g->graph, s));
-  g->ctx->launches += 2ull * ticks;
+  g->ctx->stats->launches += 2ull * ticks;
   return PB_OK;
 }
 
@@ -642,8 +642,8 @@ static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, p
       st = pb_fail(PB_ERR_CUDA, std::string("profiled launch: ") + cudaGetErrorString(e));
       break;
     }
-    g->ctx->launches += 1;
-    g->ctx->d2h += sizeof(Scal);
+    g->ctx->stats->launches += 1;
+    g->ctx->stats->d2h += sizeof(Scal);
     if (which == 1) {
       if (phase == PH_RESID) { acc.ms_resid += ms; acc.n_resid++; }
       else if (phase != PH_DONE) { acc.ms_stencil += ms; acc.n_stencil++; }
@@ -692,10 +692,10 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(g->scal, &S0, sizeof(Scal), cudaMemcpyHostToDevice, s));
-  g->ctx->h2d += sizeof(Inst) + sizeof(Scal);
+  g->ctx->stats->h2d += sizeof(Inst) + sizeof(Scal);
   if (o->warm_start) {
     CK(launch_pack(phi, g->x64, g->d.nx, g->d.ny, g->d.nz, g->g.px, s));
-    g->ctx->launches += 1;
+    g->ctx->stats->launches += 1;
   } else {
     CK(cudaMemsetAsync(g->x64, 0, g->n_pad * sizeof(double), s));
   }
@@ -711,7 +711,7 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
       if ((st = pb_run_ticks(g, mode, coef, ticks))) return st;
       done_ticks += ticks;
       CK(cudaMemcpyAsync(hs, g->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
-      g->ctx->d2h += sizeof(Scal);
+      g->ctx->stats->d2h += sizeof(Scal);
       CK(cudaStreamSynchronize(s));
       if (hs->phase == PH_DONE) break;
       if (done_ticks > max_ticks) {
@@ -728,7 +728,7 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
     if (*herr & 2) S.status = PB_ERR_TIMEOUT;  // a device pipeline wait gave up
   }
   CK(launch_unpack(S.xbuf ? g->x64b : g->x64, phi, g->d.nx, g->d.ny, g->d.nz, g->g.px, s));
-  g->ctx->launches += 1;
+  g->ctx->stats->launches += 1;
   CK(cudaStreamSynchronize(s));
   if (info) {
     info->status = S.status;
@@ -755,8 +755,8 @@ extern "C" pb_status pb_energy(pb_grid *g, const double *phi, double *energy) {
                    g->d.origin[1], g->d.origin[2], phi, g->scratch + SCR_ENERGY_PART,
                    g->scratch + SCR_ENERGY, s));
   CK(cudaMemcpyAsync(energy, g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost, s));
-  g->ctx->launches += g->n_atoms > 0 ? 2 : 1;
-  g->ctx->d2h += sizeof(double);
+  g->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;
+  g->ctx->stats->d2h += sizeof(double);
   CK(cudaStreamSynchronize(s));
   return PB_OK;
 }

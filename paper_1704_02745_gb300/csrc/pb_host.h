@@ -1,5 +1,6 @@
 // pb_host.h -- host-side objects of libpb shared by the C-ABI translation units.
 #pragma once
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -13,7 +14,9 @@ struct pb_ctx {
   bool own_stream = false;
   int num_sms = 1;
   pb::Scal *host_scal = nullptr;  // pinned, for convergence polls
-  unsigned long long launches = 0, h2d = 0, d2h = 0;  // pb_ctx_stats counters
+  // pb_ctx_stats counters; a server's internal context counts into its parent's
+  std::atomic<unsigned long long> launches{0}, h2d{0}, d2h{0};
+  pb_ctx *stats = this;
 };
 
 struct pb_grid {

@@ -55,6 +55,7 @@ struct Scal {
   double relres;       // recursive residual / ref_norm
   double relres_true;  // ||b - A x|| / ||b|| (FP64)
   double bnorm;        // ||b||
+  double itol;         // tolerance of the current inner solve
   int phase;           // Phase
   int pbuf;            // index of the buffer holding the latest direction p
   int iter;            // iterations of the current inner solve

@@ -136,7 +136,8 @@ struct Slot {
 }  // namespace
 
 struct pb_server {
-  pb_ctx *ctx = nullptr;
+  pb_ctx *ctx = nullptr;      // internal context: the caller's device, the server's stream
+  pb_ctx *parent = nullptr;   // the caller's context (counters)
   size_t budget = 0;
   pb_solve_opts opts{};
   int mode = MODE_F32_REFINE, coef = COEF_PACKED;
@@ -327,7 +328,7 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
     if (!cuda_ok(cudaMemcpyAsync(s->d_inst + j, &I, sizeof(Inst), cudaMemcpyHostToDevice, s->stream),
                  s, "upload descriptor"))
       return false;
-    s->ctx->h2d += sizeof(Inst);
+    s->ctx->stats->h2d += sizeof(Inst);
   }
   const size_t old_st = s->cap_st, old_ch = s->cap_ch;
   Item *ost = s->d_st, *och = s->d_ch;
@@ -365,7 +366,7 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
   if (!cuda_ok(cudaMemcpyAsync(s->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s->stream),
                s, "counts"))
     return false;
-  s->ctx->h2d += (st.size() + ch.size()) * sizeof(Item) + sizeof(counts);
+  s->ctx->stats->h2d += (st.size() + ch.size()) * sizeof(Item) + sizeof(counts);
   // the copies read host vectors that go out of scope: wait for them
   return cuda_ok(cudaStreamSynchronize(s->stream), s, "upload");
 }
@@ -394,7 +395,7 @@ bool run_graph(pb_server *s, bool stale) {
     if (!cuda_ok(e, s, "instantiate")) return false;
   }
   if (!cuda_ok(cudaGraphLaunch(s->graph, s->stream), s, "graph launch")) return false;
-  s->ctx->launches += 2ull * s->ticks;
+  s->ctx->stats->launches += 2ull * s->ticks;
   return true;
 }
 
@@ -417,12 +418,12 @@ void complete(pb_server *s, const std::vector<int> &fin) {
                   g->scratch + SCR_ENERGY, s->stream);
     cudaMemcpyAsync(&energy[k], g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost,
                     s->stream);
-    s->ctx->launches += 1 + (g->n_atoms > 0 ? 2 : 1);
-    s->ctx->d2h += sizeof(double);
+    s->ctx->stats->launches += 1 + (g->n_atoms > 0 ? 2 : 1);
+    s->ctx->stats->d2h += sizeof(double);
     if (sl.req.phi_out) {
       cudaMemcpyAsync(sl.req.phi_out, s->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost,
                       s->stream);
-      s->ctx->d2h += n * sizeof(double);
+      s->ctx->stats->d2h += n * sizeof(double);
     }
   }
   cudaStreamSynchronize(s->stream);
@@ -474,7 +475,7 @@ void worker_main(pb_server *s) {
         cudaMemcpyAsync(s->d_list, started.data(), started.size() * sizeof(int),
                         cudaMemcpyHostToDevice, s->stream);
         launch_start(s->d_inst, s->d_list, (int)started.size(), s->stream);
-        s->ctx->launches += 1;
+        s->ctx->stats->launches += 1;
       }
       active_changed = false;
     }
@@ -494,7 +495,7 @@ void worker_main(pb_server *s) {
     graph_stale = false;
     const int hi = *std::max_element(active.begin(), active.end()) + 1;
     cudaMemcpyAsync(s->h_scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
-    s->ctx->d2h += hi * sizeof(Scal);
+    s->ctx->stats->d2h += hi * sizeof(Scal);
     if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "tick")) break;
     std::vector<int> fin;
     for (int j : active)
@@ -554,7 +555,7 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   if (o.max_iter <= 0) o.max_iter = 100000;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return pb_fail(PB_ERR_CUDA, "cudaSetDevice");
   pb_server *s = new pb_server();
-  s->ctx = ctx;
+  s->parent = ctx;
   s->budget = budget;
   s->opts = o;
   s->mode = o.precision == PB_PREC_F64 ? MODE_F64 : o.precision == PB_PREC_F32 ? MODE_F32
@@ -564,6 +565,14 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   s->slots.resize(MAX_SLOTS);
   for (int j = MAX_SLOTS - 1; j >= 0; j--) s->free_slots.push_back(j);
   bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
+  // every grid of the server works on the server's stream
+  s->ctx = new pb_ctx();
+  s->ctx->device = ctx->device;
+  s->ctx->stream = s->stream;
+  s->ctx->own_stream = false;
+  s->ctx->num_sms = ctx->num_sms;
+  s->ctx->stats = ctx->stats;
+  ok = ok && cudaMallocHost((void **)&s->ctx->host_scal, sizeof(Scal) * 64) == cudaSuccess;
   ok = ok && !pb_dalloc((void **)&s->d_scal, MAX_SLOTS * sizeof(Scal));
   ok = ok && !pb_dalloc((void **)&s->d_inst, MAX_SLOTS * sizeof(Inst));
   ok = ok && !pb_dalloc((void **)&s->d_counts, 2 * sizeof(int));
@@ -589,7 +598,7 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
   }
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
-  cudaSetDevice(s->ctx->device);
+  cudaSetDevice(s->parent->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (int j = 0; j < (int)s->slots.size(); j++)
     if (s->slots[j].g) {
@@ -604,6 +613,10 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
     if (p) cudaFree(p);
   if (s->h_scal) cudaFreeHost(s->h_scal);
   if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->ctx) {
+    if (s->ctx->host_scal) cudaFreeHost(s->ctx->host_scal);
+    delete s->ctx;
+  }
   delete s;
   return PB_OK;
 }

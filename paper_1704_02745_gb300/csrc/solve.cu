@@ -515,7 +515,7 @@ __device__ void fin_update(const Inst &I, Scal *S, double rz, double rr) {
   S->iter += 1;
   S->total_iter += 1;
   S->relres = sqrt(rr) / S->ref_norm;
-  const double tol = I.mode == MODE_F32_REFINE ? I.inner_tol : I.tol;
+  const double tol = I.mode == MODE_F32_REFINE ? S->itol : I.tol;
   if (S->relres < tol) {
     S->phase = PH_RESID;
   } else if (S->total_iter >= I.max_iter) {
@@ -555,6 +555,9 @@ __device__ void fin_resid(const Inst &I, Scal *S, double rr64, double rz) {
   S->rz_old = rz;
   S->ref_norm = I.mode == MODE_F32_REFINE ? sqrt(rr64) : S->bnorm;
   S->relres = I.mode == MODE_F32_REFINE ? 1.0 : rel;
+  // an inner solve reduces its residual by no more than the outer tolerance
+  // still needs (with a factor 2 of margin), and by at least inner_tol
+  S->itol = fmax(I.inner_tol, 0.5 * I.tol / rel);
   S->phase = PH_START;
 }
 

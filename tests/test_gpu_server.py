@@ -80,18 +80,22 @@ def test_warm_start_along_a_trajectory(pbm, ctx):
     a = base.atoms.copy()
     for _ in range(4):
         a = a.copy()
-        a.xyz = a.xyz + rng.normal(0, 0.2, a.xyz.shape)
+        a.xyz = a.xyz + rng.normal(0, 0.05, a.xyz.shape)
         snaps.append(a)
     with pbm.Server(ctx, 8 * GB, tol=1e-6) as srv:
         res = []
         for sn in snaps:  # one at a time: each snapshot starts from the last solution
             res.append(srv.poll(srv.submit(42, base.grid, sn), 60000)[0])
+    with pbm.Server(ctx, 8 * GB, tol=1e-6, warm_start=False) as srv:
+        cold = [srv.poll(srv.submit(43, base.grid, sn), 60000)[0] for sn in snaps]
     assert [r.warm_started for r in res] == [0, 1, 1, 1]
+    assert [r.warm_started for r in cold] == [0, 0, 0, 0]
     for sn, r in zip(snaps, res):
         s = oracle.setup(base.grid, sn)
         e_ref = oracle.energy(s, oracle.pcg(s, tol=1e-10).phi)
         assert r.status == 0 and abs(r.energy - e_ref) <= 1e-6 * abs(e_ref)
-    assert res[1].info.iterations < res[0].info.iterations
+        assert r.info.relres_true < 1e-6
+    assert sum(r.info.iterations for r in res[1:]) < sum(r.info.iterations for r in cold[1:])
 
 
 def test_budget_admission_and_eviction(pbm, ctx):
