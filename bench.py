@@ -524,32 +524,60 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def oracle_solve_sample(problem, atoms, tol, max_sample_iters):
-    """Time the oracle's setup and a bounded number of PCG iterations."""
+def oracle_solve_sample(problem, atoms, tol, max_sample_iters, dh_sample=2048):
+    """Time the oracle on one snapshot: dielectric map and charges in full, the
+    Debye-Hueckel boundary on `dh_sample` ghost nodes (scaled to all), and a
+    bounded number of PCG iterations.  Returns (fixed seconds, seconds per
+    iteration, solve result)."""
     import oracle
+    grid = problem.grid
     t0 = time.perf_counter()
-    s = oracle.setup(problem.grid, atoms)
+    oracle.dielectric(grid, atoms)
+    oracle.spread_charge(grid, atoms)
     t1 = time.perf_counter()
-    r = oracle.pcg(s, tol=tol, max_iter=max_sample_iters)
+    pos = oracle.ghost_positions(grid)
+    n_gh = pos.shape[0]
+    sel = pos[np.linspace(0, n_gh - 1, min(dh_sample, n_gh)).astype(int)]
     t2 = time.perf_counter()
-    oracle.energy(s, r.phi)
+    oracle.dh_points(grid, atoms, sel)
+    t_dh = (time.perf_counter() - t2) * n_gh / sel.shape[0]
+    ghost = oracle.dh_ghost(grid, atoms) if n_gh <= dh_sample else np.zeros(n_gh)
+    s = oracle.setup(grid, atoms, ghost=ghost)  # b from the sampled run is not used for timing
     t3 = time.perf_counter()
-    return (t1 - t0) + (t3 - t2), (t2 - t1) / max(r.iters, 1), r
+    r = oracle.pcg(s, tol=tol, max_iter=max_sample_iters)
+    t4 = time.perf_counter()
+    oracle.energy(s, r.phi)
+    t5 = time.perf_counter()
+    return (t1 - t0) + t_dh + (t5 - t4), (t4 - t3) / max(r.iters, 1), r
+
+
+def iteration_scale(tol):
+    """Full oracle Jacobi-PCG iterations per grid edge node, calibrated on the
+    smallest serving trajectory (Jacobi-PCG iterations grow about linearly
+    with the edge length on these grids)."""
+    import oracle
+    st = Stream(seed=5, req_seed=99)
+    k = int(np.argmin([t.grid.nx for t in st.trajs]))
+    g = st.trajs[k].grid
+    s = oracle.setup(g, st.trajs[k].base)
+    r = oracle.pcg(s, tol=tol)
+    return r.iters / g.nx
 
 
 def cpu_baseline(problem, atoms, gpu_iters, args):
-    """The FP64 oracle (single thread) on the host: setup + a bounded number of
-    PCG iterations, scaled to a full solve with the iteration count of a full
-    FP64 solve (estimated from the GPU run's iterations)."""
+    """The FP64 oracle (single thread) on the host: setup (boundary sampled)
+    and a bounded number of PCG iterations, scaled to a full solve."""
     import oracle
     oracle.build()
     n_iter = max(20, int(args.cpu_sample_iters))
     t_fixed, t_iter, r = oracle_solve_sample(problem, atoms, args.tol, n_iter)
-    full_iters = r.iters if r.status == 0 else gpu_iters
+    full_iters = r.iters if r.status == 0 else iteration_scale(args.tol) * problem.grid.nx
     t_solve = t_fixed + t_iter * full_iters
     return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one {problem.name} snapshot: oracle setup + {min(r.iters, n_iter)} FP64 "
-                       f"Jacobi-PCG iterations timed, scaled to {full_iters:.0f} iterations"),
+            "sample": (f"one {problem.name} ({problem.grid.nx}^3, {atoms.n} atoms): oracle "
+                       f"dielectric + charges, Debye-Hueckel on 2048 ghost nodes scaled to all, "
+                       f"{min(r.iters, n_iter)} FP64 Jacobi-PCG iterations scaled to "
+                       f"{full_iters:.0f}"),
             "cpu": platform_cpu()}
 
 
@@ -565,32 +593,32 @@ def platform_cpu():
 
 
 def run_reference(args):
-    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    """The FP64 CPU oracle as the reference arm (rank 0 only): per step one
+    request of the workload, timed as in oracle_solve_sample and scaled to a
+    full solve."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
     import oracle
     oracle.build()
     if args.workload == SERVING:
-        reqs = Stream(seed=5, req_seed=99).take(8)
-        problem = inputs.Problem("serving-request", reqs[0][1], reqs[0][2])
-        snaps = [a for _, _, a in reqs]
-        mixed = [inputs.Problem("serving-request", g, a) for _, g, a in reqs]
+        reqs = Stream(seed=5, req_seed=99).take(args.warmup + args.steps)
+        probs = [inputs.Problem("serving-request", g, a) for _, g, a in reqs]
+        scale = iteration_scale(args.tol)
+        iters_of = lambda pr: scale * pr.grid.nx
+        name = "serving stream: 16 trajectories, 300-8000 atoms, grids 33^3-193^3"
     else:
         problem = WORKLOADS[args.workload]()
-        snaps = snapshots(problem, 8, seed=100)
-        mixed = None
-    # calibrate the full iteration count once (untimed)
-    s = oracle.setup(problem.grid, snaps[0])
-    full = oracle.pcg(s, tol=args.tol, max_iter=args.cpu_sample_iters if problem.grid.n > 5e6 else 100000)
-    full_iters = full.iters
+        probs = [inputs.Problem(problem.name, problem.grid, a)
+                 for a in snapshots(problem, args.warmup + args.steps, seed=100)]
+        full = oracle.pcg(oracle.setup(problem.grid, probs[0].atoms), tol=args.tol)
+        iters_of = lambda pr: full.iters
+        name = problem.name
     times = []
-    for i in range(args.warmup + args.steps):
-        pr = mixed[i % len(mixed)] if mixed else problem
-        t_fixed, t_iter, _ = oracle_solve_sample(pr, pr.atoms if mixed else snaps[i % len(snaps)],
-                                                 args.tol, args.cpu_sample_iters)
+    for i, pr in enumerate(probs):
+        t_fixed, t_iter, _ = oracle_solve_sample(pr, pr.atoms, args.tol, args.cpu_sample_iters)
         if i >= args.warmup:
-            times.append(t_fixed + t_iter * full_iters * (pr.grid.n / problem.grid.n) ** (1 / 3))
+            times.append(t_fixed + t_iter * iters_of(pr))
     total = sum(times)
     val = args.steps / total
     print(json.dumps({
@@ -598,13 +626,14 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": (SERVING if mixed else problem.name), "tol": args.tol,
-                   "solver": "oracle FP64 Jacobi-PCG"},
+        "config": {"workload": name, "tol": args.tol, "solver": "oracle FP64 Jacobi-PCG"},
         "latency_ms": {"p50": pct([t * 1e3 for t in times], 50),
                        "p99": pct([t * 1e3 for t in times], 99)},
         "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": (f"per step: oracle setup + {args.cpu_sample_iters} FP64 "
-                                    f"Jacobi-PCG iterations, scaled to {full_iters} iterations"),
+                         "sample": (f"per step one request: oracle dielectric + charges, "
+                                    f"Debye-Hueckel on 2048 ghost nodes scaled to all, "
+                                    f"{args.cpu_sample_iters} FP64 Jacobi-PCG iterations scaled "
+                                    f"to a full solve"),
                          "cpu": platform_cpu()},
         "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -625,7 +654,7 @@ def main():
     ap.add_argument("--coef", default="packed", choices=["packed", "f32", "bf16"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
-    ap.add_argument("--cpu-sample-iters", type=int, default=40)
+    ap.add_argument("--cpu-sample-iters", type=int, default=20)
     ap.add_argument("--dh", default="f32", choices=["f32", "f64"],
                     help="precision of the Debye-Hueckel boundary sum in the grid setup")
     ap.add_argument("--no-cpu-baseline", action="store_true")

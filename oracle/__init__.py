@@ -69,6 +69,7 @@ def _load():
         lib.or_spread_charge.restype = ctypes.c_int
         lib.or_spread_charge.argtypes = [G, ctypes.c_int, _P, _P, _P]
         lib.or_dh_ghost.argtypes = [G, ctypes.c_int, _P, _P, _P]
+        lib.or_dh_points.argtypes = [G, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]
         lib.or_rhs.argtypes = [G, _P, _P, _P, _P, _P, _P]
         lib.or_diag.argtypes = [G, _P, _P, _P, _P, _P]
         lib.or_apply.argtypes = [G, _P, _P, _P, _P, _P, _P]
@@ -161,6 +162,35 @@ def dh_ghost(grid, atoms) -> np.ndarray:
     xyz = np.ascontiguousarray(atoms.xyz, dtype=np.float64)
     q = np.ascontiguousarray(atoms.q, dtype=np.float64)
     lib.or_dh_ghost(ctypes.byref(g), atoms.n, _ptr(xyz), _ptr(q), _ptr(out))
+    return out
+
+
+def ghost_positions(grid) -> np.ndarray:
+    """Coordinates (n_ghost x 3) of the ghost nodes in the face order of dh_ghost."""
+    nx, ny, nz, h = grid.nx, grid.ny, grid.nz, grid.h
+    ox, oy, oz = grid.origin
+    out = []
+    for gi in (-1, nx):
+        K, J = np.meshgrid(np.arange(nz), np.arange(ny), indexing="ij")
+        out.append(np.stack([np.full(K.size, ox + gi * h), oy + J.ravel() * h, oz + K.ravel() * h], 1))
+    for gj in (-1, ny):
+        K, I = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+        out.append(np.stack([ox + I.ravel() * h, np.full(K.size, oy + gj * h), oz + K.ravel() * h], 1))
+    for gk in (-1, nz):
+        J, I = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        out.append(np.stack([ox + I.ravel() * h, oy + J.ravel() * h, np.full(J.size, oz + gk * h)], 1))
+    return np.ascontiguousarray(np.concatenate(out), dtype=np.float64)
+
+
+def dh_points(grid, atoms, points: np.ndarray) -> np.ndarray:
+    """Debye-Hueckel potential of the atoms at arbitrary points (n x 3)."""
+    lib = _load()
+    g = _cgrid(grid)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(pts.shape[0])
+    xyz = np.ascontiguousarray(atoms.xyz, dtype=np.float64)
+    q = np.ascontiguousarray(atoms.q, dtype=np.float64)
+    lib.or_dh_points(ctypes.byref(g), atoms.n, _ptr(xyz), _ptr(q), pts.shape[0], _ptr(pts), _ptr(out))
     return out
 
 

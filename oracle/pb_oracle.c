@@ -198,6 +198,13 @@ static double dh_point(const or_grid *g, int n_atoms, const double *xyz, const d
     return s;
 }
 
+/* The same sum at n arbitrary points (p: n x 3). */
+void or_dh_points(const or_grid *g, int n_atoms, const double *xyz, const double *q, int n,
+                  const double *p, double *out) {
+    for (int t = 0; t < n; t++)
+        out[t] = dh_point(g, n_atoms, xyz, q, p[3 * t], p[3 * t + 1], p[3 * t + 2]);
+}
+
 /* Potential on the ghost faces, in face order x-, x+, y-, y+, z-, z+; each
  * face stored (nz, ny) for x faces, (nz, nx) for y faces, (ny, nx) for z faces
  * (first index slowest). */

@@ -337,6 +337,14 @@ def test_dh_boundary_closed_forms():
     assert np.max(np.abs(tot - parts)) < 1e-14 * np.max(np.abs(tot))
 
 
+def test_dh_points_match_ghost_faces():
+    p = inputs.random_small(12, 6, 7, 8, n_atoms=9)
+    pos = oracle.ghost_positions(p.grid)
+    assert pos.shape[0] == oracle.ghost_count(p.grid)
+    got = oracle.dh_points(p.grid, p.atoms, pos)
+    assert np.array_equal(got, oracle.dh_ghost(p.grid, p.atoms))
+
+
 def test_rhs_fold_reproduces_harmonic_linear_field():
     # A linear field is discrete-harmonic for constant eps: with no charge and
     # ghost values taken from it, the solve must return the field at the nodes.
