@@ -329,7 +329,11 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
       st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
     }
     if (q >= 2) {
-      if (G.row_ok) {
+      // groups with no node inside the grid store nothing: past the last
+      // tile's valid columns they may lie beyond the row pitch (a group with
+      // any valid node ends within it: pitch and group starts are multiples
+      // of NV)
+      if (G.vmask) {
         const T *rm = ring + rq1 * ring_plane;
         const Vec<T> ym = ldv(rm + cg - RGW), yp = ldv(rm + cg + RGW);
         const T xl = rm[cg - 1], xr = rm[cg + NV];

@@ -288,7 +288,10 @@ def test_solve_edge_cases(pbm, ctx):
         assert g.solve(phi, precision="f32_refine", tol=1e-6).status == 0
 
 
-@pytest.mark.parametrize("dims", [(2, 9, 9), (33, 2, 5), (64, 8, 17), (65, 9, 16)])
+# (159, ...) and (175, ...): the last x tile reaches whole NV-groups past the
+# row pitch (pitch = nx + 1), which must store nothing
+@pytest.mark.parametrize("dims", [(2, 9, 9), (33, 2, 5), (64, 8, 17), (65, 9, 16), (159, 7, 6),
+                                  (175, 5, 9), (261, 4, 3)])
 def test_ragged_tiles(pbm, ctx, dims):
     p = inputs.random_small(40, *dims, n_atoms=6)
     s = oracle.setup(p.grid, p.atoms)
