@@ -187,6 +187,28 @@ pb_status pb_grid_export(pb_grid *grid, int what, void *host_dst, size_t bytes);
  * `precision` (the admission model of the server). */
 size_t pb_grid_bytes(const pb_grid_desc *desc, int precision);
 
+/* Energy of a potential with no device allocation.  The paper has no
+ * counterpart: this is for callers that cannot allocate device memory -- for
+ * example an MD engine whose memory manager owns all device memory, or a
+ * time-critical loop in which cudaMalloc / cudaFree (which synchronise the
+ * device) are not allowed.  It computes what pb_energy computes,
+ * 1/2 * 332.0637 * sum_atoms q_a * (trilinear interpolation of phi at x_a),
+ * from the caller's arrays only:
+ *   xyzq    DEVICE array, n_atoms x 4 doubles (x, y, z, charge), 32-byte aligned
+ *   nx, ny, nz, h, origin[3] (HOST)  the grid of phi (as pb_grid_desc)
+ *   phi     DEVICE array of nx*ny*nz doubles, x fastest
+ *   energy  DEVICE pointer to one double that receives the result
+ *   cuda_stream  stream to run on (NULL: the legacy default stream)
+ * Work is queued on the stream; the call does not wait for it.  The
+ * reduction's partial sums use a fixed array inside the library's device
+ * memory (room for n_atoms <= 1,048,576; larger returns PB_ERR_ARG).  The
+ * first call on a device looks up that array's device address (make it
+ * before any stream capture); every later call on that device reuses it.
+ * All calls share the array, so calls that overlap on the GPU race. */
+pb_status pb_energy_noalloc(int n_atoms, const double *xyzq, int nx, int ny, int nz, double h,
+                            const double *origin, const double *phi, double *energy,
+                            void *cuda_stream);
+
 /* ------------------------------------------------------------------------ */
 /* Continuous-batching server.  The paper's motivation is PB on thousands to
  * millions of MD snapshots (Sec. 1); the server solves many snapshots at once:

@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
     lib.pb_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
                                     ctypes.POINTER(ctypes.c_uint64)]
+    lib.pb_energy_noalloc.argtypes = [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P, _P, _P]
     lib.pb_plan_admission.restype = ctypes.c_int
     lib.pb_plan_admission.argtypes = [ctypes.c_size_t, ctypes.POINTER(SlotState), ctypes.c_int,
                                       _P, _P, _P, ctypes.c_int, _P, _P]
@@ -232,6 +234,15 @@ def pb_energy(grid: int, phi) -> float:
     e = ctypes.c_double(0.0)
     _check(load().pb_energy(_P(grid), _P(_dptr(phi)), ctypes.byref(e)))
     return e.value
+
+
+def pb_energy_noalloc(xyzq, spec, phi, energy, stream=None):
+    """Energy without device allocation: xyzq (n x 4 doubles), phi and the
+    one-double `energy` output are device arrays; queued on `stream`."""
+    n = int(xyzq.shape[0]) if xyzq is not None else 0
+    org = (ctypes.c_double * 3)(*spec.origin)
+    _check(load().pb_energy_noalloc(n, _P(_dptr(xyzq)), spec.nx, spec.ny, spec.nz, spec.h, org,
+                                    _P(_dptr(phi)), _P(_dptr(energy)), _P(stream or 0)))
 
 
 def pb_grid_export(grid: int, what: str, shape, dtype) -> np.ndarray:
