@@ -329,14 +329,11 @@ def run_serving(args):
     p_make, p_lat_stream = poisson_run(plain_stream, Stream(seed=5, req_seed=77 + rank).take(n_pois),
                                        rate)
     plain.close()
-    # per-kernel device time of one 129^3 solve (kernels launched one by one between events)
-    prob = inputs.globule_129()
-    spec = prob.grid.replace(dh="f32")
-    with pb.Grid(ctx, spec, prob.atoms) as g:
-        phi = torch.zeros(spec.shape, dtype=torch.float64, device="cuda")
-        g.solve(phi, precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol)
-        prof = g.solve(phi, precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol,
-                       profile=True)
+    # per-kernel device time on the served workload: one step with every
+    # phase kernel launched on its own between CUDA events
+    srv.profile_begin()
+    serve_batch(srv, [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)])
+    kp = srv.profile_end()
     srv.close()
     if rank != 0:
         ctx.close()
@@ -345,11 +342,10 @@ def run_serving(args):
         return
     n_req = args.steps * per_step
     hbm, peak_kind = peaks()
-    n129 = spec.n
-    t_st = prof.ms_stencil / max(prof.n_stencil, 1) / 1e3
-    t_up = prof.ms_update / max(prof.n_update, 1) / 1e3
-    ach_st = BYTES_PER_NODE["stencil"] * n129 / t_st / 1e9
-    ach_up = BYTES_PER_NODE["update"] * n129 / t_up / 1e9
+    t_st = kp.ms_stencil / max(kp.launches_stencil, 1) / 1e3
+    t_up = kp.ms_update / max(kp.launches_update, 1) / 1e3
+    ach_st = kp.bytes_stencil / max(kp.ms_stencil, 1e-12) / 1e6
+    ach_up = kp.bytes_update / max(kp.ms_update, 1e-12) / 1e6
     trf = NCU_TRAFFIC_PER_NODE["stencil"]
     out = {
         "metric": METRIC,
@@ -385,14 +381,19 @@ def run_serving(args):
                            "fp64_plain": {"solves_per_s": n_pois / p_make,
                                           "p50_ms": pct([1e3 * x for x in p_lat_stream], 50),
                                           "p99_ms": pct([1e3 * x for x in p_lat_stream], 99)}},
-        "roofline": {"bound": "hbm", "kernel": "k_stencil<float,packed> (CG stencil pass), 129^3 grid",
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_stencil<float,packed>: batched stencil pass over the active grids",
                      "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
                      "peak_kind": peak_kind,
-                     "traffic": None if trf is None else trf * n129,
+                     "traffic": None if trf is None else trf * kp.bytes_stencil / 25.0 /
+                     max(kp.launches_stencil, 1),
+                     "bytes_per_launch": kp.bytes_stencil / max(kp.launches_stencil, 1),
                      "bytes_per_node": BYTES_PER_NODE["stencil"], "launch_ms": t_st * 1e3,
+                     "launches": kp.launches_stencil,
+                     "measured": "one serving step, each kernel between CUDA events",
                      "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
                                      "bytes_per_node": BYTES_PER_NODE["update"],
-                                     "launch_ms": t_up * 1e3}},
+                                     "launch_ms": t_up * 1e3, "launches": kp.launches_update}},
         "e2e": {"value": world * e2e_steps * per_step / sum(e2e_walls), "unit": "solves/s",
                 "h2d_bytes_per_step": int((e2e1[1] - e2e0[1]) / e2e_steps),
                 "d2h_bytes_per_step": int((e2e1[2] - e2e0[2]) / e2e_steps),

@@ -258,6 +258,20 @@ pb_status pb_batch_poll(pb_server *server, uint64_t ticket, int timeout_ms, pb_r
 pb_status pb_server_stats(pb_server *server, int *queued, int *active, int *resident,
                           size_t *bytes_resident, uint64_t *completed);
 
+/* Kernel measurement of a running server.  Between begin and end the worker
+ * launches each phase kernel on its own between CUDA events (slower, for
+ * measurement) and sums, per kind of launch, the device time and the
+ * algorithmic HBM bytes of the grids active in it: per grid node, 25 B for a
+ * CG stencil pass, 37 B for an FP64 residual pass, 13 B for an update pass
+ * (FP32 inner solves with one-byte coefficients; FP64 solves: 49, 37, 25). */
+typedef struct {
+    double ms_stencil, bytes_stencil;  /* stencil-kernel launches (CG and residual work) */
+    double ms_update, bytes_update;    /* update-kernel launches */
+    int launches_stencil, launches_update;
+} pb_kernel_profile;
+pb_status pb_server_profile_begin(pb_server *server);
+pb_status pb_server_profile_end(pb_server *server, pb_kernel_profile *out);
+
 /* Admission decision of the server, exposed for testing.  Requests are
  * considered in queue order.  A request whose trajectory has an idle
  * resident grid of the same dims reuses it; a request whose trajectory is

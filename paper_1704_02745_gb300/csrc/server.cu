@@ -18,6 +18,7 @@
 //   5. reads all grids' scalars and completes the finished requests (energy,
 //      optional copy of phi to the caller).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -166,6 +167,10 @@ struct pb_server {
   size_t cap_dense = 0;
   cudaGraphExec_t graph = nullptr;
   int ticks = 8;
+  // kernel measurement (pb_server_profile_begin/end)
+  std::atomic<bool> profiling{false};
+  pb_kernel_profile prof{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   KernelGrid kg{};
   std::string worker_error;
 };
@@ -452,6 +457,63 @@ void complete(pb_server *s, const std::vector<int> &fin) {
   s->cv_done.notify_all();
 }
 
+// Algorithmic bytes of one launch over the active grids, from their phases.
+double launch_bytes(pb_server *s, const std::vector<int> &active, bool stencil) {
+  const bool f64 = s->mode == MODE_F64;
+  double b = 0;
+  for (int j : active) {
+    const pb_grid *g = s->slots[j].g;
+    const double n = (double)g->d.nx * g->d.ny * g->d.nz;
+    const int ph = s->h_scal[j].phase;
+    if (stencil) {
+      if (ph == PH_INNER || ph == PH_START) b += n * (f64 ? 49 : 25);
+      else if (ph == PH_RESID) b += n * 37;
+    } else if (ph == PH_INNER) {
+      b += n * (f64 ? 25 : 13);
+    }
+  }
+  return b;
+}
+
+// Measurement ticks: each kernel on its own between events, phases read
+// before each launch.
+bool run_profiled(pb_server *s, const std::vector<int> &active) {
+  Batch B;
+  B.inst = s->d_inst;
+  B.st_items = s->d_st;
+  B.ch_items = s->d_ch;
+  B.n_items = s->d_counts;
+  B.st_part = s->d_st_part;
+  B.ch_part = s->d_ch_part;
+  B.error = s->d_err;
+  const int hi = *std::max_element(active.begin(), active.end()) + 1;
+  for (int t = 0; t < 2 * s->ticks; t++) {
+    const bool st = (t & 1) == 0;
+    cudaMemcpyAsync(s->h_scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
+    if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "profile")) return false;
+    const double bytes = launch_bytes(s, active, st);
+    cudaEventRecord(s->ev0, s->stream);
+    if (!cuda_ok(launch_phase(B, s->mode, s->coef, s->kg, st ? 1 : 2, s->stream), s, "launch"))
+      return false;
+    cudaEventRecord(s->ev1, s->stream);
+    if (!cuda_ok(cudaEventSynchronize(s->ev1), s, "profile")) return false;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+    s->ctx->stats->launches += 1;
+    if (bytes <= 0) continue;  // nothing of this kind was active
+    if (st) {
+      s->prof.ms_stencil += ms;
+      s->prof.bytes_stencil += bytes;
+      s->prof.launches_stencil++;
+    } else {
+      s->prof.ms_update += ms;
+      s->prof.bytes_update += bytes;
+      s->prof.launches_update++;
+    }
+  }
+  return true;
+}
+
 void worker_main(pb_server *s) {
   cudaSetDevice(s->ctx->device);
   bool active_changed = true, graph_stale = true;
@@ -491,8 +553,12 @@ void worker_main(pb_server *s) {
         if (x.g) { s->n_resident++; s->bytes_resident += x.bytes; }
     }
     if (active.empty()) continue;
-    if (!run_graph(s, graph_stale)) break;
-    graph_stale = false;
+    if (s->profiling.load()) {
+      if (!run_profiled(s, active)) break;
+    } else {
+      if (!run_graph(s, graph_stale)) break;
+      graph_stale = false;
+    }
     const int hi = *std::max_element(active.begin(), active.end()) + 1;
     cudaMemcpyAsync(s->h_scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
     s->ctx->stats->d2h += hi * sizeof(Scal);
@@ -581,6 +647,7 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMallocHost((void **)&s->h_scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
   ok = ok && cudaMemset(s->d_scal, 0, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
   ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
   if (!ok) {
     pb_server_destroy(s);
     return pb_fail(PB_ERR_OOM, "pb_server_create: device allocation failed");
@@ -612,6 +679,8 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->h_scal) cudaFreeHost(s->h_scal);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->ctx) {
     if (s->ctx->host_scal) cudaFreeHost(s->ctx->host_scal);
@@ -679,5 +748,21 @@ extern "C" pb_status pb_server_stats(pb_server *s, int *queued, int *active, int
   if (resident) *resident = s->n_resident;
   if (bytes) *bytes = s->bytes_resident;
   if (completed) *completed = s->completed;
+  return PB_OK;
+}
+
+extern "C" pb_status pb_server_profile_begin(pb_server *s) {
+  if (!s) return pb_fail(PB_ERR_ARG, "pb_server_profile_begin: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(&s->prof, 0, sizeof(s->prof));
+  s->profiling.store(true);
+  return PB_OK;
+}
+
+extern "C" pb_status pb_server_profile_end(pb_server *s, pb_kernel_profile *out) {
+  if (!s || !out) return pb_fail(PB_ERR_ARG, "pb_server_profile_end: NULL argument");
+  s->profiling.store(false);
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->prof;
   return PB_OK;
 }

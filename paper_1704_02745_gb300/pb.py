@@ -81,6 +81,15 @@ class Result(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("warm_started", ctypes.c_int)]
 
 
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("ms_stencil", ctypes.c_double), ("bytes_stencil", ctypes.c_double),
+                ("ms_update", ctypes.c_double), ("bytes_update", ctypes.c_double),
+                ("launches_stencil", ctypes.c_int), ("launches_update", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SlotState(ctypes.Structure):
     _fields_ = [("trajectory_id", ctypes.c_int64), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("bytes", ctypes.c_size_t), ("busy", ctypes.c_int),
@@ -124,6 +133,8 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_uint64)]
     lib.pb_energy_noalloc.argtypes = [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P, _P, _P]
+    lib.pb_server_profile_begin.argtypes = [_P]
+    lib.pb_server_profile_end.argtypes = [_P, ctypes.POINTER(KernelProfile)]
     lib.pb_plan_admission.restype = ctypes.c_int
     lib.pb_plan_admission.argtypes = [ctypes.c_size_t, ctypes.POINTER(SlotState), ctypes.c_int,
                                       _P, _P, _P, ctypes.c_int, _P, _P]
@@ -411,6 +422,14 @@ class Server:
 
     def stats(self):
         return pb_server_stats(self.handle)
+
+    def profile_begin(self):
+        _check(load().pb_server_profile_begin(_P(self.handle)))
+
+    def profile_end(self) -> KernelProfile:
+        out = KernelProfile()
+        _check(load().pb_server_profile_end(_P(self.handle), ctypes.byref(out)))
+        return out
 
     def close(self):
         if self.handle:

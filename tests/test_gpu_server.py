@@ -141,3 +141,17 @@ def test_fp64_server(pbm, ctx):
     assert r.status == 0
     assert np.max(np.abs(phi - ref.phi)) <= 1e-8 * np.max(np.abs(ref.phi))
     assert abs(r.info.iterations - ref.iters) <= max(1, 0.02 * ref.iters)
+
+
+def test_kernel_profile(pbm, ctx):
+    probs = mixed_requests(4, seed=21)
+    with pbm.Server(ctx, 8 * GB, warm_start=False) as srv:
+        srv.profile_begin()
+        res = run_all(srv, list(enumerate(probs)))
+        kp = srv.profile_end()
+    assert all(r.status == 0 for r, _ in res)
+    assert kp.launches_stencil > 0 and kp.launches_update > 0
+    assert kp.bytes_stencil > 0 and kp.ms_stencil > 0 and kp.ms_update > 0
+    # every update launch covers at most all grids, each at 13 B per node
+    total_nodes = sum(p.grid.n for p in probs)
+    assert kp.bytes_update <= kp.launches_update * 13 * total_nodes
