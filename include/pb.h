@@ -212,10 +212,11 @@ pb_status pb_energy_noalloc(int n_atoms, const double *xyzq, int nx, int ny, int
 /* ------------------------------------------------------------------------ */
 /* Continuous-batching server.  The paper's motivation is PB on thousands to
  * millions of MD snapshots (Sec. 1); the server solves many snapshots at once:
- * requests are admitted as device memory allows, each snapshot's grid stays
- * resident per trajectory (the next snapshot warm-starts from the last
- * solution), and all active grids advance together through the same
- * persistent phase kernels, each under its own convergence mask.  A result
+ * requests are admitted as device memory allows, grids stay resident per
+ * trajectory (a snapshot warm-starts from the trajectory's latest solution;
+ * snapshots of one trajectory may solve at the same time on separate grids),
+ * and all active grids advance together through the same persistent phase
+ * kernels, each under its own convergence mask.  A result
  * does not depend on which other requests share the device (each grid's
  * reductions are summed in its own fixed order). */
 
@@ -274,12 +275,14 @@ pb_status pb_server_profile_end(pb_server *server, pb_kernel_profile *out);
 
 /* Admission decision of the server, exposed for testing.  Requests are
  * considered in queue order.  A request whose trajectory has an idle
- * resident grid of the same dims reuses it; a request whose trajectory is
- * busy waits; any other request needs req_bytes[i] new bytes, for which idle
- * grids are evicted least recently used first.  The first request that does
- * not fit stops admission of requests that need new memory (no overtaking).
- * Outputs: admit[i] = index of the reused slot, -1 for a new slot, -2 not
- * admitted; evict[j] = 1 for slots to evict.  Returns the number admitted. */
+ * resident grid of the same dims reuses it (the most recently used one);
+ * any other request needs req_bytes[i] new bytes (a trajectory whose grids
+ * are all busy gets one more grid), for which idle grids of the same
+ * trajectory with other dims, then idle grids least recently used first, are
+ * evicted.  The first request that does not fit stops admission of requests
+ * that need new memory (no overtaking).  Outputs: admit[i] = index of the
+ * reused slot, -1 for a new slot, -2 not admitted; evict[j] = 1 for slots to
+ * evict.  Returns the number admitted. */
 typedef struct {
     int64_t trajectory_id;
     int nx, ny, nz;

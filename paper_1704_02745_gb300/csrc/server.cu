@@ -51,39 +51,35 @@ extern "C" int pb_plan_admission(size_t budget, const pb_slot_state *slots, int 
   }
   int n_admit = 0;
   bool blocked = false;  // a request needing new memory did not fit: no overtaking
-  std::vector<int64_t> waiting;  // trajectories with an earlier request not admitted
   for (int i = 0; i < n_reqs; i++) {
     admit[i] = -2;
     const int64_t tr = req_traj[i];
-    const bool has_traj = tr >= 0;
-    if (has_traj && std::find(waiting.begin(), waiting.end(), tr) != waiting.end()) continue;
-    // a resident grid of this trajectory
+    const int *dm = req_dims + 3 * i;
+    // an idle resident grid of this trajectory with the same dims, most recent first
     int own = -1;
-    if (has_traj)
+    if (tr >= 0)
       for (int j = 0; j < n_slots; j++)
-        if (!gone[j] && slots[j].trajectory_id == tr) { own = j; break; }
-    if (own >= 0 && busy[own]) {  // the previous snapshot is still on the device
-      waiting.push_back(tr);
-      continue;
-    }
-    if (own >= 0 && slots[own].nx == req_dims[3 * i] && slots[own].ny == req_dims[3 * i + 1] &&
-        slots[own].nz == req_dims[3 * i + 2]) {
+        if (!gone[j] && !busy[j] && slots[j].trajectory_id == tr && slots[j].nx == dm[0] &&
+            slots[j].ny == dm[1] && slots[j].nz == dm[2] &&
+            (own < 0 || slots[j].last_used > slots[own].last_used))
+          own = j;
+    if (own >= 0) {
       admit[i] = own;
       busy[own] = 1;
       n_admit++;
       continue;
     }
-    if (blocked) {
-      if (has_traj) waiting.push_back(tr);
-      continue;
-    }
-    // new memory: a stale grid of this trajectory goes first, then LRU idle grids
-    size_t need = req_bytes[i];
-    if (own >= 0) {
-      gone[own] = 1;
-      evict[own] = 1;
-      used -= slots[own].bytes;
-    }
+    if (blocked) continue;
+    // new memory: idle grids of this trajectory with other dims go first, then
+    // idle grids least recently used first
+    const size_t need = req_bytes[i];
+    if (tr >= 0)
+      for (int j = 0; j < n_slots; j++)
+        if (!gone[j] && !busy[j] && slots[j].trajectory_id == tr) {
+          gone[j] = 1;
+          evict[j] = 1;
+          used -= slots[j].bytes;
+        }
     while (used + need > budget) {
       int lru = -1;
       for (int j = 0; j < n_slots; j++)
@@ -95,7 +91,6 @@ extern "C" int pb_plan_admission(size_t budget, const pb_slot_state *slots, int 
     }
     if (used + need > budget) {
       blocked = true;
-      if (has_traj) waiting.push_back(tr);
       continue;
     }
     used += need;
@@ -128,8 +123,10 @@ struct Slot {
   int64_t traj = -1;
   size_t bytes = 0;
   bool busy = false;
-  bool has_solution = false;  // x64 holds this trajectory's last solution
+  bool has_solution = false;  // x64[xbuf] holds a solution of this trajectory
   uint64_t last_used = 0;
+  uint64_t solved_at = 0;     // clock of that solution
+  int xbuf = 0;               // which x64 buffer holds it
   Request req;
   bool warm = false;
 };
@@ -285,6 +282,29 @@ std::vector<int> admit(pb_server *s) {
       sl.has_solution = false;
     }
     Slot &sl = s->slots[j];
+    // a new grid of a trajectory starts from the trajectory's latest solution
+    // held by an idle grid of the same dims, if any (device-to-device copy)
+    if (adm[i] == -1 && s->opts.warm_start && rq.traj >= 0) {
+      int src = -1;
+      for (int k = 0; k < (int)s->slots.size(); k++) {
+        const Slot &o = s->slots[k];
+        if (k != j && o.g && o.traj == rq.traj && o.has_solution && !o.busy &&
+            o.g->d.nx == rq.desc.nx && o.g->d.ny == rq.desc.ny && o.g->d.nz == rq.desc.nz &&
+            (src < 0 || o.solved_at > s->slots[src].solved_at))
+          src = k;
+      }
+      if (src >= 0) {
+        const Slot &o = s->slots[src];
+        const double *from = o.xbuf ? o.g->x64b : o.g->x64;
+        cudaMemcpyAsync(sl.g->x64, from, sl.g->n_pad * sizeof(double), cudaMemcpyDeviceToDevice,
+                        s->stream);
+        Scal z;
+        memset(&z, 0, sizeof(z));
+        cudaMemcpyAsync(s->d_scal + j, &z, sizeof(Scal), cudaMemcpyHostToDevice, s->stream);
+        sl.has_solution = true;
+        sl.solved_at = o.solved_at;
+      }
+    }
     sl.busy = true;
     sl.last_used = ++s->clock;
     sl.warm = s->opts.warm_start && sl.has_solution;
@@ -450,8 +470,10 @@ void complete(pb_server *s, const std::vector<int> &fin) {
     s->done[sl.req.ticket] = r;
     s->completed++;
     sl.busy = false;
-    sl.has_solution = S.status == PB_OK;
+    sl.has_solution = S.status == PB_OK && S.outer != -1;
+    sl.xbuf = S.xbuf;
     sl.last_used = ++s->clock;
+    sl.solved_at = sl.last_used;
     sl.req = Request();
   }
   s->cv_done.notify_all();

@@ -26,11 +26,17 @@ def test_reuses_idle_grid_of_the_trajectory():
     assert admit == [0] and evict == [0]
 
 
-def test_busy_trajectory_waits_but_others_proceed():
+def test_busy_trajectory_gets_another_grid():
     admit, evict = pb.pb_plan_admission(1000, [slot(7, busy=True)],
                                         [(7, (33, 33, 33), 100), (8, (33, 33, 33), 100),
                                          (7, (33, 33, 33), 100)])
-    assert admit == [-2, -1, -2]
+    assert admit == [-1, -1, -1] and evict == [0]
+
+
+def test_reuses_the_most_recent_idle_grid():
+    slots = [slot(7, last=3), slot(7, last=9), slot(7, busy=True, last=12)]
+    admit, evict = pb.pb_plan_admission(1000, slots, [(7, (33, 33, 33), 100), (7, (33, 33, 33), 100)])
+    assert admit == [1, 0] and evict == [0, 0, 0]
 
 
 def test_lru_eviction_of_idle_grids_only():
