@@ -52,7 +52,7 @@ WORKLOADS = {
 BYTES_PER_NODE = {"stencil": 4 + 4 + 4 + 1 + 4 + 4 + 4, "update": 4 + 4 + 1 + 4}
 # DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
 # profiles/ (None until a capture of the current kernel exists).
-NCU_TRAFFIC_PER_NODE = {"stencil": None}
+NCU_TRAFFIC_PER_NODE = {"stencil": (244.852992e6 + 158.896384e6) / 16974593}  # k_stencil_globule257.md
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
 
 
