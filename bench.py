@@ -3,8 +3,8 @@
 
 Default workload ("serving"): 16 MD-like trajectories (300-8,000 atoms, grids
 33^3-193^3 at fill ratio 1.5, snapshots a 0.2 A random walk).  One step = a
-batch of 64 snapshot requests submitted at once to the continuous-batching
-server (grid setup, FP32 Jacobi-PCG with FP64 iterative refinement to a 1e-6
+batch of 64 snapshot requests to the continuous-batching server (steady state:
+step k+1 is queued while step k completes) (grid setup, FP32 Jacobi-PCG with FP64 iterative refinement to a 1e-6
 true relative residual, warm start along each trajectory, energy back to the
 host).  The same requests are also solved one at a time with plain FP64 PCG,
 and a Poisson request stream at 0.8x the measured plain-FP64 capacity gives
@@ -201,6 +201,24 @@ def serve_batch(srv, reqs, want_phi=False):
     return time.perf_counter() - t0, [r.seconds for r in res], res
 
 
+def serve_steps(srv, batches, want_phi=False):
+    """Steady state: step k+1's requests are queued before step k's results are
+    collected, so the server always has work.  Returns (wall seconds, latencies
+    s (submit -> ready), results)."""
+    t0 = time.perf_counter()
+    pend = [srv.submit(k, g, a, want_phi=want_phi) for k, g, a in batches[0]]
+    lats, res = [], []
+    for i in range(len(batches)):
+        nxt = ([srv.submit(k, g, a, want_phi=want_phi) for k, g, a in batches[i + 1]]
+               if i + 1 < len(batches) else [])
+        for t in pend:
+            r, _ = srv.poll(t, 600000)
+            res.append(r)
+            lats.append(r.seconds)
+        pend = nxt
+    return time.perf_counter() - t0, lats, res
+
+
 class PlainFP64:
     """One request at a time: per-trajectory grid, setup, FP64 Jacobi-PCG from
     phi0 = 0, energy (pb_pcg_solve)."""
@@ -258,32 +276,27 @@ def run_serving(args):
     st0 = ctx.stats()
     clocks = ClockSampler(local)
     clocks.start()
-    walls, lats, iters = [], [], []
-    for _ in range(args.steps):
-        reqs = [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
-        w, l, res = serve_batch(srv, reqs)
-        walls.append(w)
-        lats += l
-        iters += [r.info.iterations for r in res]
-        bad = [r.status for r in res if r.status != 0]
-        if bad:
-            raise RuntimeError(f"served requests failed: {bad[:5]}")
+    batches = [[(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
+               for _ in range(args.steps)]
+    total, lats, res = serve_steps(srv, batches)
+    iters = [r.info.iterations for r in res]
+    bad = [r.status for r in res if r.status != 0]
+    if bad:
+        raise RuntimeError(f"served requests failed: {bad[:5]}")
     clk = clocks.stop()
     torch.cuda.synchronize()
     st1 = ctx.stats()
-    total = sum(walls)
     if world > 1:
         t = torch.tensor([total], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total = float(t[0])
-    # end to end: the same steps with phi copied back to the host per request
-    e2e_walls, e2e0 = [], ctx.stats()
-    for _ in range(max(1, args.steps // 2)):
-        reqs = [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
-        w, _, _ = serve_batch(srv, reqs, want_phi=True)
-        e2e_walls.append(w)
+    # end to end: the same steady state with phi copied back to the host per request
+    e2e_steps = max(2, args.steps // 2)
+    e2e0 = ctx.stats()
+    e2e_wall, _, _ = serve_steps(srv, [[(k, g.replace(dh="f32"), a) for k, g, a in
+                                        stream.take(per_step)] for _ in range(e2e_steps)],
+                                 want_phi=True)
     e2e1 = ctx.stats()
-    e2e_steps = len(e2e_walls)
     # plain FP64, one at a time, on the same kind of requests (fresh trajectories)
     plain = PlainFP64(pb, ctx, torch)
     pstream = Stream(seed=5, req_seed=98 + 1000 * rank)
@@ -368,7 +381,8 @@ def run_serving(args):
                    "l2": "inputs larger than L2 (2.1 M nodes mean per request, 64 per step)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": pct([1e3 * x for x in lats], 50), "p99": pct([1e3 * x for x in lats], 99),
-                       "note": "closed loop: 64 requests submitted at once, submit -> result"},
+                       "note": "steady state: 64 requests per step, the next step queued while "
+                               "this one completes; submit -> result"},
         "iterations_mean": float(np.mean(iters)),
         "fp64_plain": {"value": plain_rate, "unit": "solves/s",
                        "latency_ms": {"p50": pct([1e3 * x for x in p_lat], 50),
@@ -394,7 +408,7 @@ def run_serving(args):
                      "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
                                      "bytes_per_node": BYTES_PER_NODE["update"],
                                      "launch_ms": t_up * 1e3, "launches": kp.launches_update}},
-        "e2e": {"value": world * e2e_steps * per_step / sum(e2e_walls), "unit": "solves/s",
+        "e2e": {"value": world * e2e_steps * per_step / e2e_wall, "unit": "solves/s",
                 "h2d_bytes_per_step": int((e2e1[1] - e2e0[1]) / e2e_steps),
                 "d2h_bytes_per_step": int((e2e1[2] - e2e0[2]) / e2e_steps),
                 "note": "same steps with phi copied to host memory per request"},
