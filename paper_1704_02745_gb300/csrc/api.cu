@@ -146,7 +146,7 @@ void pb_grid_release(pb_grid *g) {
   if (g->graph) cudaGraphExecDestroy(g->graph);
   void *ptrs[] = {g->code, g->b, g->ghost, g->xyzq, g->xyzr, g->err, g->counts, g->scratch, g->ex, g->ey,
                   g->ez, g->diag, g->ex64, g->ey64, g->ez64, g->diag64, g->x64, g->x64b, g->d32,
-                  g->r32, g->p032, g->p132, g->ap32, g->r64, g->p064, g->p164, g->ap64,
+                  g->z32, g->p032, g->p132, g->ap32, g->z64, g->p064, g->p164, g->ap64,
                   g->own_scal ? (void *)g->scal : nullptr, g->dinst, g->st_items, g->ch_items, g->st_part,
                   g->ch_part};
   for (void *p : ptrs) dfree(p);
@@ -164,7 +164,8 @@ extern "C" pb_status pb_free_grid(pb_grid *g) {
 // Stencil tiles: the fewest x tiles of width <= WMAX, then the tallest H with
 // W*H <= NV*NT, then z chunks so that all tiles fit in one wave of resident CTAs.
 // batch = true (grids of a server): z chunks of at least 32 planes and update
-// chunks of at least 4*CH elements, since many grids share each launch.
+// chunks of at least 16*CH elements, since many grids share each launch and
+// each chunk ends with a CTA-wide reduction.
 void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
   g->tiles_x = (nx + WMAX - 1) / WMAX;
@@ -183,7 +184,7 @@ void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   // fewer than CH elements per chunk
   const long rows = (long)ny * nz;
   const long by_count = (rows + kg.update_blocks - 1) / kg.update_blocks;
-  g->rows_per_chunk = (int)std::max<long>(std::max(1, (batch ? 4 * CH : CH) / nx), by_count);
+  g->rows_per_chunk = (int)std::max<long>(std::max(1, (batch ? 16 * CH : CH) / nx), by_count);
   g->n_ch = (int)((rows + g->rows_per_chunk - 1) / g->rows_per_chunk);
 }
 
@@ -306,7 +307,11 @@ pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_g
   ALLOC(g->b, g->n_pad * sizeof(double));
   ALLOC(g->ghost, g->n_ghost * sizeof(double));
   ALLOC(g->err, sizeof(int) * 4);
-  ALLOC(g->counts, sizeof(int) * 2);
+  ALLOC(g->counts, sizeof(int) * 8);  // item counts, then the work counters
+  if (cudaMemset(g->counts, 0, sizeof(int) * 8) != cudaSuccess) {
+    pb_grid_release(g);
+    return pb_fail(PB_ERR_CUDA, "clear work counters");
+  }
   if (desc->coef != PB_COEF_PACKED) {
     const size_t nc = (size_t)px * (desc->ny + 1) * (desc->nz + 1);
     if (desc->coef == PB_COEF_F64) {
@@ -379,13 +384,13 @@ pb_status pb_ensure_workspace(pb_grid *g, int mode) {
   if ((st = alloc0((void **)&g->x64, n * 8))) return st;
   if ((st = alloc0((void **)&g->x64b, n * 8))) return st;
   if (mode == MODE_F64) {
-    if ((st = alloc0((void **)&g->r64, n * 8))) return st;
+    if ((st = alloc0((void **)&g->z64, n * 8))) return st;
     if ((st = alloc0((void **)&g->p064, n * 8))) return st;
     if ((st = alloc0((void **)&g->p164, n * 8))) return st;
     if ((st = alloc0((void **)&g->ap64, n * 8))) return st;
   } else {
     if ((st = alloc0(&g->d32, n * 4))) return st;
-    if ((st = alloc0(&g->r32, n * 4))) return st;
+    if ((st = alloc0(&g->z32, n * 4))) return st;
     if ((st = alloc0(&g->p032, n * 4))) return st;
     if ((st = alloc0(&g->p132, n * 4))) return st;
     if ((st = alloc0(&g->ap32, n * 4))) return st;
@@ -470,9 +475,9 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   I.x64 = g->x64; I.x64b = g->x64b;
   I.b = g->b;
   if (mode == MODE_F64) {
-    I.d = nullptr; I.r = g->r64; I.p0 = g->p064; I.p1 = g->p164; I.ap = g->ap64;
+    I.d = nullptr; I.z = g->z64; I.p0 = g->p064; I.p1 = g->p164; I.ap = g->ap64;
   } else {
-    I.d = g->d32; I.r = g->r32; I.p0 = g->p032; I.p1 = g->p132; I.ap = g->ap32;
+    I.d = g->d32; I.z = g->z32; I.p0 = g->p032; I.p1 = g->p132; I.ap = g->ap32;
   }
   I.s = g->scal;
   const double ein = g->d.eps_in, eout = g->d.eps_out;
@@ -507,7 +512,7 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const void *x0 = mode == MODE_F64 ? (const void *)g->x64 : g->d32;
   const void *x1 = mode == MODE_F64 ? (const void *)g->x64b : g->d32;
-  if (!encode_map(&I.tm_r, I.r, dt, es, g, L.rw, L.rows) ||
+  if (!encode_map(&I.tm_z, I.z, dt, es, g, L.rw, L.rows) ||
       !encode_map(&I.tm_p0, I.p0, dt, es, g, L.rw, L.rows) ||
       !encode_map(&I.tm_p1, I.p1, dt, es, g, L.rw, L.rows) ||
       !encode_map(&I.tm_code, g->code, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, L.cw, L.rows) ||
@@ -565,6 +570,7 @@ Batch pb_single_batch(pb_grid *g) {
   B.st_items = g->st_items;
   B.ch_items = g->ch_items;
   B.n_items = g->counts;
+  B.work = (unsigned *)(g->counts + 4);
   B.st_part = g->st_part;
   B.ch_part = g->ch_part;
   B.error = g->err;

@@ -38,8 +38,8 @@ struct pb_grid {
   void *ex64 = nullptr, *ey64 = nullptr, *ez64 = nullptr, *diag64 = nullptr;
   // solve workspace
   double *x64 = nullptr, *x64b = nullptr;
-  void *d32 = nullptr, *r32 = nullptr, *p032 = nullptr, *p132 = nullptr, *ap32 = nullptr;
-  double *r64 = nullptr, *p064 = nullptr, *p164 = nullptr, *ap64 = nullptr;
+  void *d32 = nullptr, *z32 = nullptr, *p032 = nullptr, *p132 = nullptr, *ap32 = nullptr;
+  double *z64 = nullptr, *p064 = nullptr, *p164 = nullptr, *ap64 = nullptr;
   pb::Scal *scal = nullptr;  // own allocation, or a slot of a server's scalar array
   bool own_scal = true;
   int *counts = nullptr;     // device: stencil and update item counts of the single-grid batch

@@ -11,7 +11,8 @@
 //                                pad bytes are 0
 //   b      f64    [nz][ny][px]   right-hand side of Eq. (4) with the boundary folded in
 //   x64    f64    [nz][ny][px]   solution (FP64)
-//   d,r,p0,p1,ap  T [nz][ny][px] CG work vectors in the inner precision T
+//   d,z,p0,p1,ap  T [nz][ny][px] CG work vectors in the inner precision T: inner
+//                                x increment, z = M^-1 r, directions, A p
 //   ex     C      [nz][ny][px]   explicit modes only: edge (i-1, i) at column i, i = 0..nx
 //   ey     C      [nz][ny+1][px] edge (j-1, j) at row j
 //   ez     C      [nz+1][ny][px] edge (k-1, k) at plane k
@@ -69,7 +70,7 @@ struct Scal {
 // Everything a phase kernel needs to know about one instance (one grid).
 // The TMA descriptors come first (64-byte aligned).
 struct alignas(64) Inst {
-  CUtensorMap tm_r, tm_p0, tm_p1, tm_code, tm_x0, tm_x1;  // r, p buffers, codes, inner x
+  CUtensorMap tm_z, tm_p0, tm_p1, tm_code, tm_x0, tm_x1;  // z, p buffers, codes, inner x
   int W, H;                           // stencil tile
   int cw;                             // width of the code box (bytes, multiple of 16)
   int stage_bytes, off_p, off_c, off_x, tma_bytes;  // TMA stage layout and bytes per stage
@@ -86,7 +87,7 @@ struct alignas(64) Inst {
   const void *ex, *ey, *ez, *diag;    // explicit coefficient arrays (inner precision)
   double *x64, *x64b;                 // solution, double-buffered across RESID passes
   const double *b;
-  void *d, *r, *p0, *p1, *ap;         // inner work vectors
+  void *d, *z, *p0, *p1, *ap;         // inner work vectors (z = M^-1 r)
   Scal *s;
   const int *err;                     // the grid's setup error word
   const double *bnorm2;               // ||b||^2 as the setup left it
@@ -107,6 +108,8 @@ struct Batch {  // device pointers describing a batch of instances
   const Item *ch_items;  // elementwise chunks of all instances
   const int *n_items;    // [0]: stencil items, [1]: update items (device memory, so a
                          // captured device graph serves any active set)
+  unsigned *work;        // [0] next stencil item, [1] stencil CTAs done, [2] next update
+                         // item, [3] update CTAs done: zero between launches
   double *st_part;       // 3 doubles per stencil tile
   double *ch_part;       // 2 doubles per chunk
   int *error;            // device error word

@@ -355,6 +355,23 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
       return false;
     s->ctx->stats->h2d += sizeof(Inst);
   }
+  // Largest items first: the phase kernels take items in list order, so the
+  // small ones fill in at the end of each launch.  (The order changes no
+  // result: each item's partial sum has a fixed place.)
+  auto st_cost = [&](const Item &it) {
+    const pb_grid *g = s->slots[it.inst].g;
+    const int bz = it.tile / (g->tiles_x * g->tiles_y);
+    return (long)g->W * g->H * (std::min(g->tz, g->d.nz - bz * g->tz) + 2);
+  };
+  auto ch_cost = [&](const Item &it) {
+    const pb_grid *g = s->slots[it.inst].g;
+    const long rows = (long)g->d.ny * g->d.nz;
+    return std::min<long>(g->rows_per_chunk, rows - (long)it.tile * g->rows_per_chunk) * g->d.nx;
+  };
+  std::stable_sort(st.begin(), st.end(),
+                   [&](const Item &a, const Item &b) { return st_cost(a) > st_cost(b); });
+  std::stable_sort(ch.begin(), ch.end(),
+                   [&](const Item &a, const Item &b) { return ch_cost(a) > ch_cost(b); });
   const size_t old_st = s->cap_st, old_ch = s->cap_ch;
   Item *ost = s->d_st, *och = s->d_ch;
   if (!grow(&s->d_st, &s->cap_st, std::max<size_t>(st.size(), 1)) ||
@@ -407,6 +424,7 @@ bool run_graph(pb_server *s, bool stale) {
     B.st_items = s->d_st;
     B.ch_items = s->d_ch;
     B.n_items = s->d_counts;
+    B.work = (unsigned *)(s->d_counts + 4);
     B.st_part = s->d_st_part;
     B.ch_part = s->d_ch_part;
     B.error = s->d_err;
@@ -505,6 +523,7 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
   B.st_items = s->d_st;
   B.ch_items = s->d_ch;
   B.n_items = s->d_counts;
+  B.work = (unsigned *)(s->d_counts + 4);
   B.st_part = s->d_st_part;
   B.ch_part = s->d_ch_part;
   B.error = s->d_err;
@@ -663,7 +682,8 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMallocHost((void **)&s->ctx->host_scal, sizeof(Scal) * 64) == cudaSuccess;
   ok = ok && !pb_dalloc((void **)&s->d_scal, MAX_SLOTS * sizeof(Scal));
   ok = ok && !pb_dalloc((void **)&s->d_inst, MAX_SLOTS * sizeof(Inst));
-  ok = ok && !pb_dalloc((void **)&s->d_counts, 2 * sizeof(int));
+  ok = ok && !pb_dalloc((void **)&s->d_counts, 8 * sizeof(int));  // item counts, work counters
+  ok = ok && cudaMemset(s->d_counts, 0, 8 * sizeof(int)) == cudaSuccess;
   ok = ok && !pb_dalloc((void **)&s->d_list, MAX_SLOTS * sizeof(int));
   ok = ok && !pb_dalloc((void **)&s->d_err, 4 * sizeof(int));
   ok = ok && cudaMallocHost((void **)&s->h_scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;

@@ -71,6 +71,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 // Wait for phase `parity` of a barrier, giving up after ~1 s of clock.
 constexpr long long WAIT_CYCLES = 2000000000LL;
+constexpr int CG_RING_PLANES = 4;  // p planes with halo held by a CG stencil pass
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
@@ -142,14 +143,6 @@ __device__ __forceinline__ HaloG halo_g(const Inst &I) {
   return h;
 }
 
-// z = M^-1 r from a code byte (packed) -- or from the explicit diagonal.
-template <typename T, int CM>
-__device__ __forceinline__ T zval_code(const Inst &I, uint32_t code, T r, size_t e) {
-  if (!I.precond) return r;
-  if (CM == COEF_PACKED) return r * tab_i<T>(I, dtab_index(code));
-  return r / ((const T *)I.diag)[e];
-}
-
 // NV-element vectors in 16-byte pieces.
 template <typename T> struct Vec { T v[NV]; };
 template <typename T>
@@ -203,11 +196,12 @@ struct StageRing {
 // INNER phase, stencil pass of one tile (TMA pipeline).  Returns this
 // thread's p.Ap; sets `abort` if a pipeline wait timed out.
 //
-// tab: {diag, 1/diag} of the FP32/FP64 operator for every code byte (1/diag
-// replaced by 1 without preconditioner), built in shared memory per item.
+// The update pass stores z = M^-1 r, so the new direction p = z + beta p_old
+// is one fused multiply-add per node, halo included.  dtab: the diagonal of
+// the FP32/FP64 operator for every code byte, in shared memory per item.
 template <typename T, int CM, int NS>
 __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int tile,
-                                          uint8_t *stages, T *ring, const Pair<T> *tab,
+                                          uint8_t *stages, T *ring, const T *dtab,
                                           uint64_t *full, StageRing &SR, bool &abort) {
   constexpr bool SEP = sizeof(T) == 4;  // FP32 inner solves accumulate into d
   const TileG G = tile_g(I, tile);
@@ -218,7 +212,6 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
   // statements of the pipeline clobber memory, which would force reloads)
   const uint32_t stage_bytes = I.stage_bytes, off_p = I.off_p, off_c = I.off_c, off_x = I.off_x;
   const uint32_t tma_bytes = I.tma_bytes;
-  const int nzg = I.nz;
   const int cx0 = ((G.x0 - 1) >> 4) << 4;  // code box start: 16-byte aligned, <= x0 - 1
   const int Q = (G.z1 - G.z0) + 2;         // planes z0-1 .. z1
   const bool first = S.phase == PH_START;
@@ -238,7 +231,7 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
     uint8_t *sb = stages + st * stage_bytes;
     const int z = G.z0 - 1 + q;
     mbar_expect_tx(&full[st], tma_bytes);
-    tma_load_3d(sb, &I.tm_r, &full[st], G.x0 - NV, G.y0 - 1, z);
+    tma_load_3d(sb, &I.tm_z, &full[st], G.x0 - NV, G.y0 - 1, z);
     tma_load_3d(sb + off_p, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
     tma_load_3d(sb + off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
     tma_load_3d(sb + off_x, m_x, &full[st], G.x0, G.y0, z);
@@ -257,16 +250,14 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
   const int cg = (G.ty + 1) * RGW + NV + G.tx;
   const int cx = G.ty * W + G.tx;
   const int hr = (Hh.hy + 1) * RW + NV + Hh.hx;
-  const int hc = (Hh.hy + 1) * CW + (G.x0 + Hh.hx - cx0);
   const int hg = (Hh.hy + 1) * RGW + NV + Hh.hx;
-  const int hi = G.x0 + Hh.hx, hj = G.y0 + Hh.hy;
-  const bool hin = hi >= 0 && hi < I.nx && hj >= 0 && hj < I.ny;
-  const size_t eh0 = hin ? (size_t)hj * I.px + hi : 0;
 
-  Vec<T> pm = {}, pc = {}, po_prev = {}, x_prev = {};
   uint32_t code_prev = 0;
   T acc = 0;
-  int rq = 0, rq1 = 2;  // ring plane of q and of q-1
+  // ring slot of plane q; planes q-1 and q-2 sit in the two slots before it.
+  // A thread writes slot q while a slower one, still in its pass q-1, may
+  // read the slots of q-2 and q-3: hence four slots with one barrier a plane.
+  int rq = 0;
   uint32_t st_issue = SR.st;
   for (int u = 0; u < min(NS, Q); ++u) st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
   for (int q = 0; q < Q; ++q) {
@@ -275,39 +266,40 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
     SR.phase ^= 1u << st;
     SR.st = st + 1 == NS ? 0 : st + 1;
     const uint8_t *sb = stages + st * stage_bytes;
-    const T *sr = (const T *)sb;
+    const T *sz = (const T *)sb;
     const T *sp = (const T *)(sb + off_p);
     const uint8_t *sc = sb + off_c;
     const T *sx = (const T *)(sb + off_x);
     T *rg = ring + rq * ring_plane;
+    const int rq1 = (rq + CG_RING_PLANES - 1) % CG_RING_PLANES, rq2 = (rq + CG_RING_PLANES - 2) % CG_RING_PLANES;
     const int z = G.z0 - 1 + q;
-    const bool zin = z >= 0 && z < nzg;
-    Vec<T> pn = {}, po = {}, xv = {};
+    Vec<T> pn = {};
     uint32_t codes = 0;
+    // z and p_old are zero outside the grid (TMA fill, zero pads), and so is
+    // p; the first direction is z itself, whatever p_old holds
     if (ok && G.in_tile) {
-      const Vec<T> rv = ldv(sr + cr);
-      po = ldv(sp + cr);
-      xv = ldv(sx + cx);
+      pn = ldv(sz + cr);
+      const Vec<T> po = ldv(sp + cr);
       codes = *(const uint32_t *)(sc + cc);
+      if (!first) {
 #pragma unroll
-      for (int u = 0; u < NV; u++) {
-        if (CM == COEF_PACKED) {
-          pn.v[u] = rv.v[u] * tab[(codes >> (8 * u)) & 127u].i + beta * po.v[u];
-        } else if (zin && ((G.vmask >> u) & 1u)) {
-          pn.v[u] = zval_code<T, CM>(I, 0, rv.v[u], (size_t)z * plane + ec0 + u) + beta * po.v[u];
-        }
+        for (int u = 0; u < NV; u++) pn.v[u] += beta * po.v[u];
       }
       stv(rg + cg, pn);
-    }
-    if (ok && Hh.role) {
-      T hv = 0;
-      if (CM == COEF_PACKED) {
-        hv = sr[hr] * tab[sc[hc] & 127u].i + beta * sp[hr];
-      } else if (hin && zin) {
-        hv = zval_code<T, CM>(I, 0, sr[hr], (size_t)z * plane + eh0) + beta * sp[hr];
+      // deferred update of the previous iteration: x += alpha p_old (the
+      // first inner iteration starts the FP32 increment d from zero)
+      if (G.vmask && q >= 1 && q < Q - 1) {
+        Vec<T> xn = {};
+        if (!first) {
+          xn = ldv(sx + cx);
+#pragma unroll
+          for (int u = 0; u < NV; u++) xn.v[u] += alpha * po.v[u];
+        }
+        if (SEP || !first) stv(x, xn);
       }
-      rg[hg] = hv;
     }
+    if (q >= 1 && q < Q - 1) x += plane;
+    if (ok && Hh.role) rg[hg] = first ? sz[hr] : sz[hr] + beta * sp[hr];
     if (__syncthreads_or(!ok)) {
       // A wait gave up: let the copies already issued land, each for a
       // bounded time, before the CTA leaves.
@@ -335,44 +327,54 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
       // of NV)
       if (G.vmask) {
         const T *rm = ring + rq1 * ring_plane;
+        const Vec<T> pc = ldv(rm + cg), pm = ldv(ring + rq2 * ring_plane + cg);
         const Vec<T> ym = ldv(rm + cg - RGW), yp = ldv(rm + cg + RGW);
         const T xl = rm[cg - 1], xr = rm[cg + NV];
-        Vec<T> a, xn;
+        Vec<T> a;
 #pragma unroll
         for (int u = 0; u < NV; u++) {
-          NodeCoef<T> c;
+          const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
+          T av;
           if (CM == COEF_PACKED) {
-            const uint32_t b = (code_prev >> (8 * u)) & 0xffu;
-            c.exm = (b & 1u) ? ei : eo; c.exp = (b & 2u) ? ei : eo;
-            c.eym = (b & 4u) ? ei : eo; c.eyp = (b & 8u) ? ei : eo;
-            c.ezm = (b & 16u) ? ei : eo; c.ezp = (b & 32u) ? ei : eo;
-            c.diag = tab[b & 127u].d;
-          } else if ((G.vmask >> u) & 1u) {
-            c = node_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0 + u, z - 1);
+            // Eq. (3) with the six edge coefficients of the code byte; a node
+            // whose edges all lie on one side (all but the nodes next to the
+            // surface) takes a single coefficient times the neighbour sum
+            const uint32_t b = (code_prev >> (8 * u)) & 0xffu, e6 = b & 63u;
+            const T dg = dtab[b & 127u];
+            if (e6 == 0u || e6 == 63u) {
+              const T s6 = ((pl + pr) + (ym.v[u] + yp.v[u])) + (pm.v[u] + pn.v[u]);
+              av = dg * pc.v[u] - (e6 ? ei : eo) * s6;
+            } else {
+              T s = ((b & 1u) ? ei : eo) * pl;
+              s += ((b & 2u) ? ei : eo) * pr;
+              s += ((b & 4u) ? ei : eo) * ym.v[u];
+              s += ((b & 8u) ? ei : eo) * yp.v[u];
+              s += ((b & 16u) ? ei : eo) * pm.v[u];
+              s += ((b & 32u) ? ei : eo) * pn.v[u];
+              av = dg * pc.v[u] - s;
+            }
           } else {
-            c = NodeCoef<T>{0, 0, 0, 0, 0, 0, 0};
+            NodeCoef<T> c = NodeCoef<T>{0, 0, 0, 0, 0, 0, 0};
+            if ((G.vmask >> u) & 1u) c = node_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0 + u, z - 1);
+            T s = c.exm * pl;
+            s += c.exp * pr;
+            s += c.eym * ym.v[u];
+            s += c.eyp * yp.v[u];
+            s += c.ezm * pm.v[u];
+            s += c.ezp * pn.v[u];
+            av = c.diag * pc.v[u] - s;
           }
-          T s = c.exm * (u == 0 ? xl : pc.v[u - 1]);
-          s += c.exp * (u == NV - 1 ? xr : pc.v[u + 1]);
-          s += c.eym * ym.v[u];
-          s += c.eyp * yp.v[u];
-          s += c.ezm * pm.v[u];
-          s += c.ezp * pn.v[u];
-          T av = c.diag * pc.v[u] - s;
           if (!((G.vmask >> u) & 1u)) av = 0;  // pad columns keep Ap = 0
           a.v[u] = av;
           acc += pc.v[u] * av;
-          xn.v[u] = first ? (T)0 : x_prev.v[u] + alpha * po_prev.v[u];
         }
         stv(pnew, pc);
         stv(ap, a);
-        if (SEP || !first) stv(x, xn);
       }
-      pnew += plane; ap += plane; x += plane;
+      pnew += plane; ap += plane;
     }
-    pm = pc; pc = pn; po_prev = po; x_prev = xv; code_prev = codes;
-    rq1 = rq;
-    rq = rq == 2 ? 0 : rq + 1;
+    code_prev = codes;
+    rq = (rq + 1) % CG_RING_PLANES;
   }
   return (double)acc;
 }
@@ -397,7 +399,7 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
   double *__restrict__ xout = S.xbuf ? I.x64 : I.x64b;
   const T *__restrict__ d = (const T *)I.d;
   const T *__restrict__ p = (const T *)(S.pbuf ? I.p1 : I.p0);
-  T *__restrict__ r = (T *)I.r;
+  T *__restrict__ zo = (T *)I.z;
   // Before the first inner solve there is nothing to fold (d and p unset).
   const bool fold = S.outer > 0;
   auto xn = [&](size_t e) -> double {
@@ -443,10 +445,10 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
       s += c.ezp * xnx[u];
       const double res = I.b[e] - (c.diag * xc[u] - s);
       xout[e] = xc[u];
-      const T rt = (T)res;
-      r[e] = rt;
+      const T rt = (T)res, zt = zval<T, CM>(I, e, rt);
+      zo[e] = zt;
       rr64 += res * res;
-      rz += (double)(rt * zval<T, CM>(I, e, rt));
+      rz += (double)(rt * zt);
     }
 #pragma unroll
     for (int u = 0; u < NV; u++) { xm[u] = xc[u]; xc[u] = xnx[u]; }
@@ -571,8 +573,8 @@ __device__ void fin_resid(const Inst &I, Scal *S, double rr64, double rz) {
 // Ring of three planes with halo, sized for the largest tile in FP64 (the
 // RESID pass).
 constexpr int RING_CELLS = max_ring_cells();
-__host__ __device__ constexpr size_t ring_bytes(size_t es) {
-  return ((size_t)3 * RING_CELLS * es + 127) / 128 * 128;
+__host__ __device__ constexpr size_t ring_bytes(size_t es, int planes = 3) {
+  return ((size_t)planes * RING_CELLS * es + 127) / 128 * 128;
 }
 #ifndef PB_STAGES_F32
 #define PB_STAGES_F32 4  // TMA pipeline depth in z planes, FP32 inner solves
@@ -587,13 +589,32 @@ template <typename T> struct Stages {
   static constexpr int n = sizeof(T) == 4 ? PB_STAGES_F32 : PB_STAGES_F64;
 };
 
-// {diag, 1/diag} by code byte for the operator of precision T (shared memory).
+// Diagonal of the operator of precision T by code byte (shared memory).
 template <typename T>
-__device__ __forceinline__ void build_tab(const Inst &I, Pair<T> *tab) {
+__device__ __forceinline__ void build_dtab(const Inst &I, T *dtab) {
+  if (threadIdx.x < 128) dtab[threadIdx.x] = tab_d<T>(I, dtab_index(threadIdx.x));
+}
+
+// Jacobi preconditioner M by code byte: {M, M^-1} = {diag, 1/diag}, or {1, 1}
+// without preconditioner (shared memory).
+template <typename T>
+__device__ __forceinline__ void build_mtab(const Inst &I, Pair<T> *mtab) {
   if (threadIdx.x < 128) {
     const int k = dtab_index(threadIdx.x);
-    tab[threadIdx.x].d = tab_d<T>(I, k);
-    tab[threadIdx.x].i = I.precond ? tab_i<T>(I, k) : (T)1;
+    mtab[threadIdx.x].d = I.precond ? tab_d<T>(I, k) : (T)1;
+    mtab[threadIdx.x].i = I.precond ? tab_i<T>(I, k) : (T)1;
+  }
+}
+
+// Dynamic item scheduling: a CTA takes the next item of the list from a
+// counter in device memory when it finishes one, so items of unequal cost
+// balance across the SMs.  The last CTA to leave puts the counters back to
+// zero for the next launch (which reads them only after this grid completed).
+__device__ __forceinline__ int take_item(unsigned *next) { return (int)atomicAdd(next, 1u); }
+__device__ __forceinline__ void leave_items(unsigned *next, unsigned *done) {
+  if (atomicAdd(done, 1u) == gridDim.x - 1) {
+    atomicExch(next, 0u);
+    atomicExch(done, 0u);
   }
 }
 
@@ -603,14 +624,14 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
   extern __shared__ __align__(128) uint8_t dyn[];
   __shared__ __align__(8) uint64_t full[NS];
   __shared__ double red[2 * (NT / 32)];
-  __shared__ Pair<T> tab[128];
-  __shared__ int s_phase, s_last, s_inst;
+  __shared__ T dtab[128];
+  __shared__ int s_phase, s_last, s_inst, s_item;
   // TMA destinations must be 16-byte aligned; align the whole region to 128.
   // CG pass: ring of T planes, then the stages.  RESID pass (no TMA): an FP64
   // ring over the same bytes.
   uint8_t *base = (uint8_t *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
   double *ring = (double *)base;
-  uint8_t *stages = base + ring_bytes(sizeof(T));
+  uint8_t *stages = base + ring_bytes(sizeof(T), CG_RING_PLANES);
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; s++) mbar_init(&full[s], 1);
     mbar_fence_init();
@@ -618,11 +639,12 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
   }
   pdl_launch_dependents();
   pdl_wait();
+  if (threadIdx.x == 0) s_item = take_item(&B.work[0]);
   __syncthreads();
   StageRing SR{0u, 0u};
   bool abort = false;
   const int n_items = B.n_items[0];
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  for (int it = s_item; it < n_items; it = s_item) {
     const Item item = B.st_items[it];
     const Inst &I = B.inst[item.inst];
     Scal *Sp = I.s;
@@ -632,20 +654,21 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
       s_phase = *(volatile int *)&Sp->phase;
       s_inst = item.inst;
     }
-    if (new_inst) build_tab<T>(I, tab);
+    if (new_inst) build_dtab<T>(I, dtab);
     __syncthreads();
     const int ph = s_phase;
     if (ph == PH_INNER || ph == PH_START || ph == PH_RESID) {
       const TileScal S = tile_scal(Sp);
       double v0 = 0, v1 = 0;
       if (ph != PH_RESID)
-        v0 = cg_tile<T, CM, NS>(I, S, item.tile, stages, (T *)ring, tab, full, SR, abort);
+        v0 = cg_tile<T, CM, NS>(I, S, item.tile, stages, (T *)ring, dtab, full, SR, abort);
       else
         resid_tile<T, CM>(I, S, item.tile, ring, v0, v1);
       if (abort) {
         if (threadIdx.x == 0) atomicOr(B.error, 2);  // a pipeline wait timed out
         break;
       }
+      if (threadIdx.x == 0) s_item = take_item(&B.work[0]);
       block_sum2<NT>(v0, v1, red);
       if (threadIdx.x == 0) {
         double *part = B.st_part + 2 * (size_t)(I.st_base + item.tile);
@@ -665,9 +688,12 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
           else fin_cg(I, Sp, s0);
         }
       }
+    } else if (threadIdx.x == 0) {
+      s_item = take_item(&B.work[0]);
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0) leave_items(&B.work[0], &B.work[1]);
 }
 
 template <typename T, int CM>
@@ -676,14 +702,15 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
   constexpr int U = 4;  // vectors loaded before any is stored (loads in flight per thread)
   typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type VT;
   __shared__ double red[2 * (NT_UPD / 32)];
-  __shared__ Pair<T> tab[128];
-  __shared__ int s_phase, s_last, s_inst;
+  __shared__ Pair<T> mtab[128];
+  __shared__ int s_phase, s_last, s_inst, s_item;
   if (threadIdx.x == 0) s_inst = -1;
   pdl_launch_dependents();
   pdl_wait();
+  if (threadIdx.x == 0) s_item = take_item(&B.work[2]);
   __syncthreads();
   const int n_items = B.n_items[1];
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  for (int it = s_item; it < n_items; it = s_item) {
     const Item item = B.ch_items[it];
     const Inst &I = B.inst[item.inst];
     Scal *Sp = I.s;
@@ -693,7 +720,7 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
       s_phase = *(volatile int *)&Sp->phase;
       s_inst = item.inst;
     }
-    if (new_inst) build_tab<T>(I, tab);
+    if (new_inst) build_mtab<T>(I, mtab);
     __syncthreads();
     if (s_phase == PH_INNER) {
       const T alpha = (T)Sp->alpha;
@@ -702,14 +729,14 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
       const int row0 = item.tile * I.rows_per_chunk;
       const uint32_t nrows = (uint32_t)min(I.rows_per_chunk, I.ny * I.nz - row0);
       const uint32_t nvec = nrows * vx;
-      T *__restrict__ r = (T *)I.r + (size_t)row0 * I.px;
+      T *__restrict__ zp = (T *)I.z + (size_t)row0 * I.px;
       const T *__restrict__ ap = (const T *)I.ap + (size_t)row0 * I.px;
       const uint8_t *__restrict__ code = I.code + (size_t)row0 * I.px;
       const uint32_t px = I.px;
       T rz = 0, rr = 0;
       for (uint32_t f0 = threadIdx.x; f0 < nvec; f0 += U * NT_UPD) {
         uint32_t e[U];
-        VT rv[U], av[U];
+        VT zv[U], av[U];
         uint32_t codes[U];
 #pragma unroll
         for (int k = 0; k < U; k++) {
@@ -717,7 +744,7 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
           const uint32_t row = vx == 1 ? f : __umulhi(f, magic);
           e[k] = row * px + (f - row * vx) * V;
           if (f < nvec) {
-            rv[k] = *(const VT *)(r + e[k]);
+            zv[k] = *(const VT *)(zp + e[k]);
             av[k] = __ldcs((const VT *)(ap + e[k]));
             codes[k] = V == 4 ? *(const uint32_t *)(code + e[k]) : *(const uint16_t *)(code + e[k]);
           }
@@ -725,21 +752,29 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
 #pragma unroll
         for (int k = 0; k < U; k++) {
           if (f0 + k * NT_UPD >= nvec) break;
-          T *rp = (T *)&rv[k];
+          T *zk = (T *)&zv[k];
           const T *apv = (const T *)&av[k];
 #pragma unroll
           for (int u = 0; u < V; u++) {
-            rp[u] = rp[u] - alpha * apv[u];
-            T z;
-            if (CM == COEF_PACKED) z = rp[u] * tab[(codes[k] >> (8 * u)) & 127u].i;
-            else z = zval_code<T, CM>(I, 0, rp[u], (size_t)row0 * px + e[k] + u);
-            rz += rp[u] * z;
-            rr += rp[u] * rp[u];
+            // r = M z - alpha A p, then z = M^-1 r (pads: z = Ap = 0 stay 0)
+            T m, mi = (T)1;
+            if (CM == COEF_PACKED) {
+              const Pair<T> t = mtab[(codes[k] >> (8 * u)) & 127u];
+              m = t.d;
+              mi = t.i;
+            } else {
+              m = I.precond ? ((const T *)I.diag)[(size_t)row0 * px + e[k] + u] : (T)1;
+            }
+            const T r = m * zk[u] - alpha * apv[u];
+            zk[u] = CM == COEF_PACKED ? r * mi : r / m;
+            rz += r * zk[u];
+            rr += r * r;
           }
-          *(VT *)(r + e[k]) = rv[k];
+          *(VT *)(zp + e[k]) = zv[k];
         }
       }
       double a = (double)rz, b = (double)rr;
+      if (threadIdx.x == 0) s_item = take_item(&B.work[2]);
       block_sum2<NT_UPD>(a, b, red);
       if (threadIdx.x == 0) {
         double *part = B.ch_part + 2 * (size_t)(I.ch_base + item.tile);
@@ -756,9 +791,12 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
         sum_partials<NT_UPD>(B.ch_part + 2 * (size_t)I.ch_base, I.n_ch, s0, s1, red);
         if (threadIdx.x == 0) fin_update(I, Sp, s0, s1);
       }
+    } else if (threadIdx.x == 0) {
+      s_item = take_item(&B.work[2]);
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0) leave_items(&B.work[2], &B.work[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -802,7 +840,7 @@ cudaError_t launch_start(const Inst *inst, const int *list, int n, cudaStream_t 
 
 size_t stencil_smem_bytes(int elem_size) {
   const int ns = elem_size == 4 ? Stages<float>::n : Stages<double>::n;
-  const size_t cg = ring_bytes(elem_size) + (size_t)ns * max_stage_bytes(elem_size);
+  const size_t cg = ring_bytes(elem_size, CG_RING_PLANES) + (size_t)ns * max_stage_bytes(elem_size);
   const size_t resid = ring_bytes(sizeof(double));
   return 128 + (cg > resid ? cg : resid);  // + alignment slack
 }
