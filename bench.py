@@ -47,12 +47,12 @@ WORKLOADS = {
 }
 # Algorithmic HBM bytes per grid node of one launch of each phase kernel
 # (FP32 inner solve, packed one-byte coefficients):
-#   stencil pass: read r, p_old, d (4 B each) and the code byte; write p, Ap, d
-#   update pass:  read r, Ap and the code byte; write r
+#   stencil pass: read z = M^-1 r, p_old, d (4 B each) and the code byte; write p, Ap, d
+#   update pass:  read z, Ap and the code byte; write z
 BYTES_PER_NODE = {"stencil": 4 + 4 + 4 + 1 + 4 + 4 + 4, "update": 4 + 4 + 1 + 4}
 # DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
 # profiles/ (None until a capture of the current kernel exists).
-NCU_TRAFFIC_PER_NODE = {"stencil": (244.852992e6 + 158.896384e6) / 16974593}  # k_stencil_globule257.md
+NCU_TRAFFIC_PER_NODE = {"stencil": None}
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
 
 
@@ -407,7 +407,11 @@ def run_serving(args):
                      "measured": "one serving step, each kernel between CUDA events",
                      "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
                                      "bytes_per_node": BYTES_PER_NODE["update"],
-                                     "launch_ms": t_up * 1e3, "launches": kp.launches_update}},
+                                     "launch_ms": t_up * 1e3, "launches": kp.launches_update},
+                     "resid_pass": {"achieved": kp.bytes_resid / max(kp.ms_resid, 1e-12) / 1e6,
+                                    "bytes_per_node": 37, "note": "FP64 arithmetic",
+                                    "launch_ms": kp.ms_resid / max(kp.launches_resid, 1),
+                                    "launches": kp.launches_resid}},
         "e2e": {"value": world * e2e_steps * per_step / e2e_wall, "unit": "solves/s",
                 "h2d_bytes_per_step": int((e2e1[1] - e2e0[1]) / e2e_steps),
                 "d2h_bytes_per_step": int((e2e1[2] - e2e0[2]) / e2e_steps),

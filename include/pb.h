@@ -263,12 +263,15 @@ pb_status pb_server_stats(pb_server *server, int *queued, int *active, int *resi
  * launches each phase kernel on its own between CUDA events (slower, for
  * measurement) and sums, per kind of launch, the device time and the
  * algorithmic HBM bytes of the grids active in it: per grid node, 25 B for a
- * CG stencil pass, 37 B for an FP64 residual pass, 13 B for an update pass
- * (FP32 inner solves with one-byte coefficients; FP64 solves: 49, 37, 25). */
+ * CG stencil pass, 13 B for an update pass, 37 B for an FP64 residual pass
+ * (FP32 inner solves with one-byte coefficients; FP64 solves: 49, 25, 37).
+ * Launches with no grid in the phase they serve are not counted. */
 typedef struct {
-    double ms_stencil, bytes_stencil;  /* stencil-kernel launches (CG and residual work) */
-    double ms_update, bytes_update;    /* update-kernel launches */
+    double ms_stencil, bytes_stencil;  /* CG stencil-pass launches */
+    double ms_update, bytes_update;    /* update-pass launches */
     int launches_stencil, launches_update;
+    double ms_resid, bytes_resid;      /* residual-pass launches */
+    int launches_resid;
 } pb_kernel_profile;
 pb_status pb_server_profile_begin(pb_server *server);
 pb_status pb_server_profile_end(pb_server *server, pb_kernel_profile *out);

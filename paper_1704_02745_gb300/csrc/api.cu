@@ -307,8 +307,8 @@ pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_g
   ALLOC(g->b, g->n_pad * sizeof(double));
   ALLOC(g->ghost, g->n_ghost * sizeof(double));
   ALLOC(g->err, sizeof(int) * 4);
-  ALLOC(g->counts, sizeof(int) * 8);  // item counts, then the work counters
-  if (cudaMemset(g->counts, 0, sizeof(int) * 8) != cudaSuccess) {
+  ALLOC(g->counts, sizeof(int) * PB_COUNTS);
+  if (cudaMemset(g->counts, 0, sizeof(int) * PB_COUNTS) != cudaSuccess) {
     pb_grid_release(g);
     return pb_fail(PB_ERR_CUDA, "clear work counters");
   }
@@ -571,6 +571,7 @@ Batch pb_single_batch(pb_grid *g) {
   B.ch_items = g->ch_items;
   B.n_items = g->counts;
   B.work = (unsigned *)(g->counts + 4);
+  B.resid_pending = g->counts + 2;
   B.st_part = g->st_part;
   B.ch_part = g->ch_part;
   B.error = g->err;
@@ -615,7 +616,7 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
     g->graph_ticks = ticks;
   }
   CK(cudaGraphLaunch(g->graph, s));
-  g->ctx->stats->launches += 2ull * ticks;
+  g->ctx->stats->launches += 3ull * ticks;
   return PB_OK;
 }
 
@@ -635,8 +636,8 @@ static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, p
   memset(&acc, 0, sizeof(acc));
   int phase = PH_RESID;
   pb_status st = PB_OK;
-  for (long t = 0; t < 2 * max_ticks; t++) {
-    const int which = (t & 1) ? 2 : 1;
+  for (long t = 0; t < 3 * max_ticks; t++) {
+    const int which = t % 3 == 0 ? 4 : t % 3 == 1 ? 1 : 2;
     cudaError_t e = cudaEventRecord(e0, s);
     if (!e) e = launch_phase(B, mode, coef, kg, which, s);
     if (!e) e = cudaEventRecord(e1, s);
@@ -650,9 +651,10 @@ static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, p
     }
     g->ctx->stats->launches += 1;
     g->ctx->stats->d2h += sizeof(Scal);
-    if (which == 1) {
+    if (which == 4) {
       if (phase == PH_RESID) { acc.ms_resid += ms; acc.n_resid++; }
-      else if (phase != PH_DONE) { acc.ms_stencil += ms; acc.n_stencil++; }
+    } else if (which == 1) {
+      if (phase == PH_START || phase == PH_INNER) { acc.ms_stencil += ms; acc.n_stencil++; }
     } else if (phase == PH_INNER) {
       acc.ms_update += ms;
       acc.n_update++;
@@ -698,7 +700,9 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(g->scal, &S0, sizeof(Scal), cudaMemcpyHostToDevice, s));
-  g->ctx->stats->h2d += sizeof(Inst) + sizeof(Scal);
+  static const int one_pending = 1;  // the solve opens with a residual pass
+  CK(cudaMemcpyAsync(g->counts + 2, &one_pending, sizeof(int), cudaMemcpyHostToDevice, s));
+  g->ctx->stats->h2d += sizeof(Inst) + sizeof(Scal) + sizeof(int);
   if (o->warm_start) {
     CK(launch_pack(phi, g->x64, g->d.nx, g->d.ny, g->d.nz, g->g.px, s));
     g->ctx->stats->launches += 1;

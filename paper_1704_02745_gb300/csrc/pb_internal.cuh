@@ -102,6 +102,10 @@ struct Item {  // one unit of work of a phase kernel
   int tile;
 };
 
+// Ints of the count block of a batch: [0] stencil items, [1] update items,
+// [2] residual passes pending, [3] unused, [4..9] work counters.
+constexpr int PB_COUNTS = 12;
+
 struct Batch {  // device pointers describing a batch of instances
   const Inst *inst;
   const Item *st_items;  // stencil tiles of all instances
@@ -109,7 +113,9 @@ struct Batch {  // device pointers describing a batch of instances
   const int *n_items;    // [0]: stencil items, [1]: update items (device memory, so a
                          // captured device graph serves any active set)
   unsigned *work;        // [0] next stencil item, [1] stencil CTAs done, [2] next update
-                         // item, [3] update CTAs done: zero between launches
+                         // item, [3] update CTAs done, [4] next residual item, [5]
+                         // residual CTAs done: zero between launches
+  int *resid_pending;    // instances waiting for a residual pass (0 skips the pass)
   double *st_part;       // 3 doubles per stencil tile
   double *ch_part;       // 2 doubles per chunk
   int *error;            // device error word

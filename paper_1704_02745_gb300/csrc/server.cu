@@ -425,6 +425,8 @@ bool run_graph(pb_server *s, bool stale) {
     B.ch_items = s->d_ch;
     B.n_items = s->d_counts;
     B.work = (unsigned *)(s->d_counts + 4);
+    B.resid_pending = s->d_counts + 2;
+  B.resid_pending = s->d_counts + 2;
     B.st_part = s->d_st_part;
     B.ch_part = s->d_ch_part;
     B.error = s->d_err;
@@ -438,7 +440,7 @@ bool run_graph(pb_server *s, bool stale) {
     if (!cuda_ok(e, s, "instantiate")) return false;
   }
   if (!cuda_ok(cudaGraphLaunch(s->graph, s->stream), s, "graph launch")) return false;
-  s->ctx->stats->launches += 2ull * s->ticks;
+  s->ctx->stats->launches += 3ull * s->ticks;
   return true;
 }
 
@@ -497,17 +499,19 @@ void complete(pb_server *s, const std::vector<int> &fin) {
   s->cv_done.notify_all();
 }
 
-// Algorithmic bytes of one launch over the active grids, from their phases.
-double launch_bytes(pb_server *s, const std::vector<int> &active, bool stencil) {
+// Algorithmic bytes of one launch (which: 4 residual, 1 stencil, 2 update
+// pass) over the active grids, from their phases.
+double launch_bytes(pb_server *s, const std::vector<int> &active, int which) {
   const bool f64 = s->mode == MODE_F64;
   double b = 0;
   for (int j : active) {
     const pb_grid *g = s->slots[j].g;
     const double n = (double)g->d.nx * g->d.ny * g->d.nz;
     const int ph = s->h_scal[j].phase;
-    if (stencil) {
+    if (which == 4) {
+      if (ph == PH_RESID) b += n * 37;
+    } else if (which == 1) {
       if (ph == PH_INNER || ph == PH_START) b += n * (f64 ? 49 : 25);
-      else if (ph == PH_RESID) b += n * 37;
     } else if (ph == PH_INNER) {
       b += n * (f64 ? 25 : 13);
     }
@@ -524,17 +528,18 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
   B.ch_items = s->d_ch;
   B.n_items = s->d_counts;
   B.work = (unsigned *)(s->d_counts + 4);
+  B.resid_pending = s->d_counts + 2;
   B.st_part = s->d_st_part;
   B.ch_part = s->d_ch_part;
   B.error = s->d_err;
   const int hi = *std::max_element(active.begin(), active.end()) + 1;
-  for (int t = 0; t < 2 * s->ticks; t++) {
-    const bool st = (t & 1) == 0;
+  for (int t = 0; t < 3 * s->ticks; t++) {
+    const int which = t % 3 == 0 ? 4 : t % 3 == 1 ? 1 : 2;
     cudaMemcpyAsync(s->h_scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
     if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "profile")) return false;
-    const double bytes = launch_bytes(s, active, st);
+    const double bytes = launch_bytes(s, active, which);
     cudaEventRecord(s->ev0, s->stream);
-    if (!cuda_ok(launch_phase(B, s->mode, s->coef, s->kg, st ? 1 : 2, s->stream), s, "launch"))
+    if (!cuda_ok(launch_phase(B, s->mode, s->coef, s->kg, which, s->stream), s, "launch"))
       return false;
     cudaEventRecord(s->ev1, s->stream);
     if (!cuda_ok(cudaEventSynchronize(s->ev1), s, "profile")) return false;
@@ -542,7 +547,11 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
     cudaEventElapsedTime(&ms, s->ev0, s->ev1);
     s->ctx->stats->launches += 1;
     if (bytes <= 0) continue;  // nothing of this kind was active
-    if (st) {
+    if (which == 4) {
+      s->prof.ms_resid += ms;
+      s->prof.bytes_resid += bytes;
+      s->prof.launches_resid++;
+    } else if (which == 1) {
       s->prof.ms_stencil += ms;
       s->prof.bytes_stencil += bytes;
       s->prof.launches_stencil++;
@@ -577,7 +586,7 @@ void worker_main(pb_server *s) {
       if (!started.empty()) {
         cudaMemcpyAsync(s->d_list, started.data(), started.size() * sizeof(int),
                         cudaMemcpyHostToDevice, s->stream);
-        launch_start(s->d_inst, s->d_list, (int)started.size(), s->stream);
+        launch_start(s->d_inst, s->d_list, (int)started.size(), s->d_counts + 2, s->stream);
         s->ctx->stats->launches += 1;
       }
       active_changed = false;
@@ -682,8 +691,9 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMallocHost((void **)&s->ctx->host_scal, sizeof(Scal) * 64) == cudaSuccess;
   ok = ok && !pb_dalloc((void **)&s->d_scal, MAX_SLOTS * sizeof(Scal));
   ok = ok && !pb_dalloc((void **)&s->d_inst, MAX_SLOTS * sizeof(Inst));
-  ok = ok && !pb_dalloc((void **)&s->d_counts, 8 * sizeof(int));  // item counts, work counters
-  ok = ok && cudaMemset(s->d_counts, 0, 8 * sizeof(int)) == cudaSuccess;
+  // item counts, residual passes pending, work counters
+  ok = ok && !pb_dalloc((void **)&s->d_counts, PB_COUNTS * sizeof(int));
+  ok = ok && cudaMemset(s->d_counts, 0, PB_COUNTS * sizeof(int)) == cudaSuccess;
   ok = ok && !pb_dalloc((void **)&s->d_list, MAX_SLOTS * sizeof(int));
   ok = ok && !pb_dalloc((void **)&s->d_err, 4 * sizeof(int));
   ok = ok && cudaMallocHost((void **)&s->h_scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;

@@ -509,7 +509,7 @@ __device__ void fin_cg(const Inst &I, Scal *S, double pap) {
   S->phase = PH_INNER;
 }
 
-__device__ void fin_update(const Inst &I, Scal *S, double rz, double rr) {
+__device__ void fin_update(const Inst &I, Scal *S, double rz, double rr, int *resid_pending) {
   S->cnt3 = 0;
   if (!isfinite(rz) || !isfinite(rr)) {
     S->status = 6;
@@ -524,9 +524,11 @@ __device__ void fin_update(const Inst &I, Scal *S, double rz, double rr) {
   const double tol = I.mode == MODE_F32_REFINE ? S->itol : I.tol;
   if (S->relres < tol) {
     S->phase = PH_RESID;
+    atomicAdd(resid_pending, 1);
   } else if (S->total_iter >= I.max_iter) {
     S->status = 5;  // PB_ERR_NOT_CONVERGED
     S->phase = PH_RESID;
+    atomicAdd(resid_pending, 1);
   }
 }
 
@@ -576,17 +578,21 @@ constexpr int RING_CELLS = max_ring_cells();
 __host__ __device__ constexpr size_t ring_bytes(size_t es, int planes = 3) {
   return ((size_t)planes * RING_CELLS * es + 127) / 128 * 128;
 }
+// Stencil pass configurations: TMA pipeline depth in z planes, and resident
+// CTAs per SM the register budget targets.  The FP32 packed-code pass (the one
+// of served and refined solves) runs three CTAs of 256 threads per SM; the
+// passes that also read coefficient arrays need more registers; the FP64
+// pass is held to one CTA per SM by its shared memory.
 #ifndef PB_STAGES_F32
-#define PB_STAGES_F32 4  // TMA pipeline depth in z planes, FP32 inner solves
+#define PB_STAGES_F32 3
 #endif
-#ifndef PB_STAGES_F64
-#define PB_STAGES_F64 3  // ... FP64 solves (larger stages)
+#ifndef PB_MINB_F32
+#define PB_MINB_F32 3
 #endif
-#ifndef PB_STENCIL_MINB
-#define PB_STENCIL_MINB 2  // resident stencil CTAs per SM the register budget targets
-#endif
-template <typename T> struct Stages {
-  static constexpr int n = sizeof(T) == 4 ? PB_STAGES_F32 : PB_STAGES_F64;
+template <typename T, int CM> struct StencilCfg {
+  static constexpr bool lean = sizeof(T) == 4 && CM == COEF_PACKED;
+  static constexpr int stages = lean ? PB_STAGES_F32 : sizeof(T) == 4 ? 4 : 3;
+  static constexpr int minb = lean ? PB_MINB_F32 : sizeof(T) == 4 ? 2 : 1;
 };
 
 // Diagonal of the operator of precision T by code byte (shared memory).
@@ -619,18 +625,17 @@ __device__ __forceinline__ void leave_items(unsigned *next, unsigned *done) {
 }
 
 template <typename T, int CM>
-__global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
-  constexpr int NS = Stages<T>::n;
+__global__ void __launch_bounds__(NT, StencilCfg<T, CM>::minb) k_stencil(Batch B) {
+  constexpr int NS = StencilCfg<T, CM>::stages;
   extern __shared__ __align__(128) uint8_t dyn[];
   __shared__ __align__(8) uint64_t full[NS];
   __shared__ double red[2 * (NT / 32)];
   __shared__ T dtab[128];
   __shared__ int s_phase, s_last, s_inst, s_item;
-  // TMA destinations must be 16-byte aligned; align the whole region to 128.
-  // CG pass: ring of T planes, then the stages.  RESID pass (no TMA): an FP64
-  // ring over the same bytes.
+  // TMA destinations must be 16-byte aligned; align the whole region to 128:
+  // the ring of p planes, then the stages.
   uint8_t *base = (uint8_t *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
-  double *ring = (double *)base;
+  T *ring = (T *)base;
   uint8_t *stages = base + ring_bytes(sizeof(T), CG_RING_PLANES);
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; s++) mbar_init(&full[s], 1);
@@ -657,13 +662,9 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
     if (new_inst) build_dtab<T>(I, dtab);
     __syncthreads();
     const int ph = s_phase;
-    if (ph == PH_INNER || ph == PH_START || ph == PH_RESID) {
+    if (ph == PH_INNER || ph == PH_START) {
       const TileScal S = tile_scal(Sp);
-      double v0 = 0, v1 = 0;
-      if (ph != PH_RESID)
-        v0 = cg_tile<T, CM, NS>(I, S, item.tile, stages, (T *)ring, dtab, full, SR, abort);
-      else
-        resid_tile<T, CM>(I, S, item.tile, ring, v0, v1);
+      double v0 = cg_tile<T, CM, NS>(I, S, item.tile, stages, ring, dtab, full, SR, abort), v1 = 0;
       if (abort) {
         if (threadIdx.x == 0) atomicOr(B.error, 2);  // a pipeline wait timed out
         break;
@@ -683,10 +684,7 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
         __threadfence();
         double s0, s1;
         sum_partials<NT>(B.st_part + 2 * (size_t)I.st_base, I.n_st, s0, s1, red);
-        if (threadIdx.x == 0) {
-          if (ph == PH_RESID) fin_resid(I, Sp, s0, s1);
-          else fin_cg(I, Sp, s0);
-        }
+        if (threadIdx.x == 0) fin_cg(I, Sp, s0);
       }
     } else if (threadIdx.x == 0) {
       s_item = take_item(&B.work[0]);
@@ -694,6 +692,61 @@ __global__ void __launch_bounds__(NT, PB_STENCIL_MINB) k_stencil(Batch B) {
     __syncthreads();
   }
   if (threadIdx.x == 0) leave_items(&B.work[0], &B.work[1]);
+}
+
+// RESID pass of the instances that asked for one (FP64, plain loads).  A
+// launch with none pending returns at once.  The last CTA to leave clears the
+// pending count: every later request comes from a kernel that runs after it.
+template <typename T, int CM>
+__global__ void __launch_bounds__(NT) k_resid(Batch B) {
+  extern __shared__ __align__(128) uint8_t dyn[];
+  __shared__ double red[2 * (NT / 32)];
+  __shared__ int s_phase, s_last, s_item;
+  double *ring = (double *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
+  pdl_launch_dependents();
+  pdl_wait();
+  if (*(volatile int *)B.resid_pending == 0) return;
+  if (threadIdx.x == 0) s_item = take_item(&B.work[4]);
+  __syncthreads();
+  const int n_items = B.n_items[0];
+  for (int it = s_item; it < n_items; it = s_item) {
+    const Item item = B.st_items[it];
+    const Inst &I = B.inst[item.inst];
+    Scal *Sp = I.s;
+    __syncthreads();  // everyone has read s_item
+    if (threadIdx.x == 0) s_phase = *(volatile int *)&Sp->phase;
+    __syncthreads();
+    if (s_phase == PH_RESID) {
+      const TileScal S = tile_scal(Sp);
+      double v0 = 0, v1 = 0;
+      resid_tile<T, CM>(I, S, item.tile, ring, v0, v1);
+      if (threadIdx.x == 0) s_item = take_item(&B.work[4]);
+      block_sum2<NT>(v0, v1, red);
+      if (threadIdx.x == 0) {
+        double *part = B.st_part + 2 * (size_t)(I.st_base + item.tile);
+        part[0] = v0;
+        part[1] = v1;
+        __threadfence();
+        const unsigned prev = atomicAdd(&Sp->cnt2, 1u);
+        s_last = prev == (unsigned)(I.n_st - 1);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        double s0, s1;
+        sum_partials<NT>(B.st_part + 2 * (size_t)I.st_base, I.n_st, s0, s1, red);
+        if (threadIdx.x == 0) fin_resid(I, Sp, s0, s1);
+      }
+    } else if (threadIdx.x == 0) {
+      s_item = take_item(&B.work[4]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && atomicAdd(&B.work[5], 1u) == gridDim.x - 1) {
+    atomicExch(&B.work[4], 0u);
+    atomicExch(&B.work[5], 0u);
+    atomicExch(B.resid_pending, 0);
+  }
 }
 
 template <typename T, int CM>
@@ -789,7 +842,7 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
         __threadfence();
         double s0, s1;
         sum_partials<NT_UPD>(B.ch_part + 2 * (size_t)I.ch_base, I.n_ch, s0, s1, red);
-        if (threadIdx.x == 0) fin_update(I, Sp, s0, s1);
+        if (threadIdx.x == 0) fin_update(I, Sp, s0, s1, B.resid_pending);
       }
     } else if (threadIdx.x == 0) {
       s_item = take_item(&B.work[2]);
@@ -805,7 +858,7 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
 // PB_ERR_ARG; b = 0 ends it at once (the solution is phi = 0); otherwise
 // the FP64 residual pass comes next, from the instance's current x (warm
 // start) or from zero.
-__global__ void k_start(const Inst *inst, const int *list, int n, int cold) {
+__global__ void k_start(const Inst *inst, const int *list, int n, int *resid_pending) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const Inst &I = inst[list[t]];
@@ -824,26 +877,27 @@ __global__ void k_start(const Inst *inst, const int *list, int n, int cold) {
     z.outer = -1;  // marks "phi = 0"
   } else {
     z.phase = PH_RESID;
+    atomicAdd(resid_pending, 1);
   }
   *S = z;
-  (void)cold;
 }
 
-cudaError_t launch_start(const Inst *inst, const int *list, int n, cudaStream_t st) {
+cudaError_t launch_start(const Inst *inst, const int *list, int n, int *resid_pending,
+                         cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_start<<<(n + 127) / 128, 128, 0, st>>>(inst, list, n, 0);
+  k_start<<<(n + 127) / 128, 128, 0, st>>>(inst, list, n, resid_pending);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 
-size_t stencil_smem_bytes(int elem_size) {
-  const int ns = elem_size == 4 ? Stages<float>::n : Stages<double>::n;
-  const size_t cg = ring_bytes(elem_size, CG_RING_PLANES) + (size_t)ns * max_stage_bytes(elem_size);
-  const size_t resid = ring_bytes(sizeof(double));
-  return 128 + (cg > resid ? cg : resid);  // + alignment slack
+template <typename T, int CM>
+static size_t stencil_smem() {  // ring + stages, + alignment slack
+  return 128 + ring_bytes(sizeof(T), CG_RING_PLANES) +
+         (size_t)StencilCfg<T, CM>::stages * max_stage_bytes(sizeof(T));
 }
+static size_t resid_smem() { return 128 + ring_bytes(sizeof(double)); }
 
 // Launch with the programmatic-stream-serialization attribute, so a kernel
 // may be scheduled while its predecessor drains (each waits with
@@ -867,8 +921,9 @@ static cudaError_t launch_pdl(void (*k)(Args...), int blocks, int threads, size_
 template <typename T, int CM>
 static cudaError_t phase_impl(const Batch &B, const KernelGrid &kg, int which, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  if (which & 1)
-    e = launch_pdl(k_stencil<T, CM>, kg.stencil_blocks, NT, stencil_smem_bytes(sizeof(T)), st, B);
+  if (which & 4) e = launch_pdl(k_resid<T, CM>, kg.resid_blocks, NT, resid_smem(), st, B);
+  if (e == cudaSuccess && (which & 1))
+    e = launch_pdl(k_stencil<T, CM>, kg.stencil_blocks, NT, stencil_smem<T, CM>(), st, B);
   if (e == cudaSuccess && (which & 2)) e = launch_pdl(k_update<T, CM>, kg.update_blocks, NT_UPD, 0, st, B);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -885,30 +940,33 @@ cudaError_t launch_phase(const Batch &B, int mode, int coef, const KernelGrid &k
 }
 
 cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg, cudaStream_t st) {
-  return launch_phase(B, mode, coef, kg, 3, st);
+  return launch_phase(B, mode, coef, kg, 7, st);
 }
 
 template <typename T, int CM>
-static void occ(int &s, int &u) {
-  const size_t sm = stencil_smem_bytes(sizeof(T));
+static void occ(int &s, int &u, int &r) {
+  const size_t sm = stencil_smem<T, CM>(), rm = resid_smem();
   cudaFuncSetAttribute(k_stencil<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_resid<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rm);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM>, NT, sm);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&u, k_update<T, CM>, NT_UPD, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_resid<T, CM>, NT, rm);
 }
 
 KernelGrid kernel_grid(int mode, int coef, int num_sms) {
-  int s = 1, u = 1;
+  int s = 1, u = 1, r = 1;
   if (mode == MODE_F64) {
-    if (coef == COEF_F64) occ<double, COEF_F64>(s, u);
-    else occ<double, COEF_PACKED>(s, u);
-  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u);
-  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u);
-  else occ<float, COEF_PACKED>(s, u);
+    if (coef == COEF_F64) occ<double, COEF_F64>(s, u, r);
+    else occ<double, COEF_PACKED>(s, u, r);
+  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u, r);
+  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u, r);
+  else occ<float, COEF_PACKED>(s, u, r);
   KernelGrid kg;
   kg.stencil_per_sm = s > 0 ? s : 1;
   kg.update_per_sm = u > 0 ? u : 1;
   kg.stencil_blocks = num_sms * kg.stencil_per_sm;
   kg.update_blocks = num_sms * kg.update_per_sm;
+  kg.resid_blocks = num_sms * (r > 0 ? r : 1);
   return kg;
 }
 

@@ -6,7 +6,7 @@
 namespace pb {
 
 struct KernelGrid {  // persistent grid sizes of the phase kernels
-  int stencil_blocks, update_blocks;
+  int stencil_blocks, update_blocks, resid_blocks;
   int stencil_per_sm, update_per_sm;  // resident CTAs per SM
 };
 
@@ -50,16 +50,19 @@ constexpr int max_ring_cells() {
     }
   return m;
 }
-size_t stencil_smem_bytes(int elem_size);
 
-// One tick: the stencil pass then the update pass over every instance.
+// One tick: the residual pass (instances that asked for one), the stencil
+// pass, then the update pass over every instance.
 cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg, cudaStream_t st);
-// which: 1 = stencil pass only, 2 = update pass only, 3 = both.
+// which: bit 2 = residual pass, bit 0 = stencil pass, bit 1 = update pass
+// (launched in that order).
 cudaError_t launch_phase(const Batch &B, int mode, int coef, const KernelGrid &kg, int which,
                          cudaStream_t st);
 KernelGrid kernel_grid(int mode, int coef, int num_sms);
-// Start solves on the listed instances from their device-side setup state.
-cudaError_t launch_start(const Inst *inst, const int *list, int n, cudaStream_t st);
+// Start solves on the listed instances from their device-side setup state
+// (each asks for a residual pass: one count in *resid_pending).
+cudaError_t launch_start(const Inst *inst, const int *list, int n, int *resid_pending,
+                         cudaStream_t st);
 
 // ops.cu
 cudaError_t launch_pack(const double *dense, double *padded, int nx, int ny, int nz, int px,

@@ -84,7 +84,9 @@ class Result(ctypes.Structure):
 class KernelProfile(ctypes.Structure):
     _fields_ = [("ms_stencil", ctypes.c_double), ("bytes_stencil", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("bytes_update", ctypes.c_double),
-                ("launches_stencil", ctypes.c_int), ("launches_update", ctypes.c_int)]
+                ("launches_stencil", ctypes.c_int), ("launches_update", ctypes.c_int),
+                ("ms_resid", ctypes.c_double), ("bytes_resid", ctypes.c_double),
+                ("launches_resid", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

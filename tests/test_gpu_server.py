@@ -152,6 +152,7 @@ def test_kernel_profile(pbm, ctx):
     assert all(r.status == 0 for r, _ in res)
     assert kp.launches_stencil > 0 and kp.launches_update > 0
     assert kp.bytes_stencil > 0 and kp.ms_stencil > 0 and kp.ms_update > 0
+    assert kp.launches_resid > 0 and kp.ms_resid > 0 and kp.bytes_resid > 0
     # every update launch covers at most all grids, each at 13 B per node
     total_nodes = sum(p.grid.n for p in probs)
     assert kp.bytes_update <= kp.launches_update * 13 * total_nodes
