@@ -148,7 +148,7 @@ void pb_grid_release(pb_grid *g) {
                   g->ez, g->diag, g->ex64, g->ey64, g->ez64, g->diag64, g->x64, g->x64b, g->d32,
                   g->z32, g->p032, g->p132, g->ap32, g->z64, g->p064, g->p164, g->ap64,
                   g->own_scal ? (void *)g->scal : nullptr, g->dinst, g->st_items, g->ch_items, g->st_part,
-                  g->ch_part};
+                  g->ch_part, g->rs_part};
   for (void *p : ptrs) dfree(p);
   delete g;
 }
@@ -180,6 +180,10 @@ void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   g->tz = (nz + zc - 1) / zc;
   g->tiles_z = (nz + g->tz - 1) / g->tz;
   g->n_st = cols * g->tiles_z;
+  // residual pass (FP64 arithmetic, not memory bound): pieces of RESID_TZ
+  // planes, so that even one grid's pass spreads over every SM
+  g->rtz = std::min(g->tz, RESID_TZ);
+  g->n_rs = cols * ((nz + g->rtz - 1) / g->rtz);
   // update chunks: one wave of resident update CTAs on large grids, never
   // fewer than CH elements per chunk
   const long rows = (long)ny * nz;
@@ -357,7 +361,7 @@ extern "C" size_t pb_grid_bytes(const pb_grid_desc *d, int precision) {
   else if (d->coef == PB_COEF_BF16) bytes += 2 * (n + 2 * nc) + 4 * n;
   bytes += 16 * n;  // x64 pair
   bytes += precision == PB_PREC_F64 ? 32 * n : 20 * n;
-  bytes += n / CH * 16 + n / 256 * 16 + (1 << 16);
+  bytes += n / CH * 16 + n / 256 * 16 + n / 64 + (1 << 16);
   return bytes;
 }
 
@@ -405,6 +409,7 @@ pb_status pb_ensure_workspace(pb_grid *g, int mode) {
     if ((st = pb_dalloc((void **)&g->ch_items, ci.size() * sizeof(Item)))) return st;
     if ((st = pb_dalloc((void **)&g->st_part, 2 * sizeof(double) * g->n_st))) return st;
     if ((st = pb_dalloc((void **)&g->ch_part, 2 * sizeof(double) * g->n_ch))) return st;
+    if ((st = pb_dalloc((void **)&g->rs_part, 2 * sizeof(double) * g->n_rs))) return st;
     const int counts[2] = {g->n_st, g->n_ch};
     if (cudaMemcpy(g->st_items, si.data(), si.size() * sizeof(Item), cudaMemcpyHostToDevice) ||
         cudaMemcpy(g->ch_items, ci.data(), ci.size() * sizeof(Item), cudaMemcpyHostToDevice) ||
@@ -450,6 +455,7 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   I.W = g->W; I.H = g->H;
   I.tiles_x = g->tiles_x; I.tiles_y = g->tiles_y; I.tiles_z = g->tiles_z; I.tz = g->tz;
   I.n_st = g->n_st; I.n_ch = g->n_ch; I.rows_per_chunk = g->rows_per_chunk;
+  I.rtz = g->rtz; I.n_rs = g->n_rs; I.rs_base = 0;
   {
     const uint64_t vx = (uint64_t)(g->d.nx + (mode == MODE_F64 ? 2 : 4) - 1) / (mode == MODE_F64 ? 2 : 4);
     I.vx_magic = vx > 1 ? (uint32_t)(((1ull << 32) + vx - 1) / vx) : 0u;
@@ -572,6 +578,8 @@ Batch pb_single_batch(pb_grid *g) {
   B.n_items = g->counts;
   B.work = (unsigned *)(g->counts + 4);
   B.resid_pending = g->counts + 2;
+  B.resid_list = g->counts + 10;  // holds 0, the grid's only instance
+  B.rs_part = g->rs_part;
   B.st_part = g->st_part;
   B.ch_part = g->ch_part;
   B.error = g->err;

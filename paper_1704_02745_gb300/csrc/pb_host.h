@@ -45,8 +45,9 @@ struct pb_grid {
   int *counts = nullptr;     // device: stencil and update item counts of the single-grid batch
   pb::Inst *dinst = nullptr;
   pb::Item *st_items = nullptr, *ch_items = nullptr;
-  double *st_part = nullptr, *ch_part = nullptr;
+  double *st_part = nullptr, *ch_part = nullptr, *rs_part = nullptr;
   int W = 0, H = 0, tiles_x = 0, tiles_y = 0, tiles_z = 0, tz = 0, n_st = 0, n_ch = 0;
+  int rtz = 0, n_rs = 0;  // residual-pass z pieces
   int rows_per_chunk = 0;
   // cached device graph of `graph_ticks` ticks
   cudaGraphExec_t graph = nullptr;

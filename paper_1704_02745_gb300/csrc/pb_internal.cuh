@@ -39,6 +39,7 @@ constexpr int WMAX = 64;       // widest tile
 constexpr int HMAX = 24;       // tallest tile
 constexpr int NT_UPD = 256;    // threads per update CTA
 constexpr int CH = 2048;       // fewest elements per chunk of the update pass
+constexpr int RESID_TZ = 4;    // z planes per item of the residual pass
 constexpr int NDTAB = 14;      // diagonal table entries: (#inside edges 0..6) x (lambda 0/1)
 constexpr int PITCH_ALIGN = 16;  // node-array pitch in elements (TMA: 16-byte strides for bytes)
 
@@ -80,6 +81,8 @@ struct alignas(64) Inst {
   int tiles_x, tiles_y, tiles_z, tz;  // stencil tile decomposition
   int n_st, n_ch;                     // stencil tiles, elementwise chunks
   int st_base, ch_base;               // offsets into the partial-sum arrays
+  int rtz, n_rs, rs_base;             // residual pass: the stencil tiles cut into z
+                                      // pieces of rtz planes, their count, partials
   int mode, precond, coef, max_iter, max_outer, pad0;
   double tol, inner_tol, bnorm;
   size_t n_pad;                       // nz*ny*px
@@ -103,7 +106,8 @@ struct Item {  // one unit of work of a phase kernel
 };
 
 // Ints of the count block of a batch: [0] stencil items, [1] update items,
-// [2] residual passes pending, [3] unused, [4..9] work counters.
+// [2] residual passes pending, [3] unused, [4..9] work counters, [10] the
+// residual list of a single grid (its instance 0).
 constexpr int PB_COUNTS = 12;
 
 struct Batch {  // device pointers describing a batch of instances
@@ -116,6 +120,8 @@ struct Batch {  // device pointers describing a batch of instances
                          // item, [3] update CTAs done, [4] next residual item, [5]
                          // residual CTAs done: zero between launches
   int *resid_pending;    // instances waiting for a residual pass (0 skips the pass)
+  int *resid_list;       // ... which ones, in the order they asked
+  double *rs_part;       // 2 doubles per residual item
   double *st_part;       // 3 doubles per stencil tile
   double *ch_part;       // 2 doubles per chunk
   int *error;            // device error word

@@ -157,9 +157,10 @@ struct pb_server {
   Scal *d_scal = nullptr, *h_scal = nullptr;
   Inst *d_inst = nullptr;
   int *d_counts = nullptr, *d_list = nullptr, *d_err = nullptr;
+  int *d_rlist = nullptr;  // instances waiting for a residual pass
   Item *d_st = nullptr, *d_ch = nullptr;
-  double *d_st_part = nullptr, *d_ch_part = nullptr;
-  size_t cap_st = 0, cap_ch = 0;
+  double *d_st_part = nullptr, *d_ch_part = nullptr, *d_rs_part = nullptr;
+  size_t cap_st = 0, cap_ch = 0, cap_rs = 0;
   double *d_dense = nullptr;
   size_t cap_dense = 0;
   cudaGraphExec_t graph = nullptr;
@@ -338,7 +339,7 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
   std::vector<int> active;
   for (int j = 0; j < (int)s->slots.size(); j++)
     if (s->slots[j].g && s->slots[j].busy) active.push_back(j);
-  int st_off = 0, ch_off = 0;
+  int st_off = 0, ch_off = 0, rs_off = 0;
   for (int j : active) {
     pb_grid *g = s->slots[j].g;
     Inst I;
@@ -346,6 +347,8 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
     I.s = s->d_scal + j;
     I.st_base = st_off;
     I.ch_base = ch_off;
+    I.rs_base = rs_off;
+    rs_off += g->n_rs;
     for (int t = 0; t < g->n_st; t++) st.push_back(Item{j, t});
     for (int t = 0; t < g->n_ch; t++) ch.push_back(Item{j, t});
     st_off += g->n_st;
@@ -372,6 +375,12 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
                    [&](const Item &a, const Item &b) { return st_cost(a) > st_cost(b); });
   std::stable_sort(ch.begin(), ch.end(),
                    [&](const Item &a, const Item &b) { return ch_cost(a) > ch_cost(b); });
+  const double *old_rs = s->d_rs_part;
+  if (!grow(&s->d_rs_part, &s->cap_rs, 2 * (size_t)std::max(rs_off, 1))) {
+    s->worker_error = "out of device memory for the partial sums";
+    return false;
+  }
+  if (s->d_rs_part != old_rs) *graph_stale = true;
   const size_t old_st = s->cap_st, old_ch = s->cap_ch;
   Item *ost = s->d_st, *och = s->d_ch;
   if (!grow(&s->d_st, &s->cap_st, std::max<size_t>(st.size(), 1)) ||
@@ -426,7 +435,8 @@ bool run_graph(pb_server *s, bool stale) {
     B.n_items = s->d_counts;
     B.work = (unsigned *)(s->d_counts + 4);
     B.resid_pending = s->d_counts + 2;
-  B.resid_pending = s->d_counts + 2;
+    B.resid_list = s->d_rlist;
+    B.rs_part = s->d_rs_part;
     B.st_part = s->d_st_part;
     B.ch_part = s->d_ch_part;
     B.error = s->d_err;
@@ -529,6 +539,8 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
   B.n_items = s->d_counts;
   B.work = (unsigned *)(s->d_counts + 4);
   B.resid_pending = s->d_counts + 2;
+  B.resid_list = s->d_rlist;
+  B.rs_part = s->d_rs_part;
   B.st_part = s->d_st_part;
   B.ch_part = s->d_ch_part;
   B.error = s->d_err;
@@ -586,7 +598,8 @@ void worker_main(pb_server *s) {
       if (!started.empty()) {
         cudaMemcpyAsync(s->d_list, started.data(), started.size() * sizeof(int),
                         cudaMemcpyHostToDevice, s->stream);
-        launch_start(s->d_inst, s->d_list, (int)started.size(), s->d_counts + 2, s->stream);
+        launch_start(s->d_inst, s->d_list, (int)started.size(), s->d_counts + 2, s->d_rlist,
+                     s->stream);
         s->ctx->stats->launches += 1;
       }
       active_changed = false;
@@ -695,6 +708,7 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && !pb_dalloc((void **)&s->d_counts, PB_COUNTS * sizeof(int));
   ok = ok && cudaMemset(s->d_counts, 0, PB_COUNTS * sizeof(int)) == cudaSuccess;
   ok = ok && !pb_dalloc((void **)&s->d_list, MAX_SLOTS * sizeof(int));
+  ok = ok && !pb_dalloc((void **)&s->d_rlist, MAX_SLOTS * sizeof(int));
   ok = ok && !pb_dalloc((void **)&s->d_err, 4 * sizeof(int));
   ok = ok && cudaMallocHost((void **)&s->h_scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
   ok = ok && cudaMemset(s->d_scal, 0, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
@@ -727,7 +741,7 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
     }
   if (s->graph) cudaGraphExecDestroy(s->graph);
   void *ptrs[] = {s->d_scal, s->d_inst, s->d_counts, s->d_list, s->d_err, s->d_st, s->d_ch,
-                  s->d_st_part, s->d_ch_part, s->d_dense};
+                  s->d_st_part, s->d_ch_part, s->d_rs_part, s->d_rlist, s->d_dense};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->h_scal) cudaFreeHost(s->h_scal);

@@ -106,15 +106,16 @@ struct TileG {
   bool row_ok;                 // ... whose row is inside the grid
   uint32_t vmask;              // bit u: node tx+u is inside the grid
 };
-__device__ __forceinline__ TileG tile_g(const Inst &I, int tile) {
+// tz: z planes per tile (I.tz for the CG passes, I.rtz for the residual pass)
+__device__ __forceinline__ TileG tile_g(const Inst &I, int tile, int tz) {
   TileG g;
   const int bx = tile % I.tiles_x, rest = tile / I.tiles_x;
   const int by = rest % I.tiles_y, bz = rest / I.tiles_y;
   const int gw = I.W / NV;
   g.x0 = bx * I.W;
   g.y0 = by * I.H;
-  g.z0 = bz * I.tz;
-  g.z1 = min(g.z0 + I.tz, I.nz);
+  g.z0 = bz * tz;
+  g.z1 = min(g.z0 + tz, I.nz);
   g.tx = (threadIdx.x % gw) * NV;
   g.ty = threadIdx.x / gw;
   g.in_tile = (int)threadIdx.x < gw * I.H;
@@ -204,7 +205,7 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
                                           uint8_t *stages, T *ring, const T *dtab,
                                           uint64_t *full, StageRing &SR, bool &abort) {
   constexpr bool SEP = sizeof(T) == 4;  // FP32 inner solves accumulate into d
-  const TileG G = tile_g(I, tile);
+  const TileG G = tile_g(I, tile, I.tz);
   const HaloG Hh = halo_g(I);
   const int W = I.W, H = I.H, RW = W + 2 * NV, CW = I.cw, RGW = W + 2 * NV;
   const int ring_plane = RGW * (H + 2);
@@ -380,12 +381,16 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
 }
 
 // RESID phase (FP64, plain loads): fold the deferred update, true residual,
-// new inner right-hand side.  Same groups of NV nodes per thread.
+// new inner right-hand side.  Same groups of NV nodes per thread, z pieces of
+// I.rtz planes.  GB300 runs FP64 arithmetic at a small fraction of its FP32
+// rate, so only x and b - A x are FP64: the last inner step d + alpha p is
+// formed in the inner precision (as the next stencil pass would), and the
+// sums r.r and r.z over a thread's nodes too.
 template <typename T, int CM>
 __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int tile, double *ring,
                                            double &rr64, double &rz) {
   constexpr bool SEP = sizeof(T) == 4;
-  const TileG G = tile_g(I, tile);
+  const TileG G = tile_g(I, tile, I.rtz);
   const HaloG Hh = halo_g(I);
   const int RGW = I.W + 2 * NV, H = I.H;
   const int hi = G.x0 + Hh.hx, hj = G.y0 + Hh.hy;
@@ -395,6 +400,7 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
   const size_t eh0 = hvalid ? (size_t)hj * px + hi : 0;
   const int cg = (G.ty + 1) * RGW + NV + G.tx, hg = (Hh.hy + 1) * RGW + NV + Hh.hx;
   const double alpha = S.alpha;
+  const T alpha_t = (T)S.alpha;
   const double *__restrict__ xin = S.xbuf ? I.x64b : I.x64;
   double *__restrict__ xout = S.xbuf ? I.x64 : I.x64b;
   const T *__restrict__ d = (const T *)I.d;
@@ -403,9 +409,9 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
   // Before the first inner solve there is nothing to fold (d and p unset).
   const bool fold = S.outer > 0;
   auto xn = [&](size_t e) -> double {
-    double v = xin[e];
+    const double v = xin[e];
     if (!fold) return v;
-    if (SEP) v += (double)d[e];
+    if (SEP) return v + (double)(d[e] + alpha_t * p[e]);
     return v + alpha * (double)p[e];
   };
   auto group = [&](int k, double *out) {  // x_new of this thread's nodes in plane k
@@ -421,8 +427,7 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
     for (int u = 0; u < NV; u++) ring[cg + u] = xc[u];
   if (Hh.role) ring[hg] = hvalid ? xn((size_t)G.z0 * plane + eh0) : 0.0;
   int cur = 0;
-  rr64 = 0.0;
-  rz = 0.0;
+  T rr_t = 0, rz_t = 0;
   for (int k = G.z0; k < G.z1; ++k) {
     const int nxt = cur == 2 ? 0 : cur + 1;
     double *rn = ring + (size_t)nxt * rsz;
@@ -447,13 +452,15 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
       xout[e] = xc[u];
       const T rt = (T)res, zt = zval<T, CM>(I, e, rt);
       zo[e] = zt;
-      rr64 += res * res;
-      rz += (double)(rt * zt);
+      rr_t += rt * rt;
+      rz_t += rt * zt;
     }
 #pragma unroll
     for (int u = 0; u < NV; u++) { xm[u] = xc[u]; xc[u] = xnx[u]; }
     cur = nxt;
   }
+  rr64 = (double)rr_t;
+  rz = (double)rz_t;
 }
 
 // ---------------------------------------------------------------------------
@@ -509,7 +516,10 @@ __device__ void fin_cg(const Inst &I, Scal *S, double pap) {
   S->phase = PH_INNER;
 }
 
-__device__ void fin_update(const Inst &I, Scal *S, double rz, double rr, int *resid_pending) {
+// inst: the instance's index in the batch, listed for a residual pass when
+// its inner solve ends.
+__device__ void fin_update(const Inst &I, Scal *S, double rz, double rr, int inst,
+                           int *resid_pending, int *resid_list) {
   S->cnt3 = 0;
   if (!isfinite(rz) || !isfinite(rr)) {
     S->status = 6;
@@ -522,13 +532,11 @@ __device__ void fin_update(const Inst &I, Scal *S, double rz, double rr, int *re
   S->total_iter += 1;
   S->relres = sqrt(rr) / S->ref_norm;
   const double tol = I.mode == MODE_F32_REFINE ? S->itol : I.tol;
-  if (S->relres < tol) {
+  const bool end = S->relres < tol || S->total_iter >= I.max_iter;
+  if (S->relres >= tol && end) S->status = 5;  // PB_ERR_NOT_CONVERGED
+  if (end) {
     S->phase = PH_RESID;
-    atomicAdd(resid_pending, 1);
-  } else if (S->total_iter >= I.max_iter) {
-    S->status = 5;  // PB_ERR_NOT_CONVERGED
-    S->phase = PH_RESID;
-    atomicAdd(resid_pending, 1);
+    resid_list[atomicAdd(resid_pending, 1)] = inst;
   }
 }
 
@@ -694,51 +702,67 @@ __global__ void __launch_bounds__(NT, StencilCfg<T, CM>::minb) k_stencil(Batch B
   if (threadIdx.x == 0) leave_items(&B.work[0], &B.work[1]);
 }
 
-// RESID pass of the instances that asked for one (FP64, plain loads).  A
-// launch with none pending returns at once.  The last CTA to leave clears the
-// pending count: every later request comes from a kernel that runs after it.
+// RESID pass of the instances that asked for one (FP64, plain loads).  Its
+// items are the listed instances' z pieces, numbered instance after instance
+// (a CTA maps an item to its instance with a prefix sum of the piece counts
+// in shared memory).  A launch with none pending returns at once.  The last
+// CTA to leave clears the pending count: every later request comes from a
+// kernel that runs after this one.
+constexpr int RESID_LIST_MAX = 1024;  // instances per batch at most
 template <typename T, int CM>
 __global__ void __launch_bounds__(NT) k_resid(Batch B) {
   extern __shared__ __align__(128) uint8_t dyn[];
   __shared__ double red[2 * (NT / 32)];
-  __shared__ int s_phase, s_last, s_item;
+  __shared__ int s_cum[RESID_LIST_MAX + 1], s_inst[RESID_LIST_MAX];
+  __shared__ int s_last, s_item;
   double *ring = (double *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
   pdl_launch_dependents();
   pdl_wait();
-  if (*(volatile int *)B.resid_pending == 0) return;
+  const int n_list = min(*(volatile int *)B.resid_pending, RESID_LIST_MAX);
+  if (n_list == 0) return;
+  for (int t = threadIdx.x; t < n_list; t += NT) {
+    const int j = B.resid_list[t];
+    s_inst[t] = j;
+    s_cum[t + 1] = B.inst[j].n_rs;
+  }
   if (threadIdx.x == 0) s_item = take_item(&B.work[4]);
   __syncthreads();
-  const int n_items = B.n_items[0];
+  if (threadIdx.x == 0) {
+    s_cum[0] = 0;
+    for (int t = 0; t < n_list; t++) s_cum[t + 1] += s_cum[t];
+  }
+  __syncthreads();
+  const int n_items = s_cum[n_list];
   for (int it = s_item; it < n_items; it = s_item) {
-    const Item item = B.st_items[it];
-    const Inst &I = B.inst[item.inst];
+    int lo = 0, hi = n_list - 1;  // the entry t with s_cum[t] <= it < s_cum[t + 1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (s_cum[mid] <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const int tile = it - s_cum[lo];
+    const Inst &I = B.inst[s_inst[lo]];
     Scal *Sp = I.s;
+    const TileScal S = tile_scal(Sp);
     __syncthreads();  // everyone has read s_item
-    if (threadIdx.x == 0) s_phase = *(volatile int *)&Sp->phase;
+    double v0 = 0, v1 = 0;
+    resid_tile<T, CM>(I, S, tile, ring, v0, v1);
+    if (threadIdx.x == 0) s_item = take_item(&B.work[4]);
+    block_sum2<NT>(v0, v1, red);
+    if (threadIdx.x == 0) {
+      double *part = B.rs_part + 2 * (size_t)(I.rs_base + tile);
+      part[0] = v0;
+      part[1] = v1;
+      __threadfence();
+      const unsigned prev = atomicAdd(&Sp->cnt2, 1u);
+      s_last = prev == (unsigned)(I.n_rs - 1);
+    }
     __syncthreads();
-    if (s_phase == PH_RESID) {
-      const TileScal S = tile_scal(Sp);
-      double v0 = 0, v1 = 0;
-      resid_tile<T, CM>(I, S, item.tile, ring, v0, v1);
-      if (threadIdx.x == 0) s_item = take_item(&B.work[4]);
-      block_sum2<NT>(v0, v1, red);
-      if (threadIdx.x == 0) {
-        double *part = B.st_part + 2 * (size_t)(I.st_base + item.tile);
-        part[0] = v0;
-        part[1] = v1;
-        __threadfence();
-        const unsigned prev = atomicAdd(&Sp->cnt2, 1u);
-        s_last = prev == (unsigned)(I.n_st - 1);
-      }
-      __syncthreads();
-      if (s_last) {
-        __threadfence();
-        double s0, s1;
-        sum_partials<NT>(B.st_part + 2 * (size_t)I.st_base, I.n_st, s0, s1, red);
-        if (threadIdx.x == 0) fin_resid(I, Sp, s0, s1);
-      }
-    } else if (threadIdx.x == 0) {
-      s_item = take_item(&B.work[4]);
+    if (s_last) {
+      __threadfence();
+      double s0, s1;
+      sum_partials<NT>(B.rs_part + 2 * (size_t)I.rs_base, I.n_rs, s0, s1, red);
+      if (threadIdx.x == 0) fin_resid(I, Sp, s0, s1);
     }
     __syncthreads();
   }
@@ -842,7 +866,7 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
         __threadfence();
         double s0, s1;
         sum_partials<NT_UPD>(B.ch_part + 2 * (size_t)I.ch_base, I.n_ch, s0, s1, red);
-        if (threadIdx.x == 0) fin_update(I, Sp, s0, s1, B.resid_pending);
+        if (threadIdx.x == 0) fin_update(I, Sp, s0, s1, item.inst, B.resid_pending, B.resid_list);
       }
     } else if (threadIdx.x == 0) {
       s_item = take_item(&B.work[2]);
@@ -858,7 +882,8 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
 // PB_ERR_ARG; b = 0 ends it at once (the solution is phi = 0); otherwise
 // the FP64 residual pass comes next, from the instance's current x (warm
 // start) or from zero.
-__global__ void k_start(const Inst *inst, const int *list, int n, int *resid_pending) {
+__global__ void k_start(const Inst *inst, const int *list, int n, int *resid_pending,
+                        int *resid_list) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const Inst &I = inst[list[t]];
@@ -877,15 +902,15 @@ __global__ void k_start(const Inst *inst, const int *list, int n, int *resid_pen
     z.outer = -1;  // marks "phi = 0"
   } else {
     z.phase = PH_RESID;
-    atomicAdd(resid_pending, 1);
+    resid_list[atomicAdd(resid_pending, 1)] = list[t];
   }
   *S = z;
 }
 
 cudaError_t launch_start(const Inst *inst, const int *list, int n, int *resid_pending,
-                         cudaStream_t st) {
+                         int *resid_list, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_start<<<(n + 127) / 128, 128, 0, st>>>(inst, list, n, resid_pending);
+  k_start<<<(n + 127) / 128, 128, 0, st>>>(inst, list, n, resid_pending, resid_list);
   return cudaGetLastError();
 }
 

@@ -60,9 +60,10 @@ cudaError_t launch_phase(const Batch &B, int mode, int coef, const KernelGrid &k
                          cudaStream_t st);
 KernelGrid kernel_grid(int mode, int coef, int num_sms);
 // Start solves on the listed instances from their device-side setup state
-// (each asks for a residual pass: one count in *resid_pending).
+// (each one that has work asks for a residual pass: appended to resid_list,
+// counted in *resid_pending).
 cudaError_t launch_start(const Inst *inst, const int *list, int n, int *resid_pending,
-                         cudaStream_t st);
+                         int *resid_list, cudaStream_t st);
 
 // ops.cu
 cudaError_t launch_pack(const double *dense, double *padded, int nx, int ny, int nz, int px,
