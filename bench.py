@@ -38,9 +38,12 @@ import numpy as np  # noqa: E402
 from paper_1704_02745_gb300 import inputs  # noqa: E402
 
 METRIC = "solves/s, p50/p99 @1e-6 rel resid: served FP32+refine vs plain FP64 PCG"
+BATCH_METRIC = "solves/s @1e-6 rel resid: batch of 256 snapshots, FP32+refine"
 SERVING = "serving"
+BATCH = "batch256"
 WORKLOADS = {
     SERVING: None,
+    BATCH: None,
     "globule33": inputs.small_33,
     "globule129": inputs.globule_129,
     "globule257": inputs.globule_257,
@@ -136,13 +139,16 @@ def pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if v else None
 
 
-def run_loop(g, phi, snaps, steps, warmup, stream, flush, solve_kw, ctx=None, marks=None):
+def run_loop(g, phi, snaps, steps, warmup, stream, flush, solve_kw, ctx=None, marks=None,
+             prange=False):
     import torch
     dev_ms, wall_ms, iters, energies = [], [], [], []
     for i in range(warmup + steps):
         if i == warmup and marks is not None:
             torch.cuda.synchronize()
             marks.append(ctx.stats())
+        if i == warmup and prange:
+            torch.cuda.profiler.start()
         a = snaps[i % len(snaps)]
         flush.zero_()  # write > L2 between steps
         torch.cuda.synchronize()
@@ -161,6 +167,9 @@ def run_loop(g, phi, snaps, steps, warmup, stream, flush, solve_kw, ctx=None, ma
             wall_ms.append((t1 - t0) * 1e3)
             iters.append(info.iterations)
             energies.append(en)
+    if prange:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     if marks is not None:
         torch.cuda.synchronize()
         marks.append(ctx.stats())
@@ -278,7 +287,12 @@ def run_serving(args):
     clocks.start()
     batches = [[(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
                for _ in range(args.steps)]
+    if args.profile_range:
+        torch.cuda.profiler.start()
     total, lats, res = serve_steps(srv, batches)
+    if args.profile_range:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     iters = [r.info.iterations for r in res]
     bad = [r.status for r in res if r.status != 0]
     if bad:
@@ -459,7 +473,7 @@ def run_ours(args):
         clocks.start()
         marks = []
         dev_ms, wall_ms, iters, energies = run_loop(g, phi, snaps, args.steps, args.warmup, stream,
-                                                    flush, solve_kw, ctx, marks)
+                                                    flush, solve_kw, ctx, marks, args.profile_range)
         clk = clocks.stop()
         st0, st1 = marks
         # launches and copies of the timed steps (counted by the library)
@@ -626,6 +640,12 @@ def run_reference(args):
         scale = iteration_scale(args.tol)
         iters_of = lambda pr: scale * pr.grid.nx
         name = "serving stream: 16 trajectories, 300-8000 atoms, grids 33^3-193^3"
+    elif args.workload == BATCH:
+        probs = inputs.snapshot_batch()[:args.warmup + args.steps]
+        scale = iteration_scale(args.tol)
+        iters_of = lambda pr: scale * pr.grid.nx
+        name = ("batch of 256 snapshots: 1,000-atom cluster, sigma 0.3 A, grids 49^3-97^3, "
+                "one server batch")
     else:
         problem = WORKLOADS[args.workload]()
         probs = [inputs.Problem(problem.name, problem.grid, a)
@@ -641,7 +661,8 @@ def run_reference(args):
     total = sum(times)
     val = args.steps / total
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": world,
+        "impl": "reference", "metric": BATCH_METRIC if args.workload == BATCH else METRIC,
+        "value": val, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -657,6 +678,97 @@ def run_reference(args):
         "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# --------------------------------------------------------------------------- batch of snapshots
+
+def run_batch(args):
+    """256 snapshots of one 1,000-atom cluster (sigma 0.3 A), grids 49^3-97^3,
+    all submitted to one server at once: a step is the whole batch, cold
+    started (phi0 = 0), FP32 Jacobi-PCG + FP64 refinement to the tolerance."""
+    import torch
+    from paper_1704_02745_gb300 import pb
+    from paper_1704_02745_gb300 import build as pbbuild
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    pbbuild.build()
+    torch.cuda.set_device(local)
+    snaps = inputs.snapshot_batch(seed=4 + 1000 * rank)
+    reqs = [(s, p.grid.replace(dh="f32"), p.atoms) for s, p in enumerate(snaps)]
+    ctx = pb.Context(local)
+    srv = pb.Server(ctx, int(args.budget_gb * (1 << 30)), precision="f32_refine", tol=args.tol,
+                    inner_tol=args.inner_tol, warm_start=False)
+    for _ in range(args.warmup):
+        serve_batch(srv, reqs)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total, lats, res = serve_steps(srv, [reqs] * args.steps)
+    clk = clocks.stop()
+    st1 = ctx.stats()
+    bad = [r.status for r in res if r.status != 0]
+    if bad:
+        raise RuntimeError(f"batch requests failed: {bad[:5]}")
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t[0])
+    e0 = ctx.stats()
+    e2e_wall, _, _ = serve_steps(srv, [reqs] * max(1, args.steps // 2), want_phi=True)
+    e1 = ctx.stats()
+    e2e_steps = max(1, args.steps // 2)
+    srv.profile_begin()
+    serve_batch(srv, reqs)
+    kp = srv.profile_end()
+    srv.close()
+    if rank != 0:
+        ctx.close()
+        return
+    hbm, peak_kind = peaks()
+    nodes = sum(p.grid.n for p in snaps)
+    iters = [r.info.iterations for r in res]
+    ach_st = kp.bytes_stencil / max(kp.ms_stencil, 1e-12) / 1e6
+    ach_up = kp.bytes_update / max(kp.ms_update, 1e-12) / 1e6
+    out = {
+        "metric": BATCH_METRIC,
+        "value": world * len(reqs) * args.steps / total, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "batch of 256 snapshots: 1,000-atom cluster, sigma 0.3 A, "
+                               "grids 49^3-97^3, one server batch",
+                   "nodes_per_step": nodes, "tol": args.tol, "inner_tol": args.inner_tol,
+                   "debye_hueckel_sum": "f32", "l2": f"inputs larger than L2 ({nodes / 1e6:.0f} M nodes)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations_mean": float(np.mean(iters)),
+        "grid_point_iters_per_s": world * args.steps * sum(
+            p.grid.n * r.info.iterations for p, r in zip(snaps * args.steps, res)) / args.steps / total,
+        "roofline": {"bound": "hbm", "kernel": "k_stencil<float,packed>: batched stencil pass",
+                     "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
+                     "peak_kind": peak_kind, "traffic": None,
+                     "bytes_per_node": BYTES_PER_NODE["stencil"],
+                     "launch_ms": kp.ms_stencil / max(kp.launches_stencil, 1),
+                     "launches": kp.launches_stencil,
+                     "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
+                                     "launch_ms": kp.ms_update / max(kp.launches_update, 1),
+                                     "launches": kp.launches_update},
+                     "resid_pass": {"launch_ms": kp.ms_resid / max(kp.launches_resid, 1),
+                                    "launches": kp.launches_resid}},
+        "e2e": {"value": world * len(reqs) * e2e_steps / e2e_wall, "unit": "solves/s",
+                "h2d_bytes_per_step": int((e1[1] - e0[1]) / e2e_steps),
+                "d2h_bytes_per_step": int((e1[2] - e0[2]) / e2e_steps),
+                "note": "same steps with phi copied to host memory per request"},
+        "gpu_launches": int(st1[0] - st0[0]),
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    ctx.close()
 
 
 def main():
@@ -677,6 +789,9 @@ def main():
     ap.add_argument("--dh", default="f32", choices=["f32", "f64"],
                     help="precision of the Debye-Hueckel boundary sum in the grid setup")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--quick", action="store_true",
                     help="timed loop only (no FP64 comparator, profiled solve or CPU baseline)")
     args = ap.parse_args()
@@ -686,6 +801,8 @@ def main():
         run_reference(args)
     elif args.workload == SERVING:
         run_serving(args)
+    elif args.workload == BATCH:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -150,6 +150,7 @@ void pb_grid_release(pb_grid *g) {
                   g->own_scal ? (void *)g->scal : nullptr, g->dinst, g->st_items, g->ch_items, g->st_part,
                   g->ch_part, g->rs_part};
   for (void *p : ptrs) dfree(p);
+  if (g->h_atoms) cudaFreeHost(g->h_atoms);
   delete g;
 }
 
@@ -201,10 +202,18 @@ pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double 
     if (g->xyzq) cudaFree(g->xyzq);
     if (g->xyzr) cudaFree(g->xyzr);
     if (g->scratch) cudaFree(g->scratch);
+    if (g->h_atoms) cudaFreeHost(g->h_atoms);
     g->xyzq = g->xyzr = nullptr;
     g->scratch = nullptr;
+    g->h_atoms = nullptr;
     g->atom_cap = 0;
     pb_status st;
+    // pinned, so that the uploads below never wait for earlier work on the stream
+    if (cudaMallocHost((void **)&g->h_atoms, 2 * (size_t)(n_atoms + 1) * sizeof(dbl4)) != cudaSuccess) {
+      g->h_atoms = nullptr;
+      cudaGetLastError();
+      return pb_fail(PB_ERR_OOM, "pinned host staging of the atoms");
+    }
     if ((st = pb_dalloc((void **)&g->xyzq, (size_t)(n_atoms + 1) * sizeof(dbl4)))) return st;
     if ((st = pb_dalloc((void **)&g->xyzr, (size_t)(n_atoms + 1) * sizeof(dbl4)))) return st;
     if ((st = pb_dalloc((void **)&g->scratch,
@@ -213,14 +222,15 @@ pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double 
     g->atom_cap = n_atoms;
   }
   g->n_atoms = n_atoms;
-  g->hq.resize(n_atoms);
-  g->hr.resize(n_atoms);
+  // The staging is rewritten only by a later setup of this grid, which comes
+  // after the grid's solve (a server) or after a synchronisation.
+  dbl4 *hq = g->h_atoms, *hr = g->h_atoms + g->atom_cap + 1;
   for (int a = 0; a < n_atoms; a++) {
-    g->hq[a] = dbl4{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], q[a]};
-    g->hr[a] = dbl4{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], radius[a]};
+    hq[a] = dbl4{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], q[a]};
+    hr[a] = dbl4{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], radius[a]};
   }
-  CK(cudaMemcpyAsync(g->xyzq, g->hq.data(), n_atoms * sizeof(dbl4), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(g->xyzr, g->hr.data(), n_atoms * sizeof(dbl4), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g->xyzq, hq, n_atoms * sizeof(dbl4), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(g->xyzr, hr, n_atoms * sizeof(dbl4), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(g->b, 0, g->n_pad * sizeof(double), s));
   CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
   SetupArgs a;
@@ -254,7 +264,7 @@ pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double 
   else if (desc->coef != PB_COEF_PACKED)
     CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, desc->coef, g->ex, g->ey,
                      g->ez, g->diag, s));
-  g->ctx->stats->launches += 5 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
+  g->ctx->stats->launches += 3 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
   g->ctx->stats->h2d += 2 * (unsigned long long)n_atoms * sizeof(dbl4);
   if (!sync) return PB_OK;  // the error word and ||b||^2 stay on the device
   int *hbuf = (int *)g->ctx->host_scal;  // pinned staging: error word, then ||b||^2
@@ -312,7 +322,7 @@ pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_g
   ALLOC(g->ghost, g->n_ghost * sizeof(double));
   ALLOC(g->err, sizeof(int) * 4);
   ALLOC(g->counts, sizeof(int) * PB_COUNTS);
-  if (cudaMemset(g->counts, 0, sizeof(int) * PB_COUNTS) != cudaSuccess) {
+  if (cudaMemsetAsync(g->counts, 0, sizeof(int) * PB_COUNTS, ctx->stream) != cudaSuccess) {
     pb_grid_release(g);
     return pb_fail(PB_ERR_CUDA, "clear work counters");
   }
@@ -329,6 +339,7 @@ pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_g
   }
 #undef ALLOC
   pb_tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms), batch);
+  g->batch = batch;
   *out = g;
   return PB_OK;
 }
@@ -399,6 +410,7 @@ pb_status pb_ensure_workspace(pb_grid *g, int mode) {
     if ((st = alloc0(&g->p132, n * 4))) return st;
     if ((st = alloc0(&g->ap32, n * 4))) return st;
   }
+  if (g->batch) return PB_OK;  // scalars, descriptor and work lists are the server's
   if ((st = alloc0((void **)&g->scal, sizeof(Scal)))) return st;
   if ((st = alloc0((void **)&g->dinst, sizeof(Inst)))) return st;
   if (!g->st_items) {
@@ -769,7 +781,7 @@ extern "C" pb_status pb_energy(pb_grid *g, const double *phi, double *energy) {
   if (!g || !phi || !energy) return pb_fail(PB_ERR_ARG, "pb_energy: NULL argument");
   CK(cudaSetDevice(g->ctx->device));
   cudaStream_t s = g->ctx->stream;
-  CK(launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.h, g->d.origin[0],
+  CK(launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.nx, g->d.h, g->d.origin[0],
                    g->d.origin[1], g->d.origin[2], phi, g->scratch + SCR_ENERGY_PART,
                    g->scratch + SCR_ENERGY, s));
   CK(cudaMemcpyAsync(energy, g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -83,8 +83,11 @@ cudaError_t launch_apply(const Inst &I, const Inst *dI, const void *u, void *au,
 // sum_nodes q_node phi_node up to rounding order.  Per-CTA partials, then one
 // CTA sums them in order (deterministic).
 constexpr int EN_NT = 256;
-__global__ void k_energy_partial(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, double h,
-                                 double ox, double oy, double oz, const double *phi, double *part) {
+// px: row pitch of phi in elements (nx for a dense array).  An atom whose
+// trilinear cell leaves the grid reads nothing and makes the energy NaN.
+__global__ void k_energy_partial(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, int px,
+                                 double h, double ox, double oy, double oz, const double *phi,
+                                 double *part) {
   __shared__ double red[EN_NT];
   double acc = 0.0;
   const int a = blockIdx.x * EN_NT + threadIdx.x;
@@ -94,19 +97,28 @@ __global__ void k_energy_partial(const dbl4 *xyzq, int n_atoms, int nx, int ny, 
                          __ddiv_rn(__dsub_rn(A.z, oz), h)};
     double w[3][2];
     long c0[3];
+    const long n[3] = {nx, ny, nz};
+    bool inside = true;
     for (int d = 0; d < 3; d++) {
       const double fl = floor(f[d]);
       c0[d] = (long)fl;
       w[d][1] = __dsub_rn(f[d], fl);
       w[d][0] = __dsub_rn(1.0, w[d][1]);
+      // the cell's upper corner may be the last node only when its weight is 0
+      inside = inside && fl >= 0.0 && (c0[d] + 1 < n[d] || (c0[d] + 1 == n[d] && w[d][1] == 0.0));
     }
-    for (int dk = 0; dk < 2; dk++)
-      for (int dj = 0; dj < 2; dj++)
-        for (int di = 0; di < 2; di++) {
-          const double c = __dmul_rn(__dmul_rn(__dmul_rn(A.w, w[0][di]), w[1][dj]), w[2][dk]);
-          const size_t t = ((size_t)(c0[2] + dk) * ny + (c0[1] + dj)) * nx + (c0[0] + di);
-          acc += c * phi[t];
-        }
+    if (!inside) {
+      acc = __longlong_as_double(0x7ff8000000000000LL);  // NaN
+    } else {
+      for (int dk = 0; dk < 2; dk++)
+        for (int dj = 0; dj < 2; dj++)
+          for (int di = 0; di < 2; di++) {
+            const double c = __dmul_rn(__dmul_rn(__dmul_rn(A.w, w[0][di]), w[1][dj]), w[2][dk]);
+            if (c0[0] + di >= nx || c0[1] + dj >= ny || c0[2] + dk >= nz) continue;  // weight 0
+            const size_t t = ((size_t)(c0[2] + dk) * ny + (c0[1] + dj)) * px + (c0[0] + di);
+            acc += c * phi[t];
+          }
+    }
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -129,12 +141,12 @@ __global__ void k_energy_final(const double *part, int n, double *out) {
   if (threadIdx.x == 0) *out = 0.5 * 332.0637 * red[0];
 }
 
-cudaError_t launch_energy(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, double h,
+cudaError_t launch_energy(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, int px, double h,
                           double ox, double oy, double oz, const double *phi, double *scratch,
                           double *out, cudaStream_t st) {
   const int blocks = n_atoms > 0 ? (n_atoms + EN_NT - 1) / EN_NT : 0;
   if (blocks > 0)
-    k_energy_partial<<<blocks, EN_NT, 0, st>>>(xyzq, n_atoms, nx, ny, nz, h, ox, oy, oz, phi,
+    k_energy_partial<<<blocks, EN_NT, 0, st>>>(xyzq, n_atoms, nx, ny, nz, px, h, ox, oy, oz, phi,
                                                scratch);
   k_energy_final<<<1, EN_NT, 0, st>>>(scratch, blocks, out);
   return cudaGetLastError();

@@ -26,7 +26,7 @@ struct pb_grid {
   size_t n_pad = 0;
   long n_ghost = 0;
   int n_atoms = 0, atom_cap = 0;
-  std::vector<pb::dbl4> hq, hr;  // host staging of the atoms
+  pb::dbl4 *h_atoms = nullptr;  // pinned host staging of the atoms: xyzq, then xyzr
   double kappa = 0, kbh2 = 0, bnorm = 0;
   // setup arrays
   uint8_t *code = nullptr;
@@ -43,6 +43,7 @@ struct pb_grid {
   pb::Scal *scal = nullptr;  // own allocation, or a slot of a server's scalar array
   bool own_scal = true;
   int *counts = nullptr;     // device: stencil and update item counts of the single-grid batch
+  bool batch = false;        // a server's grid: its work lists and scalars are the server's
   pb::Inst *dinst = nullptr;
   pb::Item *st_items = nullptr, *ch_items = nullptr;
   double *st_part = nullptr, *ch_part = nullptr, *rs_part = nullptr;

@@ -2,21 +2,27 @@
 // pb_batch_*): many MD snapshots (arXiv:1704.02745 Sec. 1: PB over thousands
 // to millions of snapshots) solved together on one GPU.
 //
-// A worker thread owns the server's CUDA work.  Each loop it
+// A worker thread owns the server's CUDA work.  Each round it
 //   1. admits queued requests (pb_plan_admission) into resident grids --
 //      one per trajectory, reused snapshot after snapshot, so a solve starts
 //      from the trajectory's last solution -- evicting idle grids LRU when the
 //      device-memory budget requires;
-//   2. runs the setup kernels of the admitted snapshots and starts their
-//      solves on the device (no host round trip);
+//   2. queues the setup kernels of the admitted snapshots and the start of
+//      their solves on the device (no host round trip);
 //   3. rebuilds the batch's work list when the active set changed: stencil
 //      tiles and update chunks of every active grid, each grid's partial sums
 //      at its own offset, so its reductions are summed in a fixed order
 //      whatever else runs;
-//   4. launches a captured device graph of `ticks` phase ticks over the whole
-//      batch (finished grids are skipped by their convergence mask);
-//   5. reads all grids' scalars and completes the finished requests (energy,
-//      optional copy of phi to the caller).
+//   4. queues a captured device graph of `ticks` phase ticks over the whole
+//      batch (finished grids are skipped by their convergence mask) and a copy
+//      of all grids' scalars;
+//   5. while that graph runs, reads the scalars the previous round's graph
+//      left, queues the energy (and phi) of the solves that finished in it
+//      behind the running graph, and hands out the results queued one round
+//      earlier.
+// Everything the host uploads comes from pinned staging in two sets, one
+// per round in flight, so no copy waits for the graph ahead of it and the
+// GPU never idles on the host between rounds.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -129,6 +135,33 @@ struct Slot {
   int xbuf = 0;               // which x64 buffer holds it
   Request req;
   bool warm = false;
+  uint64_t first_round = 0;   // round whose graph first runs the current solve
+};
+
+// A finished solve whose energy (and phi) are queued behind the running graph.
+struct Finishing {
+  Request req;
+  Scal S;
+  bool warm = false;
+  double *energy = nullptr;  // pinned
+  double *phi = nullptr;     // pinned, n doubles (phi requested)
+  size_t n = 0;
+  bool zero_phi = false;     // phi requested and the solution is 0 (b = 0)
+};
+
+// Pinned host staging of one round.
+struct Stage {
+  Inst *inst = nullptr;   // descriptors of slots [0, MAX_SLOTS)
+  Item *items = nullptr;  // stencil items, then update items
+  size_t cap_items = 0;
+  int *counts = nullptr;  // 2 ints
+  int *start = nullptr;   // slots whose solves start
+  Scal *scal = nullptr;   // scalars of all slots after the round's graph
+  double *energy = nullptr;
+  double *phi = nullptr;
+  size_t cap_phi = 0;
+  cudaEvent_t ev_graph = nullptr;  // after the graph and the scalar copy
+  cudaEvent_t ev_done = nullptr;   // after the energy (and phi) copies
 };
 
 }  // namespace
@@ -165,6 +198,8 @@ struct pb_server {
   size_t cap_dense = 0;
   cudaGraphExec_t graph = nullptr;
   int ticks = 8;
+  Stage stage[2];
+  uint64_t round = 0;
   // kernel measurement (pb_server_profile_begin/end)
   std::atomic<bool> profiling{false};
   pb_kernel_profile prof{};
@@ -273,7 +308,6 @@ std::vector<int> admit(pb_server *s) {
         continue;  // device memory short of the model: retry later
       }
       s->free_slots.pop_back();
-      if (g->scal) cudaFree(g->scal);
       g->scal = s->d_scal + j;
       g->own_scal = false;
       Slot &sl = s->slots[j];
@@ -299,14 +333,13 @@ std::vector<int> admit(pb_server *s) {
         const double *from = o.xbuf ? o.g->x64b : o.g->x64;
         cudaMemcpyAsync(sl.g->x64, from, sl.g->n_pad * sizeof(double), cudaMemcpyDeviceToDevice,
                         s->stream);
-        Scal z;
-        memset(&z, 0, sizeof(z));
-        cudaMemcpyAsync(s->d_scal + j, &z, sizeof(Scal), cudaMemcpyHostToDevice, s->stream);
+        cudaMemsetAsync(s->d_scal + j, 0, sizeof(Scal), s->stream);
         sl.has_solution = true;
         sl.solved_at = o.solved_at;
       }
     }
     sl.busy = true;
+    sl.first_round = s->round;
     sl.last_used = ++s->clock;
     sl.warm = s->opts.warm_start && sl.has_solution;
     if (pb_run_setup(sl.g, (int)rq.q.size(), rq.xyz.data(), rq.q.data(), rq.r.data(), false)) {
@@ -334,15 +367,30 @@ std::vector<int> admit(pb_server *s) {
 }
 
 // Upload the descriptors, work lists and partial offsets of the active grids.
-bool rebuild_batch(pb_server *s, bool *graph_stale) {
+// Host staging capacity for n items (pinned; the set is idle when called).
+bool stage_items(Stage &st, size_t n) {
+  if (n <= st.cap_items) return true;
+  const size_t cap = std::max(n, 2 * st.cap_items);
+  if (st.items) cudaFreeHost(st.items);
+  st.items = nullptr;
+  st.cap_items = 0;
+  if (cudaMallocHost((void **)&st.items, cap * sizeof(Item)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  st.cap_items = cap;
+  return true;
+}
+
+bool rebuild_batch(pb_server *s, Stage &sg, bool *graph_stale) {
   std::vector<Item> st, ch;
   std::vector<int> active;
   for (int j = 0; j < (int)s->slots.size(); j++)
     if (s->slots[j].g && s->slots[j].busy) active.push_back(j);
-  int st_off = 0, ch_off = 0, rs_off = 0;
+  int st_off = 0, ch_off = 0, rs_off = 0, hi = 0;
   for (int j : active) {
     pb_grid *g = s->slots[j].g;
-    Inst I;
+    Inst &I = sg.inst[j];
     if (pb_make_inst(g, &s->opts, s->mode, s->coef, I)) return false;
     I.s = s->d_scal + j;
     I.st_base = st_off;
@@ -353,10 +401,14 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
     for (int t = 0; t < g->n_ch; t++) ch.push_back(Item{j, t});
     st_off += g->n_st;
     ch_off += g->n_ch;
-    if (!cuda_ok(cudaMemcpyAsync(s->d_inst + j, &I, sizeof(Inst), cudaMemcpyHostToDevice, s->stream),
-                 s, "upload descriptor"))
+    hi = j + 1;
+  }
+  // descriptors of slots [0, hi): the idle ones among them are never read
+  if (hi > 0) {
+    if (!cuda_ok(cudaMemcpyAsync(s->d_inst, sg.inst, hi * sizeof(Inst), cudaMemcpyHostToDevice,
+                                 s->stream), s, "upload descriptors"))
       return false;
-    s->ctx->stats->h2d += sizeof(Inst);
+    s->ctx->stats->h2d += hi * sizeof(Inst);
   }
   // Largest items first: the phase kernels take items in list order, so the
   // small ones fill in at the end of each launch.  (The order changes no
@@ -407,19 +459,25 @@ bool rebuild_batch(pb_server *s, bool *graph_stale) {
     s->worker_error = "out of device memory for the partial sums";
     return false;
   }
-  const int counts[2] = {(int)st.size(), (int)ch.size()};
-  if (!st.empty() && !cuda_ok(cudaMemcpyAsync(s->d_st, st.data(), st.size() * sizeof(Item),
+  if (!stage_items(sg, st.size() + ch.size())) {
+    s->worker_error = "out of pinned host memory for the work lists";
+    return false;
+  }
+  std::copy(st.begin(), st.end(), sg.items);
+  std::copy(ch.begin(), ch.end(), sg.items + st.size());
+  sg.counts[0] = (int)st.size();
+  sg.counts[1] = (int)ch.size();
+  if (!st.empty() && !cuda_ok(cudaMemcpyAsync(s->d_st, sg.items, st.size() * sizeof(Item),
                                               cudaMemcpyHostToDevice, s->stream), s, "items"))
     return false;
-  if (!ch.empty() && !cuda_ok(cudaMemcpyAsync(s->d_ch, ch.data(), ch.size() * sizeof(Item),
+  if (!ch.empty() && !cuda_ok(cudaMemcpyAsync(s->d_ch, sg.items + st.size(), ch.size() * sizeof(Item),
                                               cudaMemcpyHostToDevice, s->stream), s, "items"))
     return false;
-  if (!cuda_ok(cudaMemcpyAsync(s->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s->stream),
-               s, "counts"))
+  if (!cuda_ok(cudaMemcpyAsync(s->d_counts, sg.counts, 2 * sizeof(int), cudaMemcpyHostToDevice,
+                               s->stream), s, "counts"))
     return false;
-  s->ctx->stats->h2d += (st.size() + ch.size()) * sizeof(Item) + sizeof(counts);
-  // the copies read host vectors that go out of scope: wait for them
-  return cuda_ok(cudaStreamSynchronize(s->stream), s, "upload");
+  s->ctx->stats->h2d += (st.size() + ch.size()) * sizeof(Item) + 2 * sizeof(int);
+  return true;
 }
 
 bool run_graph(pb_server *s, bool stale) {
@@ -454,51 +512,72 @@ bool run_graph(pb_server *s, bool stale) {
   return true;
 }
 
-// Complete the finished solves among the active slots.
-void complete(pb_server *s, const std::vector<int> &fin) {
-  if (fin.empty()) return;
-  std::vector<double> energy(fin.size(), 0.0);
+// Queue, behind the running graph, the energy (and phi) of the solves that
+// finished in the previous round's graph, and free their slots.
+// snap: the scalars the previous round's graph left; sg: this round's
+// staging set (idle: its last copies were waited for).
+bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector<int> &fin,
+                    std::vector<Finishing> &out) {
+  size_t phi_total = 0;
+  for (int j : fin)
+    if (s->slots[j].req.phi_out) phi_total += (size_t)s->slots[j].g->d.nx * s->slots[j].g->d.ny * s->slots[j].g->d.nz;
+  if (phi_total > sg.cap_phi) {
+    if (sg.phi) cudaFreeHost(sg.phi);
+    sg.phi = nullptr;
+    sg.cap_phi = 0;
+    if (cudaMallocHost((void **)&sg.phi, phi_total * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      s->worker_error = "out of pinned host memory for phi";
+      return false;
+    }
+    sg.cap_phi = phi_total;
+  }
+  size_t phi_off = 0;
   for (size_t k = 0; k < fin.size(); k++) {
     Slot &sl = s->slots[fin[k]];
     pb_grid *g = sl.g;
-    const Scal &S = s->h_scal[fin[k]];
-    if (S.status == PB_ERR_ARG) continue;
-    const double *x = S.xbuf ? g->x64b : g->x64;
-    const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
-    if (!grow(&s->d_dense, &s->cap_dense, n)) continue;
-    if (S.outer == -1) cudaMemsetAsync(s->d_dense, 0, n * sizeof(double), s->stream);
-    else launch_unpack(x, s->d_dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->stream);
-    launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.h, g->d.origin[0],
-                  g->d.origin[1], g->d.origin[2], s->d_dense, g->scratch + SCR_ENERGY_PART,
-                  g->scratch + SCR_ENERGY, s->stream);
-    cudaMemcpyAsync(&energy[k], g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost,
-                    s->stream);
-    s->ctx->stats->launches += 1 + (g->n_atoms > 0 ? 2 : 1);
-    s->ctx->stats->d2h += sizeof(double);
-    if (sl.req.phi_out) {
-      cudaMemcpyAsync(sl.req.phi_out, s->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost,
-                      s->stream);
-      s->ctx->stats->d2h += n * sizeof(double);
+    const Scal &S = snap[fin[k]];
+    Finishing f;
+    f.S = S;
+    f.warm = sl.warm;
+    f.energy = sg.energy + k;
+    *f.energy = 0.0;
+    if (S.status != PB_ERR_ARG && S.outer == -1 && sl.req.phi_out) {  // phi = 0, energy 0
+      f.zero_phi = true;
+      f.n = (size_t)g->d.nx * g->d.ny * g->d.nz;
     }
-  }
-  cudaStreamSynchronize(s->stream);
-  std::lock_guard<std::mutex> lk(s->mu);
-  for (size_t k = 0; k < fin.size(); k++) {
-    Slot &sl = s->slots[fin[k]];
-    const Scal &S = s->h_scal[fin[k]];
-    pb_result r;
-    memset(&r, 0, sizeof(r));
-    r.status = S.status;
-    r.energy = S.status == PB_ERR_ARG ? 0.0 : energy[k];
-    r.info.status = S.status;
-    r.info.iterations = S.total_iter;
-    r.info.outer_steps = S.outer < 0 ? 0 : S.outer;
-    r.info.relres = S.relres;
-    r.info.relres_true = S.outer == -1 ? 0.0 : S.relres_true;
-    r.seconds = since(sl.req.t_submit);
-    r.warm_started = sl.warm ? 1 : 0;
-    s->done[sl.req.ticket] = r;
-    s->completed++;
+    if (S.status != PB_ERR_ARG && S.outer != -1) {
+      const double *x = S.xbuf ? g->x64b : g->x64;
+      const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
+      const double *phi = x;  // the padded solution itself, unless phi is wanted dense
+      int pitch = g->g.px;
+      if (sl.req.phi_out) {
+        if (!grow(&s->d_dense, &s->cap_dense, n)) {
+          s->worker_error = "out of device memory for phi";
+          return false;
+        }
+        launch_unpack(x, s->d_dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->stream);
+        s->ctx->stats->launches += 1;
+        phi = s->d_dense;
+        pitch = g->d.nx;
+      }
+      launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, pitch, g->d.h, g->d.origin[0],
+                    g->d.origin[1], g->d.origin[2], phi, g->scratch + SCR_ENERGY_PART,
+                    g->scratch + SCR_ENERGY, s->stream);
+      cudaMemcpyAsync(f.energy, g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost,
+                      s->stream);
+      s->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;
+      s->ctx->stats->d2h += sizeof(double);
+      if (sl.req.phi_out) {
+        f.phi = sg.phi + phi_off;
+        f.n = n;
+        phi_off += n;
+        cudaMemcpyAsync(f.phi, s->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        s->ctx->stats->d2h += n * sizeof(double);
+      }
+    }
+    f.req = std::move(sl.req);
+    out.push_back(std::move(f));
     sl.busy = false;
     sl.has_solution = S.status == PB_OK && S.outer != -1;
     sl.xbuf = S.xbuf;
@@ -506,6 +585,34 @@ void complete(pb_server *s, const std::vector<int> &fin) {
     sl.solved_at = sl.last_used;
     sl.req = Request();
   }
+  return cuda_ok(cudaEventRecord(sg.ev_done, s->stream), s, "event");
+}
+
+// Hand out the results of finished solves (their copies have landed).
+void publish(pb_server *s, std::vector<Finishing> &fin) {
+  if (fin.empty()) return;
+  for (auto &f : fin) {
+    if (f.phi) memcpy(f.req.phi_out, f.phi, f.n * sizeof(double));
+    if (f.zero_phi) memset(f.req.phi_out, 0, f.n * sizeof(double));
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto &f : fin) {
+    const Scal &S = f.S;
+    pb_result r;
+    memset(&r, 0, sizeof(r));
+    r.status = S.status;
+    r.energy = S.status == PB_ERR_ARG ? 0.0 : *f.energy;
+    r.info.status = S.status;
+    r.info.iterations = S.total_iter;
+    r.info.outer_steps = S.outer < 0 ? 0 : S.outer;
+    r.info.relres = S.relres;
+    r.info.relres_true = S.outer == -1 ? 0.0 : S.relres_true;
+    r.seconds = since(f.req.t_submit);
+    r.warm_started = f.warm ? 1 : 0;
+    s->done[f.req.ticket] = r;
+    s->completed++;
+  }
+  fin.clear();
   s->cv_done.notify_all();
 }
 
@@ -579,28 +686,34 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
 void worker_main(pb_server *s) {
   cudaSetDevice(s->ctx->device);
   bool active_changed = true, graph_stale = true;
+  bool prev_graph = false;             // the previous round ran a graph: its scalars are unread
+  std::vector<int> prev_active;        // ... over these slots
+  std::vector<Finishing> finishing;    // results queued in the previous round
   while (true) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       const bool any_busy = std::any_of(s->slots.begin(), s->slots.end(),
                                         [](const Slot &x) { return x.g && x.busy; });
-      if (!any_busy && s->queue.empty())
+      if (!any_busy && s->queue.empty() && !prev_graph && finishing.empty())
         s->cv_work.wait_for(lk, std::chrono::milliseconds(50),
                             [&] { return s->stop || !s->queue.empty(); });
       if (s->stop) break;
     }
+    Stage &sg = s->stage[s->round & 1], &sp = s->stage[(s->round & 1) ^ 1];
     const std::vector<int> started = admit(s);
     if (!started.empty()) active_changed = true;
     if (active_changed) {
       // descriptors first: the start kernel reads each grid's error word and
       // ||b||^2 through its descriptor
-      if (!rebuild_batch(s, &graph_stale)) break;
+      if (!rebuild_batch(s, sg, &graph_stale)) break;
       if (!started.empty()) {
-        cudaMemcpyAsync(s->d_list, started.data(), started.size() * sizeof(int),
-                        cudaMemcpyHostToDevice, s->stream);
+        std::copy(started.begin(), started.end(), sg.start);
+        cudaMemcpyAsync(s->d_list, sg.start, started.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        s->stream);
         launch_start(s->d_inst, s->d_list, (int)started.size(), s->d_counts + 2, s->d_rlist,
                      s->stream);
         s->ctx->stats->launches += 1;
+        s->ctx->stats->h2d += started.size() * sizeof(int);
       }
       active_changed = false;
     }
@@ -615,26 +728,46 @@ void worker_main(pb_server *s) {
       for (auto &x : s->slots)
         if (x.g) { s->n_resident++; s->bytes_resident += x.bytes; }
     }
-    if (active.empty()) continue;
-    if (s->profiling.load()) {
-      if (!run_profiled(s, active)) break;
-    } else {
-      if (!run_graph(s, graph_stale)) break;
-      graph_stale = false;
+    bool ran = false;
+    if (!active.empty()) {
+      if (s->profiling.load()) {
+        if (!run_profiled(s, active)) break;
+      } else {
+        if (!run_graph(s, graph_stale)) break;
+        graph_stale = false;
+      }
+      const int hi = *std::max_element(active.begin(), active.end()) + 1;
+      cudaMemcpyAsync(sg.scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
+      s->ctx->stats->d2h += hi * sizeof(Scal);
+      if (!cuda_ok(cudaEventRecord(sg.ev_graph, s->stream), s, "event")) break;
+      ran = true;
     }
-    const int hi = *std::max_element(active.begin(), active.end()) + 1;
-    cudaMemcpyAsync(s->h_scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
-    s->ctx->stats->d2h += hi * sizeof(Scal);
-    if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "tick")) break;
-    std::vector<int> fin;
-    for (int j : active)
-      if (s->h_scal[j].phase == PH_DONE) fin.push_back(j);
-    if (!fin.empty()) {
-      complete(s, fin);
-      active_changed = true;
+    // The previous round, while this round's graph runs: hand out the results
+    // queued then, and queue those of the solves its graph finished.
+    if (!finishing.empty()) {
+      if (!cuda_ok(cudaEventSynchronize(sp.ev_done), s, "round")) break;
+      publish(s, finishing);
     }
+    if (prev_graph) {
+      if (!cuda_ok(cudaEventSynchronize(sp.ev_graph), s, "round")) break;
+      std::vector<int> fin;
+      for (int j : prev_active) {
+        const Slot &sl = s->slots[j];
+        if (sl.g && sl.busy && sl.first_round < s->round && sp.scal[j].phase == PH_DONE)
+          fin.push_back(j);
+      }
+      if (!fin.empty()) {
+        if (!queue_finished(s, sg, sp.scal, fin, finishing)) break;
+        active_changed = true;
+      }
+    }
+    prev_graph = ran;
+    prev_active.swap(active);
+    s->round++;
   }
-  // fail what is left
+  // hand out what was queued, fail what is left
+  cudaStreamSynchronize(s->stream);
+  publish(s, finishing);
   std::lock_guard<std::mutex> lk(s->mu);
   for (auto &rq : s->queue) {
     pb_result r;
@@ -714,6 +847,15 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMemset(s->d_scal, 0, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
   ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
+  for (Stage &sg : s->stage) {
+    ok = ok && cudaMallocHost((void **)&sg.inst, MAX_SLOTS * sizeof(Inst)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&sg.counts, 4 * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&sg.start, MAX_SLOTS * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&sg.scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&sg.energy, MAX_SLOTS * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&sg.ev_graph, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&sg.ev_done, cudaEventDisableTiming) == cudaSuccess;
+  }
   if (!ok) {
     pb_server_destroy(s);
     return pb_fail(PB_ERR_OOM, "pb_server_create: device allocation failed");
@@ -745,6 +887,13 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->h_scal) cudaFreeHost(s->h_scal);
+  for (Stage &sg : s->stage) {
+    void *hp[] = {sg.inst, sg.items, sg.counts, sg.start, sg.scal, sg.energy, sg.phi};
+    for (void *p : hp)
+      if (p) cudaFreeHost(p);
+    if (sg.ev_graph) cudaEventDestroy(sg.ev_graph);
+    if (sg.ev_done) cudaEventDestroy(sg.ev_done);
+  }
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->stream) cudaStreamDestroy(s->stream);

@@ -56,7 +56,8 @@ __global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *
   const long k0 = max((long)floor(__ddiv_rn(A.z - A.w - g.oz, g.h)) - 1, 0L);
   const long k1 = min((long)ceil(__ddiv_rn(A.z + A.w - g.oz, g.h)) + 1, (long)g.nz - 1);
   if (i0 > i1 || j0 > j1 || k0 > k1) return;
-  const long ni = i1 - i0 + 1, nj = j1 - j0 + 1, cnt = ni * nj * (k1 - k0 + 1);
+  // box extents are a few dozen nodes: 32-bit index arithmetic
+  const int ni = (int)(i1 - i0 + 1), nj = (int)(j1 - j0 + 1), cnt = ni * nj * (int)(k1 - k0 + 1);
   // FP32 offsets from the atom of the box's first node (exact up to one FP32
   // rounding), then steps of h: a few hundred ulp of a few A at most
   const float bx = (float)(node_coord(g.ox, i0, g.h) - A.x);
@@ -64,8 +65,9 @@ __global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *
   const float bz = (float)(node_coord(g.oz, k0, g.h) - A.z);
   const float hf = (float)g.h;
   const size_t rowp = (size_t)g.px, plane = (size_t)g.px * g.ny;
-  for (long t = threadIdx.x; t < cnt; t += blockDim.x) {
-    const long i = i0 + t % ni, j = j0 + (t / ni) % nj, k = k0 + t / (ni * nj);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const int tj = t / ni, tk = tj / nj;
+    const long i = i0 + (t - tj * ni), j = j0 + (tj - tk * nj), k = k0 + tk;
     const float dx = bx + (float)(i - i0) * hf, dy = by + (float)(j - j0) * hf;
     const float dz = bz + (float)(k - k0) * hf;
     const float hh = 0.5f * hf;
@@ -235,32 +237,55 @@ __global__ void __launch_bounds__(DH_NT) k_dh_f32(const dbl4 *xyzq, int n_atoms,
 }
 
 // b = (4 pi / h) q_node, then every boundary row adds eps_edge * phi_ghost for
-// its ghost neighbours in the face order x-, x+, y-, y+, z-, z+.  qn (fixed
+// its ghost neighbours in the face order x-, x+, y-, y+, z-, z+; and the
+// partial sums of b^2 (one per CTA over its rows, in a fixed order).  A warp
+// takes one row (y, z) at a time, its lanes the x positions.  qn (fixed
 // point) and b may alias: each element is read before it is written.
-__global__ void k_fold_rhs(const long long *qn, const uint8_t *code, const double *ghost, Geom g,
-                           double inv_scale, double c4pi_h, double ein, double eout, double *b) {
-  const size_t n_pad = (size_t)g.px * g.ny * g.nz;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n_pad;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % g.px);
-    if (i >= g.nx) { b[e] = 0.0; continue; }
-    const size_t row = e / g.px;
-    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
-    double v = __dmul_rn(__dmul_rn((double)qn[e], inv_scale), c4pi_h);
-    const uint32_t c = code[e];
-    const long fx = (long)g.ny * g.nz, fy = (long)g.nx * g.nz, fz = (long)g.nx * g.ny;
-    if (i == 0) v = __dadd_rn(v, __dmul_rn((c & 1u) ? ein : eout, ghost[(long)k * g.ny + j]));
-    if (i == g.nx - 1) v = __dadd_rn(v, __dmul_rn((c & 2u) ? ein : eout, ghost[fx + (long)k * g.ny + j]));
-    if (j == 0) v = __dadd_rn(v, __dmul_rn((c & 4u) ? ein : eout, ghost[2 * fx + (long)k * g.nx + i]));
-    if (j == g.ny - 1)
-      v = __dadd_rn(v, __dmul_rn((c & 8u) ? ein : eout, ghost[2 * fx + fy + (long)k * g.nx + i]));
-    if (k == 0)
-      v = __dadd_rn(v, __dmul_rn((c & 16u) ? ein : eout, ghost[2 * fx + 2 * fy + (long)j * g.nx + i]));
-    if (k == g.nz - 1)
-      v = __dadd_rn(v, __dmul_rn((c & 32u) ? ein : eout,
-                                 ghost[2 * fx + 2 * fy + fz + (long)j * g.nx + i]));
-    b[e] = v;
+// scale = 4 pi / h / (fixed-point scale): the latter is a power of two, so
+// qn * scale rounds as (qn / fixed-point scale) * (4 pi / h) does.
+constexpr int FOLD_CTAS = 256, FOLD_NT = 256;
+__global__ void __launch_bounds__(FOLD_NT) k_fold_rhs(const long long *qn, const uint8_t *code,
+                                                      const double *ghost, Geom g, double scale,
+                                                      double ein, double eout, double *b,
+                                                      double *part) {
+  __shared__ double red[FOLD_NT];
+  const int rows = g.ny * g.nz, per = (rows + FOLD_CTAS - 1) / FOLD_CTAS;
+  const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const long fx = (long)g.ny * g.nz, fy = (long)g.nx * g.nz, fz = (long)g.nx * g.ny;
+  double s = 0.0;
+  for (int row = r0 + warp; row < r1; row += FOLD_NT / 32) {
+    const int j = row % g.ny, k = row / g.ny;
+    const size_t base = (size_t)row * g.px;
+    for (int i = lane; i < g.px; i += 32) {
+      const size_t e = base + i;
+      if (i >= g.nx) {
+        b[e] = 0.0;
+        continue;
+      }
+      double v = __dmul_rn((double)qn[e], scale);
+      const uint32_t c = code[e];
+      if (i == 0) v = __dadd_rn(v, __dmul_rn((c & 1u) ? ein : eout, ghost[(long)k * g.ny + j]));
+      if (i == g.nx - 1) v = __dadd_rn(v, __dmul_rn((c & 2u) ? ein : eout, ghost[fx + (long)k * g.ny + j]));
+      if (j == 0) v = __dadd_rn(v, __dmul_rn((c & 4u) ? ein : eout, ghost[2 * fx + (long)k * g.nx + i]));
+      if (j == g.ny - 1)
+        v = __dadd_rn(v, __dmul_rn((c & 8u) ? ein : eout, ghost[2 * fx + fy + (long)k * g.nx + i]));
+      if (k == 0)
+        v = __dadd_rn(v, __dmul_rn((c & 16u) ? ein : eout, ghost[2 * fx + 2 * fy + (long)j * g.nx + i]));
+      if (k == g.nz - 1)
+        v = __dadd_rn(v, __dmul_rn((c & 32u) ? ein : eout,
+                                   ghost[2 * fx + 2 * fy + fz + (long)j * g.nx + i]));
+      b[e] = v;
+      s = fma(v, v, s);
+    }
   }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = FOLD_NT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 // Explicit coefficient arrays from the packed codes (pitch px; see the layout
@@ -327,20 +352,6 @@ __global__ void k_export_lambda(const uint8_t *code, Geom g, uint8_t *lam) {
 }
 
 // Sum of squares of b, deterministic: per-CTA partials then one CTA in order.
-__global__ void k_sumsq_partial(const double *b, size_t n, double *part) {
-  __shared__ double red[256];
-  double s = 0.0;
-  const size_t per = (n + gridDim.x - 1) / gridDim.x;
-  const size_t lo = blockIdx.x * per, hi = min(n, lo + per);
-  for (size_t e = lo + threadIdx.x; e < hi; e += blockDim.x) s += b[e] * b[e];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
-}
 __global__ void k_sum_final(const double *part, int n, double *out) {
   __shared__ double red[256];
   double s = 0.0;
@@ -384,10 +395,9 @@ cudaError_t launch_setup(const SetupArgs &a, cudaStream_t st) {
   } else {
     cudaMemsetAsync(a.ghost, 0, sizeof(double) * n_ghost, st);
   }
-  k_fold_rhs<<<grid_for(n_pad, 256), 256, 0, st>>>((const long long *)a.b, a.code, a.ghost, g,
-                                                   1.0 / a.q_scale, a.c4pi_h, a.ein, a.eout, a.b);
-  k_sumsq_partial<<<256, 256, 0, st>>>(a.b, n_pad, a.scratch);
-  k_sum_final<<<1, 256, 0, st>>>(a.scratch, 256, a.bnorm2);
+  k_fold_rhs<<<FOLD_CTAS, FOLD_NT, 0, st>>>((const long long *)a.b, a.code, a.ghost, g,
+                                            a.c4pi_h / a.q_scale, a.ein, a.eout, a.b, a.scratch);
+  k_sum_final<<<1, 256, 0, st>>>(a.scratch, FOLD_CTAS, a.bnorm2);
   return cudaGetLastError();
 }
 

@@ -409,8 +409,15 @@ class Server:
         self.handle = pb_server_create(ctx.handle, int(budget_bytes), o)
         self._keep = {}
 
-    def submit(self, trajectory_id: int, spec, atoms, want_phi: bool = False) -> int:
-        out = np.empty(spec.shape, dtype=np.float64) if want_phi else None
+    def submit(self, trajectory_id: int, spec, atoms, want_phi: bool = False, phi_out=None) -> int:
+        """phi_out: a C-contiguous float64 host array of spec.shape that receives
+        phi (held until the poll that returns it); want_phi allocates one."""
+        out = phi_out
+        if out is None and want_phi:
+            out = np.empty(spec.shape, dtype=np.float64)
+        if out is not None and (out.dtype != np.float64 or out.shape != tuple(spec.shape)
+                                or not out.flags.c_contiguous):
+            raise ValueError("phi_out must be a C-contiguous float64 array of the grid's shape")
         t = pb_batch_submit(self.handle, trajectory_id, spec, atoms, out)
         self._keep[t] = out
         return t

@@ -301,3 +301,25 @@ def test_ragged_tiles(pbm, ctx, dims):
         assert rel_max(phi, ref.phi) < 1e-8
         phi, info = solve(pbm, g, p.grid, precision="f32_refine", tol=1e-10)
         assert info.status == 0 and rel_max(phi, ref.phi) < 1e-8
+
+
+def test_energy_atoms_on_and_off_the_grid(pbm, ctx):
+    """Trilinear interpolation at the last node reads only nodes of the grid;
+    an atom whose cell leaves the grid reads nothing and gives NaN."""
+    spec = inputs.random_small(8, 9, 7, 6, n_atoms=3).grid
+    rng = np.random.default_rng(11)
+    phi = rng.normal(size=spec.shape)
+    last = np.array(spec.origin) + spec.h * (np.array([spec.nx, spec.ny, spec.nz]) - 1)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def energy_of(xyz, q):
+        xyzq = torch.as_tensor(np.concatenate([xyz, q[:, None]], 1)).cuda().contiguous()
+        pbm.pb_energy_noalloc(xyzq, spec, dev(phi), out, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        return float(out.item())
+
+    e = energy_of(last[None, :], np.array([1.5]))
+    assert e == pytest.approx(0.5 * 332.0637 * 1.5 * phi[-1, -1, -1], rel=1e-14)
+    for off in ([spec.h * 0.25, 0, 0], [0, spec.h * 0.5, 0], [0, 0, 1e-3]):
+        assert np.isnan(energy_of((last + np.array(off))[None, :], np.array([1.0])))
+    assert np.isnan(energy_of(np.array(spec.origin)[None, :] - 0.1, np.array([1.0])))

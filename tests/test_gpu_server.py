@@ -156,3 +156,16 @@ def test_kernel_profile(pbm, ctx):
     # every update launch covers at most all grids, each at 13 B per node
     total_nodes = sum(p.grid.n for p in probs)
     assert kp.bytes_update <= kp.launches_update * 13 * total_nodes
+
+
+def test_zero_charge_request(pbm, ctx):
+    p = inputs.random_small(7, 21, 19, 17, n_atoms=6)
+    a = p.atoms.copy()
+    a.q = np.zeros_like(a.q)  # b = 0: the solution is phi = 0
+    phi = np.ones(p.grid.shape)
+    with pbm.Server(ctx, 4 * GB) as srv:
+        r, _ = srv.poll(srv.submit(5, p.grid, a, phi_out=phi), 60000)
+        ok, phi2 = srv.poll(srv.submit(5, p.grid, p.atoms, want_phi=True), 60000)
+    assert r.status == 0 and r.energy == 0.0 and r.info.iterations == 0
+    assert not phi.any()
+    assert ok.status == 0 and np.abs(phi2).max() > 0
