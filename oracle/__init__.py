@@ -14,6 +14,8 @@ Functions and the passage each follows:
 * ``pcg``            -- O3/O4: CG and Jacobi-preconditioned CG (Sec. 2.2, 2.4)
 * ``energy``         -- O5: 1/2 * 332.0637 * sum q phi (the energies compared in Sec. 3.1)
 * ``dense_matrix`` / ``cholesky_solve`` -- O6: explicit A and a dense solve, small grids
+* ``solvation_energy`` -- the electrostatic solvation energy of Sec. 3.1 (Figs. 1-2):
+  energy of the solvated system minus that of the reference system
 
 Every function is pinned by the CPU tests (``tests/test_oracle_*.py``) against
 closed forms, special cases and brute force; none is "parity unpinned".
@@ -51,7 +53,8 @@ class _Grid(ctypes.Structure):
                 ("h", ctypes.c_double), ("ox", ctypes.c_double), ("oy", ctypes.c_double),
                 ("oz", ctypes.c_double), ("eps_in", ctypes.c_double),
                 ("eps_out", ctypes.c_double), ("kappa_d", ctypes.c_double),
-                ("kbar2_h2", ctypes.c_double), ("kappa_mask", ctypes.c_int)]
+                ("kbar2_h2", ctypes.c_double), ("kappa_mask", ctypes.c_int),
+                ("periodic", ctypes.c_int)]
 
 
 _lib = None
@@ -66,6 +69,7 @@ def _load():
         lib.or_kappa_debye2.argtypes = [ctypes.c_double] * 3
         G = ctypes.POINTER(_Grid)
         lib.or_dielectric.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+        lib.or_dielectric_periodic.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
         lib.or_spread_charge.restype = ctypes.c_int
         lib.or_spread_charge.argtypes = [G, ctypes.c_int, _P, _P, _P]
         lib.or_dh_ghost.argtypes = [G, ctypes.c_int, _P, _P, _P]
@@ -100,7 +104,7 @@ def _cgrid(g) -> _Grid:
     kd2 = kappa_debye2(g.ionic_strength, g.temperature, g.eps_out)
     return _Grid(g.nx, g.ny, g.nz, g.h, g.origin[0], g.origin[1], g.origin[2], g.eps_in,
                  g.eps_out, float(np.sqrt(kd2)), g.eps_out * kd2 * g.h * g.h,
-                 1 if g.kappa_mask else 0)
+                 1 if g.kappa_mask else 0, 1 if getattr(g, "periodic", False) else 0)
 
 
 @dataclass
@@ -134,8 +138,8 @@ def dielectric(grid, atoms):
     lam = np.empty((nz, ny, nx), dtype=np.uint8)
     xyz = np.ascontiguousarray(atoms.xyz, dtype=np.float64)
     r = np.ascontiguousarray(atoms.r, dtype=np.float64)
-    lib.or_dielectric(ctypes.byref(g), atoms.n, _ptr(xyz), _ptr(r), _ptr(ex), _ptr(ey), _ptr(ez),
-                      _ptr(lam))
+    fn = lib.or_dielectric_periodic if g.periodic else lib.or_dielectric
+    fn(ctypes.byref(g), atoms.n, _ptr(xyz), _ptr(r), _ptr(ex), _ptr(ey), _ptr(ez), _ptr(lam))
     return ex, ey, ez, lam
 
 
@@ -195,12 +199,15 @@ def dh_points(grid, atoms, points: np.ndarray) -> np.ndarray:
 
 
 def setup(grid, atoms, ghost: Optional[np.ndarray] = None) -> Setup:
-    """O1 for one problem.  `ghost` may be passed to skip the O(atoms x faces) DH sum."""
+    """O1 for one problem.  `ghost` may be passed to skip the O(atoms x faces) DH sum.
+    A periodic grid has no boundary: no ghost values, nothing folded into b."""
     lib = _load()
     g = _cgrid(grid)
     ex, ey, ez, lam = dielectric(grid, atoms)
     qn = spread_charge(grid, atoms)
-    if ghost is None:
+    if g.periodic:
+        ghost = np.zeros(ghost_count(grid))
+    elif ghost is None:
         ghost = dh_ghost(grid, atoms)
     b = np.empty(grid.shape)
     lib.or_rhs(ctypes.byref(g), _ptr(qn), _ptr(ghost), _ptr(ex), _ptr(ey), _ptr(ez), _ptr(b))
@@ -213,8 +220,12 @@ def operator_from(grid, ex, ey, ez, lam) -> Setup:
     """A Setup holding only an operator (no charges), e.g. for random coefficients."""
     lib = _load()
     g = _cgrid(grid)
-    ex, ey, ez = (np.ascontiguousarray(a, dtype=np.float64) for a in (ex, ey, ez))
+    ex, ey, ez = (np.array(a, dtype=np.float64, order="C") for a in (ex, ey, ez))
     lam = np.ascontiguousarray(lam, dtype=np.uint8)
+    if g.periodic:  # the entries at -1 are the wrap-around edges (entries n-1)
+        ex[:, :, 0] = ex[:, :, -1]
+        ey[:, 0, :] = ey[:, -1, :]
+        ez[0, :, :] = ez[-1, :, :]
     diag = np.empty(grid.shape)
     lib.or_diag(ctypes.byref(g), _ptr(ex), _ptr(ey), _ptr(ez), _ptr(lam), _ptr(diag))
     z = np.zeros(grid.shape)
@@ -282,3 +293,20 @@ def relres(s: Setup, phi: np.ndarray, b: Optional[np.ndarray] = None) -> float:
     b = s.b if b is None else b.reshape(s.grid.shape)
     r = b - apply(s, phi)
     return float(np.linalg.norm(r.ravel()) / np.linalg.norm(b.ravel()))
+
+
+def reference_grid(grid):
+    """The reference system of the solvation energy: eps_in everywhere (the
+    solute in a medium of its own dielectric) and no salt."""
+    return grid.replace(eps_out=grid.eps_in, ionic_strength=0.0)
+
+
+def solvation_energy(grid, atoms, tol: float = 1e-10):
+    """Electrostatic solvation energy (Sec. 3.1, Figs. 1-2): E of the solvated
+    system (grid as given) minus E of the reference system, each from a
+    Jacobi-PCG solve to `tol`.  Returns (dG, E_solvated, E_reference)."""
+    s1 = setup(grid, atoms)
+    e1 = energy(s1, pcg(s1, tol=tol).phi)
+    s0 = setup(reference_grid(grid), atoms)
+    e0 = energy(s0, pcg(s0, tol=tol).phi)
+    return e1 - e0, e1, e0

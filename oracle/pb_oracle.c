@@ -19,6 +19,11 @@
  * midpoint of an x-edge as o + (i + 0.5)*h.  Dirichlet values live on the ghost
  * layer i = -1, i = nx (and likewise in y, z); the seven-point stencil reads
  * only face ghosts.
+ *
+ * Periodic grids (the periodic boundary of the paper's Fig. 2) have period
+ * n*h on each axis and no ghost layer: node i's neighbours are i-1 and i+1
+ * modulo n, and the edge array entry at i = -1 repeats the edge between
+ * nodes n-1 and 0 (entry n-1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -38,7 +43,10 @@ typedef struct {
     double kappa_d;    /* inverse Debye length, 1/A (0 for no salt)            */
     double kbar2_h2;   /* eps_out * kappa_d^2 * h^2: the Boltzmann diagonal term */
     int kappa_mask;    /* 1: lambda = 0 inside atoms; 0: lambda = 1 everywhere */
+    int periodic;      /* 1: periodic on every axis (no ghost layer)            */
 } or_grid;
+
+static long wrap(long i, long n) { return ((i % n) + n) % n; }
 
 static size_t nid(const or_grid *g, long i, long j, long k) {
     return (size_t)i + (size_t)g->nx * ((size_t)j + (size_t)g->ny * (size_t)k);
@@ -146,6 +154,54 @@ void or_dielectric(const or_grid *g, int n_atoms, const double *xyz, const doubl
     }
 }
 
+/* The same map on a periodic grid: an edge takes eps_in when some periodic
+ * image of its midpoint lies strictly inside an atom sphere, a node gets
+ * lambda = 0 likewise.  Each atom visits its bounding box in unwrapped
+ * indices (no clamping); points are placed at their unwrapped coordinates
+ * o + i*h (i + 0.5 for midpoints), tested against the atom, and the result
+ * lands on the element at the wrapped index.  The entry at i = -1 then copies
+ * the edge between nodes n-1 and 0. */
+void or_dielectric_periodic(const or_grid *g, int n_atoms, const double *xyz, const double *rad,
+                            double *ex, double *ey, double *ez, uint8_t *lam) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const double h = g->h;
+    size_t nex = (size_t)(nx + 1) * ny * nz, ney = (size_t)nx * (ny + 1) * nz,
+           nez = (size_t)nx * ny * (nz + 1), nn = (size_t)nx * ny * nz;
+    for (size_t t = 0; t < nex; t++) ex[t] = g->eps_out;
+    for (size_t t = 0; t < ney; t++) ey[t] = g->eps_out;
+    for (size_t t = 0; t < nez; t++) ez[t] = g->eps_out;
+    for (size_t t = 0; t < nn; t++) lam[t] = 1;
+    for (int a = 0; a < n_atoms; a++) {
+        double ax = xyz[3 * a], ay = xyz[3 * a + 1], az = xyz[3 * a + 2], r = rad[a];
+        double r2 = r * r;
+        long i0 = (long)floor((ax - r - g->ox) / h) - 1, i1 = (long)ceil((ax + r - g->ox) / h) + 1;
+        long j0 = (long)floor((ay - r - g->oy) / h) - 1, j1 = (long)ceil((ay + r - g->oy) / h) + 1;
+        long k0 = (long)floor((az - r - g->oz) / h) - 1, k1 = (long)ceil((az + r - g->oz) / h) + 1;
+        for (long k = k0; k <= k1; k++)
+            for (long j = j0; j <= j1; j++)
+                for (long i = i0; i <= i1; i++) {
+                    double nxc = g->ox + (double)i * h, nyc = g->oy + (double)j * h,
+                           nzc = g->oz + (double)k * h;
+                    long iw = wrap(i, nx), jw = wrap(j, ny), kw = wrap(k, nz);
+                    /* the x-, y- and z-edges whose lower node is (i, j, k) */
+                    if (inside(g->ox + ((double)i + 0.5) * h, nyc, nzc, ax, ay, az, r2))
+                        ex[exid(g, iw, jw, kw)] = g->eps_in;
+                    if (inside(nxc, g->oy + ((double)j + 0.5) * h, nzc, ax, ay, az, r2))
+                        ey[eyid(g, iw, jw, kw)] = g->eps_in;
+                    if (inside(nxc, nyc, g->oz + ((double)k + 0.5) * h, ax, ay, az, r2))
+                        ez[ezid(g, iw, jw, kw)] = g->eps_in;
+                    if (g->kappa_mask && inside(nxc, nyc, nzc, ax, ay, az, r2))
+                        lam[nid(g, iw, jw, kw)] = 0;
+                }
+    }
+    for (long k = 0; k < nz; k++)
+        for (long j = 0; j < ny; j++) ex[exid(g, -1, j, k)] = ex[exid(g, nx - 1, j, k)];
+    for (long k = 0; k < nz; k++)
+        for (long i = 0; i < nx; i++) ey[eyid(g, i, -1, k)] = ey[eyid(g, i, ny - 1, k)];
+    for (long j = 0; j < ny; j++)
+        for (long i = 0; i < nx; i++) ez[ezid(g, i, j, -1)] = ez[ezid(g, i, j, nz - 1)];
+}
+
 /* Grid charges q(i,j,k) (Eq. 3: the charge within the cube centred on the
  * node) by trilinear spreading of each atom onto the 8 nodes of its cell:
  * f = (x - o)/h, i0 = floor(f), w = f - i0; corner weights w or 1 - w per axis,
@@ -161,8 +217,9 @@ int or_spread_charge(const or_grid *g, int n_atoms, const double *xyz, const dou
         double fy = (xyz[3 * a + 1] - g->oy) / g->h;
         double fz = (xyz[3 * a + 2] - g->oz) / g->h;
         double flx = floor(fx), fly = floor(fy), flz = floor(fz);
-        if (!(flx >= 0.0 && flx + 1.0 <= nx - 1) || !(fly >= 0.0 && fly + 1.0 <= ny - 1) ||
-            !(flz >= 0.0 && flz + 1.0 <= nz - 1))
+        if (!g->periodic && (!(flx >= 0.0 && flx + 1.0 <= nx - 1) ||
+                             !(fly >= 0.0 && fly + 1.0 <= ny - 1) ||
+                             !(flz >= 0.0 && flz + 1.0 <= nz - 1)))
             return OR_ERR_ARG;
         long i0 = (long)flx, j0 = (long)fly, k0 = (long)flz;
         double w[3][2];
@@ -175,7 +232,8 @@ int or_spread_charge(const or_grid *g, int n_atoms, const double *xyz, const dou
                     double c = q[a] * w[0][di];
                     c = c * w[1][dj];
                     c = c * w[2][dk];
-                    q_node[nid(g, i0 + di, j0 + dj, k0 + dk)] += c;
+                    /* periodic: the corners wrap around */
+                    q_node[nid(g, wrap(i0 + di, nx), wrap(j0 + dj, ny), wrap(k0 + dk, nz))] += c;
                 }
     }
     return OR_OK;
@@ -246,6 +304,7 @@ void or_rhs(const or_grid *g, const double *q_node, const double *ghost, const d
     const double c = 4.0 * M_PI / g->h;
     size_t nn = (size_t)nx * ny * nz, off = 0;
     for (size_t t = 0; t < nn; t++) b[t] = q_node[t] * c;
+    if (g->periodic) return; /* no boundary to fold */
     for (int side = 0; side < 2; side++) {
         long i = side ? nx - 1 : 0, ie = side ? nx - 1 : -1;
         for (long k = 0; k < nz; k++)
@@ -304,12 +363,21 @@ void or_apply(const or_grid *g, const double *ex, const double *ey, const double
             for (long i = 0; i < nx; i++) {
                 size_t c = nid(g, i, j, k);
                 double s = 0.0;
-                if (i > 0) s += ex[exid(g, i - 1, j, k)] * u[nid(g, i - 1, j, k)];
-                if (i < nx - 1) s += ex[exid(g, i, j, k)] * u[nid(g, i + 1, j, k)];
-                if (j > 0) s += ey[eyid(g, i, j - 1, k)] * u[nid(g, i, j - 1, k)];
-                if (j < ny - 1) s += ey[eyid(g, i, j, k)] * u[nid(g, i, j + 1, k)];
-                if (k > 0) s += ez[ezid(g, i, j, k - 1)] * u[nid(g, i, j, k - 1)];
-                if (k < nz - 1) s += ez[ezid(g, i, j, k)] * u[nid(g, i, j, k + 1)];
+                if (g->periodic) { /* every neighbour exists, modulo n */
+                    s += ex[exid(g, i - 1, j, k)] * u[nid(g, wrap(i - 1, nx), j, k)];
+                    s += ex[exid(g, i, j, k)] * u[nid(g, wrap(i + 1, nx), j, k)];
+                    s += ey[eyid(g, i, j - 1, k)] * u[nid(g, i, wrap(j - 1, ny), k)];
+                    s += ey[eyid(g, i, j, k)] * u[nid(g, i, wrap(j + 1, ny), k)];
+                    s += ez[ezid(g, i, j, k - 1)] * u[nid(g, i, j, wrap(k - 1, nz))];
+                    s += ez[ezid(g, i, j, k)] * u[nid(g, i, j, wrap(k + 1, nz))];
+                } else {
+                    if (i > 0) s += ex[exid(g, i - 1, j, k)] * u[nid(g, i - 1, j, k)];
+                    if (i < nx - 1) s += ex[exid(g, i, j, k)] * u[nid(g, i + 1, j, k)];
+                    if (j > 0) s += ey[eyid(g, i, j - 1, k)] * u[nid(g, i, j - 1, k)];
+                    if (j < ny - 1) s += ey[eyid(g, i, j, k)] * u[nid(g, i, j + 1, k)];
+                    if (k > 0) s += ez[ezid(g, i, j, k - 1)] * u[nid(g, i, j, k - 1)];
+                    if (k < nz - 1) s += ez[ezid(g, i, j, k)] * u[nid(g, i, j, k + 1)];
+                }
                 au[c] = diag[c] * u[c] - s;
             }
 }
@@ -398,6 +466,15 @@ void or_dense_matrix(const or_grid *g, const double *ex, const double *ey, const
             for (long i = 0; i < nx; i++) {
                 size_t c = nid(g, i, j, k);
                 A[c * n + c] = diag[c];
+                if (g->periodic) { /* accumulate: on n = 2 two edges join the same pair */
+                    A[c * n + nid(g, wrap(i - 1, nx), j, k)] -= ex[exid(g, i - 1, j, k)];
+                    A[c * n + nid(g, wrap(i + 1, nx), j, k)] -= ex[exid(g, i, j, k)];
+                    A[c * n + nid(g, i, wrap(j - 1, ny), k)] -= ey[eyid(g, i, j - 1, k)];
+                    A[c * n + nid(g, i, wrap(j + 1, ny), k)] -= ey[eyid(g, i, j, k)];
+                    A[c * n + nid(g, i, j, wrap(k - 1, nz))] -= ez[ezid(g, i, j, k - 1)];
+                    A[c * n + nid(g, i, j, wrap(k + 1, nz))] -= ez[ezid(g, i, j, k)];
+                    continue;
+                }
                 if (i > 0) A[c * n + nid(g, i - 1, j, k)] = -ex[exid(g, i - 1, j, k)];
                 if (i < nx - 1) A[c * n + nid(g, i + 1, j, k)] = -ex[exid(g, i, j, k)];
                 if (j > 0) A[c * n + nid(g, i, j - 1, k)] = -ey[eyid(g, i, j - 1, k)];

@@ -43,7 +43,8 @@ class GridSpec:
     ``nx*ny*nz`` nodes and the Dirichlet values on a ghost layer one spacing
     outside the box.  ``coef`` chooses how the CUDA library stores the
     dielectric coefficients ("packed", "f32", "bf16", "f64"); ``dh`` chooses the
-    precision of the Debye-Hueckel boundary sum ("f64" or "f32").
+    precision of the Debye-Hueckel boundary sum ("f64" or "f32").  ``periodic``
+    makes every axis periodic with period n*h (no ghost layer, no boundary sum).
     """
 
     nx: int
@@ -58,6 +59,7 @@ class GridSpec:
     kappa_mask: bool = True  # lambda = 0 inside atoms (ion exclusion)
     coef: str = "packed"
     dh: str = "f64"
+    periodic: bool = False
 
     @property
     def n(self) -> int:

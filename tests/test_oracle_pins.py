@@ -398,13 +398,9 @@ def test_energy_adjoint_of_spreading():
 
 # --------------------------------------------------------------------------- physics
 
-def born_dG(n, h):
-    p = inputs.single_charge(n, h, ionic_strength=0.0)
-    s1 = oracle.setup(p.grid, p.atoms)
-    r1 = oracle.pcg(s1, tol=1e-9)
-    s0 = oracle.setup(p.grid.replace(eps_out=p.grid.eps_in), p.atoms)
-    r0 = oracle.pcg(s0, tol=1e-9)
-    return oracle.energy(s1, r1.phi) - oracle.energy(s0, r0.phi)
+def born_dG(n, h, ionic_strength=0.0):
+    p = inputs.single_charge(n, h, ionic_strength=ionic_strength)
+    return oracle.solvation_energy(p.grid, p.atoms, tol=1e-9)[0]
 
 
 def test_born_ion_converges():
