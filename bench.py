@@ -41,9 +41,12 @@ METRIC = "solves/s, p50/p99 @1e-6 rel resid: served FP32+refine vs plain FP64 PC
 BATCH_METRIC = "solves/s @1e-6 rel resid: batch of 256 snapshots, FP32+refine"
 SERVING = "serving"
 BATCH = "batch256"
+SOLVATION = "solvation129"
+SOLVATION_METRIC = "solvation energies/s @1e-6 rel resid (two solves each), FP32+refine"
 WORKLOADS = {
     SERVING: None,
     BATCH: None,
+    SOLVATION: inputs.globule_129,
     "globule33": inputs.small_33,
     "globule129": inputs.globule_129,
     "globule257": inputs.globule_257,
@@ -646,6 +649,19 @@ def run_reference(args):
         iters_of = lambda pr: scale * pr.grid.nx
         name = ("batch of 256 snapshots: 1,000-atom cluster, sigma 0.3 A, grids 49^3-97^3, "
                 "one server batch")
+    elif args.workload == SOLVATION:
+        # each step: the solvated and the reference system of one snapshot
+        problem = WORKLOADS[args.workload]()
+        ref_grid = oracle.reference_grid(problem.grid)
+        atoms = snapshots(problem, args.warmup + args.steps, seed=100)
+        full = {g.eps_out: oracle.pcg(oracle.setup(g, atoms[0]), tol=args.tol).iters
+                for g in (problem.grid, ref_grid)}
+        probs = []
+        for a in atoms:
+            probs.append([inputs.Problem("solvated", problem.grid, a),
+                          inputs.Problem("reference", ref_grid, a)])
+        iters_of = lambda pr: full[pr.grid.eps_out]
+        name = "solvation energy of 129^3 globule snapshots (2,500 atoms)"
     else:
         problem = WORKLOADS[args.workload]()
         probs = [inputs.Problem(problem.name, problem.grid, a)
@@ -654,30 +670,103 @@ def run_reference(args):
         iters_of = lambda pr: full.iters
         name = problem.name
     times = []
-    for i, pr in enumerate(probs):
-        t_fixed, t_iter, _ = oracle_solve_sample(pr, pr.atoms, args.tol, args.cpu_sample_iters)
+    for i, step in enumerate(probs):
+        t = 0.0
+        for pr in (step if isinstance(step, list) else [step]):
+            t_fixed, t_iter, _ = oracle_solve_sample(pr, pr.atoms, args.tol, args.cpu_sample_iters)
+            t += t_fixed + t_iter * iters_of(pr)
         if i >= args.warmup:
-            times.append(t_fixed + t_iter * iters_of(pr))
+            times.append(t)
     total = sum(times)
     val = args.steps / total
+    unit = "energies/s" if args.workload == SOLVATION else "solves/s"
     print(json.dumps({
-        "impl": "reference", "metric": BATCH_METRIC if args.workload == BATCH else METRIC,
-        "value": val, "unit": "solves/s", "n_gpus": world,
+        "impl": "reference",
+        "metric": {BATCH: BATCH_METRIC, SOLVATION: SOLVATION_METRIC}.get(args.workload, METRIC),
+        "value": val, "unit": unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": name, "tol": args.tol, "solver": "oracle FP64 Jacobi-PCG"},
         "latency_ms": {"p50": pct([t * 1e3 for t in times], 50),
                        "p99": pct([t * 1e3 for t in times], 99)},
-        "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": unit, "cores": 1, "kind": "oracle",
                          "sample": (f"per step one request: oracle dielectric + charges, "
                                     f"Debye-Hueckel on 2048 ghost nodes scaled to all, "
                                     f"{args.cpu_sample_iters} FP64 Jacobi-PCG iterations scaled "
                                     f"to a full solve"),
                          "cpu": platform_cpu()},
-        "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# --------------------------------------------------------------------------- solvation energy
+
+def run_solvation(args):
+    """The solvation-energy pipeline (pb_solvation_energy) on snapshots of the
+    129^3 globule: per step, setup + solve + energy of the solvated system and
+    of the reference system (eps_in everywhere, no salt), one grid at a time."""
+    import torch
+    from paper_1704_02745_gb300 import pb
+    from paper_1704_02745_gb300 import build as pbbuild
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    pbbuild.build()
+    torch.cuda.set_device(local)
+    problem = inputs.globule_129()
+    spec = problem.grid.replace(dh=args.dh)
+    snaps = snapshots(problem, 8, seed=100 + rank)
+    ctx = pb.Context(local)
+    phi = torch.zeros(spec.shape, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    kw = dict(precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol)
+    times, outs = [], []
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            if world > 1:
+                torch.distributed.barrier()
+            st0 = ctx.stats()
+            clocks = ClockSampler(local)
+            clocks.start()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ctx.solvation(spec, snaps[i % len(snaps)], phi, **kw)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            outs.append(out)
+    clk = clocks.stop()
+    st1 = ctx.stats()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t[0])
+    if rank == 0:
+        print(json.dumps({
+            "metric": SOLVATION_METRIC, "value": world * args.steps / total, "unit": "energies/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "solvation energy of 129^3 globule snapshots (2,500 atoms)",
+                       "tol": args.tol, "inner_tol": args.inner_tol, "debye_hueckel_sum": args.dh,
+                       "l2": "256 MB buffer written between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "dG_kcal": [o.dG for o in outs[:3]],
+            "iterations_mean": {"solvated": float(np.mean([o.solv.iterations for o in outs])),
+                                "reference": float(np.mean([o.ref.iterations for o in outs]))},
+            "e2e": {"value": world * args.steps / total, "unit": "energies/s",
+                    "h2d_bytes_per_step": int((st1[1] - st0[1]) / args.steps),
+                    "d2h_bytes_per_step": int((st1[2] - st0[2]) / args.steps),
+                    "note": "host atoms in, energies out: the call is end to end"},
+            "gpu_launches": int(st1[0] - st0[0]), "clocks": clk,
+        }), flush=True)
+    ctx.close()
 
 
 # --------------------------------------------------------------------------- batch of snapshots
@@ -803,6 +892,8 @@ def main():
         run_serving(args)
     elif args.workload == BATCH:
         run_batch(args)
+    elif args.workload == SOLVATION:
+        run_solvation(args)
     else:
         run_ours(args)
 

@@ -84,6 +84,12 @@ typedef struct {
     int kappa_mask;           /* 1: lambda = 0 at nodes strictly inside an atom; 0: lambda = 1 */
     int coef;                 /* PB_COEF_*: storage of the FP32 operator's coefficients */
     int dh_precision;         /* pb_dtype of the Debye-Hueckel boundary sum */
+    int periodic;             /* 1: every axis periodic with period n*h (the periodic boundary
+                                 of Fig. 2): node i's neighbours are i-1, i+1 modulo n, an edge
+                                 or node is inside an atom if some periodic image is, charges
+                                 spread modulo n, no boundary sum.  Needs n >= 3 per axis and
+                                 ionic_strength > 0 (without salt, or with every node inside
+                                 an atom under kappa_mask, A is singular) */
 } pb_grid_desc;
 
 typedef struct {
@@ -107,7 +113,7 @@ typedef struct {
     double relres_true;  /* ||b - A phi|| / ||b|| evaluated in FP64 at exit */
     /* profile = 1 only: summed device time (ms) and count of the launches of
      * the stencil pass doing CG work, of the update pass doing CG work, and of
-     * the stencil pass doing the FP64 residual (refinement) work */
+     * the residual pass doing the FP64 residual (refinement) work */
     double ms_stencil, ms_update, ms_resid;
     int n_stencil, n_update, n_resid;
 } pb_solve_info;
@@ -170,6 +176,24 @@ pb_status pb_pcg_solve(pb_grid *grid, const pb_solve_opts *opts, double *phi,
  * Sec. 3.1 compares.  Evaluated in FP64 as sum_atoms q_a * (trilinear
  * interpolation of phi at x_a), the adjoint of the charge spreading. */
 pb_status pb_energy(pb_grid *grid, const double *phi, double *energy_kcal);
+
+/* Electrostatic solvation energy, the quantity Sec. 3.1 (Figs. 1-2) compares:
+ * dG = E_solv - E_ref (kcal/mol), where E_solv is the energy of the solved
+ * system `desc` and E_ref that of the reference system with eps_out replaced
+ * by eps_in (the solute's own dielectric everywhere) and no salt, on the same
+ * grid and atoms.  Runs setup, solve (opts) and energy for the solvated
+ * system, then for the reference system cold-started; one grid is held at a
+ * time.  phi: DEVICE array of nx*ny*nz doubles, borrowed: phi0 of the
+ * solvated solve if opts->warm_start, its solution on return.  Returns the
+ * first non-OK solve status (the results are still filled in).  A periodic
+ * desc is PB_ERR_ARG: its reference system (no salt) has a singular A. */
+typedef struct {
+    double dG, e_solv, e_ref;   /* kcal/mol */
+    pb_solve_info solv, ref;    /* the two solves */
+} pb_solvation;
+pb_status pb_solvation_energy(pb_ctx *ctx, const pb_grid_desc *desc, int n_atoms,
+                              const double *xyz, const double *q, const double *radius,
+                              const pb_solve_opts *opts, double *phi, pb_solvation *out);
 
 /* Export a setup array to HOST memory for inspection (dense layouts):
  *   PB_EXPORT_EPS_X  double (nz, ny, nx+1): edge between x-nodes i-1 and i at [.., i]

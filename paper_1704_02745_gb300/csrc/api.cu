@@ -135,6 +135,11 @@ pb_status pb_check_desc(const pb_grid_desc *d) {
   if (d->coef < PB_COEF_PACKED || d->coef > PB_COEF_F64) return pb_fail(PB_ERR_ARG, "bad coef");
   if (d->dh_precision != PB_F64 && d->dh_precision != PB_F32)
     return pb_fail(PB_ERR_ARG, "bad dh_precision");
+  if (d->periodic != 0 && d->periodic != 1) return pb_fail(PB_ERR_ARG, "bad periodic flag");
+  if (d->periodic && (d->nx < 3 || d->ny < 3 || d->nz < 3))
+    return pb_fail(PB_ERR_ARG, "a periodic grid needs at least 3 nodes per axis");
+  if (d->periodic && !(d->ionic_strength > 0))
+    return pb_fail(PB_ERR_ARG, "a periodic grid needs salt (ionic_strength > 0): without it A is singular");
   return PB_OK;
 }
 
@@ -306,7 +311,7 @@ pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_g
   g->d = *desc;
   const int px = pitch_of(desc->nx);
   g->g = Geom{desc->nx, desc->ny, desc->nz, px, desc->h, desc->origin[0], desc->origin[1],
-              desc->origin[2]};
+              desc->origin[2], desc->periodic};
   g->n_pad = (size_t)px * desc->ny * desc->nz;
   const double kd2 = debye_kappa2(desc->ionic_strength, desc->temperature, desc->eps_out);
   g->kappa = std::sqrt(kd2);
@@ -474,6 +479,7 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   }
   I.st_base = 0; I.ch_base = 0;
   I.mode = mode;
+  I.periodic = g->d.periodic;
   I.precond = o ? (o->precond == PB_PRECOND_JACOBI) : 1;
   I.coef = coef;
   I.max_iter = o ? o->max_iter : 0;
@@ -781,14 +787,59 @@ extern "C" pb_status pb_energy(pb_grid *g, const double *phi, double *energy) {
   if (!g || !phi || !energy) return pb_fail(PB_ERR_ARG, "pb_energy: NULL argument");
   CK(cudaSetDevice(g->ctx->device));
   cudaStream_t s = g->ctx->stream;
-  CK(launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.nx, g->d.h, g->d.origin[0],
-                   g->d.origin[1], g->d.origin[2], phi, g->scratch + SCR_ENERGY_PART,
-                   g->scratch + SCR_ENERGY, s));
+  CK(launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->d.nx, g->d.periodic, g->d.h,
+                   g->d.origin[0], g->d.origin[1], g->d.origin[2], phi,
+                   g->scratch + SCR_ENERGY_PART, g->scratch + SCR_ENERGY, s));
   CK(cudaMemcpyAsync(energy, g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost, s));
   g->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;
   g->ctx->stats->d2h += sizeof(double);
   CK(cudaStreamSynchronize(s));
   return PB_OK;
+}
+
+// Solvation energy (Sec. 3.1): the solved system, then the reference system
+// (eps_out -> eps_in, no salt), one grid at a time.
+extern "C" pb_status pb_solvation_energy(pb_ctx *ctx, const pb_grid_desc *desc, int n_atoms,
+                                         const double *xyz, const double *q, const double *radius,
+                                         const pb_solve_opts *opts, double *phi, pb_solvation *out) {
+  if (!ctx || !desc || !opts || !phi || !out)
+    return pb_fail(PB_ERR_ARG, "pb_solvation_energy: NULL argument");
+  memset(out, 0, sizeof(*out));
+  pb_status st = pb_check_desc(desc);
+  if (st) return st;
+  if ((st = check_opts(opts))) return st;
+  if (desc->periodic)
+    return pb_fail(PB_ERR_ARG, "pb_solvation_energy: the reference system of a periodic grid "
+                               "has no salt, and its operator is singular");
+  CK(cudaSetDevice(ctx->device));
+  const size_t n = (size_t)desc->nx * desc->ny * desc->nz;
+  pb_status first = PB_OK;
+  auto solve_one = [&](const pb_grid_desc *d, const pb_solve_opts *o, double *x, double *e,
+                       pb_solve_info *info) -> pb_status {
+    pb_grid *g = nullptr;
+    pb_status s = pb_setup_grid(ctx, d, n_atoms, xyz, q, radius, &g);
+    if (s) return s;
+    s = pb_pcg_solve(g, o, x, info);
+    if (s == PB_OK || s == PB_ERR_NOT_CONVERGED || s == PB_ERR_BREAKDOWN) {
+      if (s && !first) first = s;
+      s = pb_energy(g, x, e);
+    }
+    pb_free_grid(g);
+    return s;
+  };
+  if ((st = solve_one(desc, opts, phi, &out->e_solv, &out->solv))) return st;
+  pb_grid_desc d0 = *desc;
+  d0.eps_out = desc->eps_in;
+  d0.ionic_strength = 0.0;
+  pb_solve_opts o0 = *opts;
+  o0.warm_start = 0;
+  double *x0 = nullptr;
+  if ((st = pb_dalloc((void **)&x0, n * sizeof(double)))) return st;
+  st = solve_one(&d0, &o0, x0, &out->e_ref, &out->ref);
+  cudaFree(x0);
+  if (st) return st;
+  out->dG = out->e_solv - out->e_ref;
+  return first;
 }
 
 extern "C" pb_status pb_grid_export(pb_grid *g, int what, void *dst, size_t bytes) {

@@ -62,7 +62,7 @@ extern "C" pb_status pb_energy_noalloc(int n_atoms, const double *xyzq, int nx, 
   }
   // Every partial the final sum reads is written by this call first, so the
   // array needs no clearing; calls that overlap on the GPU share it and race.
-  e = launch_energy((const dbl4 *)xyzq, n_atoms, nx, ny, nz, nx, h, origin[0], origin[1], origin[2], phi,
+  e = launch_energy((const dbl4 *)xyzq, n_atoms, nx, ny, nz, nx, 0, h, origin[0], origin[1], origin[2], phi,
                     scratch, energy, (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return pb_fail(PB_ERR_CUDA, std::string("energy kernels: ") + cudaGetErrorString(e));
   return PB_OK;

@@ -49,12 +49,22 @@ __global__ void k_apply(const Inst *dI, const T *u, T *au) {
     const size_t e = row * I.px + i;
     const NodeCoef<T> c = node_coef<T, CM>(I, e, k);
     T s = 0;
-    if (i > 0) s += c.exm * u[t - 1];
-    if (i < nx - 1) s += c.exp * u[t + 1];
-    if (j > 0) s += c.eym * u[t - nx];
-    if (j < ny - 1) s += c.eyp * u[t + nx];
-    if (k > 0) s += c.ezm * u[t - (size_t)nx * ny];
-    if (k < nz - 1) s += c.ezp * u[t + (size_t)nx * ny];
+    if (I.periodic) {  // neighbours modulo n
+      const size_t rowb = t - i, pl = (size_t)nx * ny, plb = t - (size_t)k * pl;
+      s += c.exm * u[rowb + (i > 0 ? i - 1 : nx - 1)];
+      s += c.exp * u[rowb + (i < nx - 1 ? i + 1 : 0)];
+      s += c.eym * u[t - (size_t)j * nx + (size_t)(j > 0 ? j - 1 : ny - 1) * nx];
+      s += c.eyp * u[t - (size_t)j * nx + (size_t)(j < ny - 1 ? j + 1 : 0) * nx];
+      s += c.ezm * u[plb + (size_t)(k > 0 ? k - 1 : nz - 1) * pl];
+      s += c.ezp * u[plb + (size_t)(k < nz - 1 ? k + 1 : 0) * pl];
+    } else {
+      if (i > 0) s += c.exm * u[t - 1];
+      if (i < nx - 1) s += c.exp * u[t + 1];
+      if (j > 0) s += c.eym * u[t - nx];
+      if (j < ny - 1) s += c.eyp * u[t + nx];
+      if (k > 0) s += c.ezm * u[t - (size_t)nx * ny];
+      if (k < nz - 1) s += c.ezp * u[t + (size_t)nx * ny];
+    }
     au[t] = c.diag * u[t] - s;
   }
 }
@@ -84,10 +94,11 @@ cudaError_t launch_apply(const Inst &I, const Inst *dI, const void *u, void *au,
 // CTA sums them in order (deterministic).
 constexpr int EN_NT = 256;
 // px: row pitch of phi in elements (nx for a dense array).  An atom whose
-// trilinear cell leaves the grid reads nothing and makes the energy NaN.
+// trilinear cell leaves the grid reads nothing and makes the energy NaN; on a
+// periodic grid the cell's corners wrap modulo n.
 __global__ void k_energy_partial(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, int px,
-                                 double h, double ox, double oy, double oz, const double *phi,
-                                 double *part) {
+                                 int periodic, double h, double ox, double oy, double oz,
+                                 const double *phi, double *part) {
   __shared__ double red[EN_NT];
   double acc = 0.0;
   const int a = blockIdx.x * EN_NT + threadIdx.x;
@@ -105,7 +116,8 @@ __global__ void k_energy_partial(const dbl4 *xyzq, int n_atoms, int nx, int ny, 
       w[d][1] = __dsub_rn(f[d], fl);
       w[d][0] = __dsub_rn(1.0, w[d][1]);
       // the cell's upper corner may be the last node only when its weight is 0
-      inside = inside && fl >= 0.0 && (c0[d] + 1 < n[d] || (c0[d] + 1 == n[d] && w[d][1] == 0.0));
+      if (periodic) inside = inside && isfinite(fl);
+      else inside = inside && fl >= 0.0 && (c0[d] + 1 < n[d] || (c0[d] + 1 == n[d] && w[d][1] == 0.0));
     }
     if (!inside) {
       acc = __longlong_as_double(0x7ff8000000000000LL);  // NaN
@@ -114,8 +126,15 @@ __global__ void k_energy_partial(const dbl4 *xyzq, int n_atoms, int nx, int ny, 
         for (int dj = 0; dj < 2; dj++)
           for (int di = 0; di < 2; di++) {
             const double c = __dmul_rn(__dmul_rn(__dmul_rn(A.w, w[0][di]), w[1][dj]), w[2][dk]);
-            if (c0[0] + di >= nx || c0[1] + dj >= ny || c0[2] + dk >= nz) continue;  // weight 0
-            const size_t t = ((size_t)(c0[2] + dk) * ny + (c0[1] + dj)) * px + (c0[0] + di);
+            long ci = c0[0] + di, cj = c0[1] + dj, ck = c0[2] + dk;
+            if (periodic) {
+              ci = ((ci % nx) + nx) % nx;
+              cj = ((cj % ny) + ny) % ny;
+              ck = ((ck % nz) + nz) % nz;
+            } else if (ci >= nx || cj >= ny || ck >= nz) {
+              continue;  // weight 0
+            }
+            const size_t t = ((size_t)ck * ny + cj) * px + ci;
             acc += c * phi[t];
           }
     }
@@ -141,13 +160,13 @@ __global__ void k_energy_final(const double *part, int n, double *out) {
   if (threadIdx.x == 0) *out = 0.5 * 332.0637 * red[0];
 }
 
-cudaError_t launch_energy(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, int px, double h,
-                          double ox, double oy, double oz, const double *phi, double *scratch,
-                          double *out, cudaStream_t st) {
+cudaError_t launch_energy(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, int px,
+                          int periodic, double h, double ox, double oy, double oz,
+                          const double *phi, double *scratch, double *out, cudaStream_t st) {
   const int blocks = n_atoms > 0 ? (n_atoms + EN_NT - 1) / EN_NT : 0;
   if (blocks > 0)
-    k_energy_partial<<<blocks, EN_NT, 0, st>>>(xyzq, n_atoms, nx, ny, nz, px, h, ox, oy, oz, phi,
-                                               scratch);
+    k_energy_partial<<<blocks, EN_NT, 0, st>>>(xyzq, n_atoms, nx, ny, nz, px, periodic, h, ox, oy,
+                                               oz, phi, scratch);
   k_energy_final<<<1, EN_NT, 0, st>>>(scratch, blocks, out);
   return cudaGetLastError();
 }

@@ -83,7 +83,7 @@ struct alignas(64) Inst {
   int st_base, ch_base;               // offsets into the partial-sum arrays
   int rtz, n_rs, rs_base;             // residual pass: the stencil tiles cut into z
                                       // pieces of rtz planes, their count, partials
-  int mode, precond, coef, max_iter, max_outer, pad0;
+  int mode, precond, coef, max_iter, max_outer, periodic;
   double tol, inner_tol, bnorm;
   size_t n_pad;                       // nz*ny*px
   const uint8_t *code;

@@ -561,9 +561,9 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
         phi = s->d_dense;
         pitch = g->d.nx;
       }
-      launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, pitch, g->d.h, g->d.origin[0],
-                    g->d.origin[1], g->d.origin[2], phi, g->scratch + SCR_ENERGY_PART,
-                    g->scratch + SCR_ENERGY, s->stream);
+      launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, pitch, g->d.periodic, g->d.h,
+                    g->d.origin[0], g->d.origin[1], g->d.origin[2], phi,
+                    g->scratch + SCR_ENERGY_PART, g->scratch + SCR_ENERGY, s->stream);
       cudaMemcpyAsync(f.energy, g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost,
                       s->stream);
       s->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;

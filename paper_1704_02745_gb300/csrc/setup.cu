@@ -12,6 +12,12 @@
 namespace pb {
 
 // ---------------------------------------------------------------------------
+// Index i modulo n in [0, n).
+__device__ __forceinline__ long wrap_index(long i, long n) {
+  const long r = i % n;
+  return r < 0 ? r + n : r;
+}
+
 // Packed codes start at 0: every edge outside (eps_out), every node outside.
 __global__ void k_init_code(uint8_t *code, size_t n_pad) {
   size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -41,6 +47,11 @@ __device__ __forceinline__ double mid_coord(double o, long i, double h) {
 // so the two copies of its bit agree.  The test runs in FP32 with a wide
 // margin; points within the margin of the sphere surface are decided by the
 // exact FP64 test, so the map is the one the FP64 definition gives.
+//
+// Periodic grids: the box is not clipped; a node visited at unwrapped index i
+// tests its points at their unwrapped coordinates o + i*h and ORs into the
+// node at i modulo n, so each edge or node is inside when some periodic image
+// of it is (its two end nodes test the same unwrapped midpoints).
 constexpr float INSIDE_MARGIN = 1e-3f;  // relative to r^2 + 1; the FP32 error of d^2 is < 1e-5 A^2
 __global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *code32,
                               int kappa_mask) {
@@ -49,12 +60,17 @@ __global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *
   const dbl4 A = atoms[a];  // x, y, z, radius
   const double r2 = __dmul_rn(A.w, A.w);
   const float r2f = (float)r2, margin = INSIDE_MARGIN * (r2f + 1.0f);
-  const long i0 = max((long)floor(__ddiv_rn(A.x - A.w - g.ox, g.h)) - 1, 0L);
-  const long i1 = min((long)ceil(__ddiv_rn(A.x + A.w - g.ox, g.h)) + 1, (long)g.nx - 1);
-  const long j0 = max((long)floor(__ddiv_rn(A.y - A.w - g.oy, g.h)) - 1, 0L);
-  const long j1 = min((long)ceil(__ddiv_rn(A.y + A.w - g.oy, g.h)) + 1, (long)g.ny - 1);
-  const long k0 = max((long)floor(__ddiv_rn(A.z - A.w - g.oz, g.h)) - 1, 0L);
-  const long k1 = min((long)ceil(__ddiv_rn(A.z + A.w - g.oz, g.h)) + 1, (long)g.nz - 1);
+  long i0 = (long)floor(__ddiv_rn(A.x - A.w - g.ox, g.h)) - 1;
+  long i1 = (long)ceil(__ddiv_rn(A.x + A.w - g.ox, g.h)) + 1;
+  long j0 = (long)floor(__ddiv_rn(A.y - A.w - g.oy, g.h)) - 1;
+  long j1 = (long)ceil(__ddiv_rn(A.y + A.w - g.oy, g.h)) + 1;
+  long k0 = (long)floor(__ddiv_rn(A.z - A.w - g.oz, g.h)) - 1;
+  long k1 = (long)ceil(__ddiv_rn(A.z + A.w - g.oz, g.h)) + 1;
+  if (!g.periodic) {
+    i0 = max(i0, 0L); i1 = min(i1, (long)g.nx - 1);
+    j0 = max(j0, 0L); j1 = min(j1, (long)g.ny - 1);
+    k0 = max(k0, 0L); k1 = min(k1, (long)g.nz - 1);
+  }
   if (i0 > i1 || j0 > j1 || k0 > k1) return;
   // box extents are a few dozen nodes: 32-bit index arithmetic
   const int ni = (int)(i1 - i0 + 1), nj = (int)(j1 - j0 + 1), cnt = ni * nj * (int)(k1 - k0 + 1);
@@ -97,7 +113,9 @@ __global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *
       if (in) bits |= p == 0 ? (kappa_mask ? 64u : 0u) : (1u << (p - 1));
     }
     if (bits) {
-      const size_t e = k * plane + j * rowp + i;
+      const long iw = g.periodic ? wrap_index(i, g.nx) : i, jw = g.periodic ? wrap_index(j, g.ny) : j;
+      const long kw = g.periodic ? wrap_index(k, g.nz) : k;
+      const size_t e = kw * plane + jw * rowp + iw;
       atomicOr(code32 + (e >> 2), bits << ((e & 3) * 8));
     }
   }
@@ -108,7 +126,8 @@ __global__ void k_eps_scatter(const dbl4 *atoms, int n_atoms, Geom g, uint32_t *
 // Contributions are accumulated as 64-bit fixed point (rounded to a multiple
 // of 1/scale, scale a power of two with sum|q| * scale <= 2^62): integer
 // addition is associative, so the grid charges do not depend on the order in
-// which the atomics land.  An atom whose cell leaves the grid sets *err.
+// which the atomics land.  An atom whose cell leaves the grid sets *err; on a
+// periodic grid the corners wrap modulo n instead.
 __global__ void k_spread(const dbl4 *xyzq, int n_atoms, Geom g, double scale,
                          unsigned long long *qn, int *err) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,7 +140,7 @@ __global__ void k_spread(const dbl4 *xyzq, int n_atoms, Geom g, double scale,
   long c0[3];
   for (int d = 0; d < 3; d++) {
     double fl = floor(f[d]);
-    if (!(fl >= 0.0 && fl + 1.0 <= (double)(n[d] - 1))) {
+    if (g.periodic ? !isfinite(fl) : !(fl >= 0.0 && fl + 1.0 <= (double)(n[d] - 1))) {
       atomicOr(err, 1);
       return;
     }
@@ -133,7 +152,13 @@ __global__ void k_spread(const dbl4 *xyzq, int n_atoms, Geom g, double scale,
     for (int dj = 0; dj < 2; dj++)
       for (int di = 0; di < 2; di++) {
         double c = __dmul_rn(__dmul_rn(__dmul_rn(A.w, w[0][di]), w[1][dj]), w[2][dk]);
-        size_t e = ((size_t)(c0[2] + dk) * g.ny + (c0[1] + dj)) * g.px + (c0[0] + di);
+        long ci = c0[0] + di, cj = c0[1] + dj, ck = c0[2] + dk;
+        if (g.periodic) {
+          ci = wrap_index(ci, g.nx);
+          cj = wrap_index(cj, g.ny);
+          ck = wrap_index(ck, g.nz);
+        }
+        size_t e = ((size_t)ck * g.ny + cj) * g.px + ci;
         atomicAdd(qn + e, (unsigned long long)__double2ll_rn(__dmul_rn(c, scale)));
       }
 }
@@ -384,7 +409,7 @@ cudaError_t launch_setup(const SetupArgs &a, cudaStream_t st) {
                                                       (unsigned long long *)a.b, a.err);
   }
   const long n_ghost = 2L * ((long)g.ny * g.nz + (long)g.nx * g.nz + (long)g.nx * g.ny);
-  if (a.n_atoms > 0) {
+  if (a.n_atoms > 0 && !g.periodic) {  // a periodic grid has no boundary
     const int blocks = (int)((n_ghost + DH_NT - 1) / DH_NT);
     if (a.dh_f32)
       k_dh_f32<<<blocks, DH_NT, 0, st>>>(a.atoms_xyzq, a.n_atoms, g, a.kappa, a.eout, a.ghost,

@@ -7,6 +7,7 @@ namespace pb {
 struct Geom {  // grid geometry as the setup kernels see it
   int nx, ny, nz, px;
   double h, ox, oy, oz;
+  int periodic;  // every axis periodic with period n*h
 };
 
 struct SetupArgs {

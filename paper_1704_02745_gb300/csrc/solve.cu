@@ -200,6 +200,11 @@ struct StageRing {
 // The update pass stores z = M^-1 r, so the new direction p = z + beta p_old
 // is one fused multiply-add per node, halo included.  dtab: the diagonal of
 // the FP32/FP64 operator for every code byte, in shared memory per item.
+//
+// Periodic grids: the z planes before and after the grid are the last and
+// the first (the TMA loads wrap the plane index), and every ring cell that
+// lies outside the grid in x or y -- halo cells and the overhanging lanes and
+// rows of the last tiles -- takes the wrapped node's value from global memory.
 template <typename T, int CM, int NS>
 __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int tile,
                                           uint8_t *stages, T *ring, const T *dtab,
@@ -226,11 +231,21 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
   T *pnew = (T *)(S.pbuf ? I.p0 : I.p1) + (size_t)G.z0 * plane + ec0;
   T *ap = (T *)I.ap + (size_t)G.z0 * plane + ec0;
   T *x = (SEP ? (T *)I.d : (T *)(S.xbuf ? I.x64b : I.x64)) + (size_t)G.z0 * plane + ec0;
+  const bool per = I.periodic != 0;
+  const int nzg = I.nz;
+  auto zwrap = [&](int z) { return !per ? z : z < 0 ? z + nzg : z >= nzg ? z - nzg : z; };
+  // new direction at a node outside the grid (periodic): that of its image
+  auto wrapped_p = [&](int gx, int gy, int zt) -> T {
+    const int xw = gx % I.nx, yw = gy < 0 ? gy + I.ny : gy % I.ny;
+    const size_t e = (size_t)zt * plane + (size_t)yw * I.px + xw;
+    const T zv = ((const T *)I.z)[e];
+    return first ? zv : zv + beta * ((const T *)(S.pbuf ? I.p1 : I.p0))[e];
+  };
 
   // thread 0 issues plane z0-1+q into stage st
   auto issue = [&](int q, uint32_t st) {
     uint8_t *sb = stages + st * stage_bytes;
-    const int z = G.z0 - 1 + q;
+    const int z = zwrap(G.z0 - 1 + q);
     mbar_expect_tx(&full[st], tma_bytes);
     tma_load_3d(sb, &I.tm_z, &full[st], G.x0 - NV, G.y0 - 1, z);
     tma_load_3d(sb + off_p, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
@@ -286,6 +301,12 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
 #pragma unroll
         for (int u = 0; u < NV; u++) pn.v[u] += beta * po.v[u];
       }
+      if (per && (G.x0 + G.tx + NV > I.nx || G.y0 + G.ty >= I.ny)) {
+#pragma unroll
+        for (int u = 0; u < NV; u++)
+          if (G.x0 + G.tx + u >= I.nx || G.y0 + G.ty >= I.ny)
+            pn.v[u] = wrapped_p(G.x0 + G.tx + u, G.y0 + G.ty, zwrap(z));
+      }
       stv(rg + cg, pn);
       // deferred update of the previous iteration: x += alpha p_old (the
       // first inner iteration starts the FP32 increment d from zero)
@@ -300,7 +321,13 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
       }
     }
     if (q >= 1 && q < Q - 1) x += plane;
-    if (ok && Hh.role) rg[hg] = first ? sz[hr] : sz[hr] + beta * sp[hr];
+    if (ok && Hh.role) {
+      const int gx = G.x0 + Hh.hx, gy = G.y0 + Hh.hy;
+      if (per && (gx < 0 || gx >= I.nx || gy < 0 || gy >= I.ny))
+        rg[hg] = wrapped_p(gx < 0 ? gx + I.nx : gx, gy, zwrap(z));
+      else
+        rg[hg] = first ? sz[hr] : sz[hr] + beta * sp[hr];
+    }
     if (__syncthreads_or(!ok)) {
       // A wait gave up: let the copies already issued land, each for a
       // bounded time, before the CTA leaves.
@@ -369,7 +396,15 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
           a.v[u] = av;
           acc += pc.v[u] * av;
         }
-        stv(pnew, pc);
+        if (per) {  // pad lanes of the ring hold wrapped values; p keeps zero pads
+          Vec<T> pst = pc;
+#pragma unroll
+          for (int u = 0; u < NV; u++)
+            if (!((G.vmask >> u) & 1u)) pst.v[u] = 0;
+          stv(pnew, pst);
+        } else {
+          stv(pnew, pc);
+        }
         stv(ap, a);
       }
       pnew += plane; ap += plane;
@@ -393,7 +428,12 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
   const TileG G = tile_g(I, tile, I.rtz);
   const HaloG Hh = halo_g(I);
   const int RGW = I.W + 2 * NV, H = I.H;
-  const int hi = G.x0 + Hh.hx, hj = G.y0 + Hh.hy;
+  const bool per = I.periodic != 0;
+  // periodic: positions outside the grid read their images
+  auto wx = [&](int i) { return !per ? i : i < 0 ? i + I.nx : i % I.nx; };
+  auto wy = [&](int j) { return !per ? j : j < 0 ? j + I.ny : j % I.ny; };
+  auto wz = [&](int k) { return !per ? k : k < 0 ? k + I.nz : k % I.nz; };
+  const int hi = wx(G.x0 + Hh.hx), hj = wy(G.y0 + Hh.hy);
   const bool hvalid = Hh.role && hi >= 0 && hi < I.nx && hj >= 0 && hj < I.ny;
   const size_t px = I.px, plane = (size_t)I.px * I.ny;
   const size_t ec0 = (size_t)(G.y0 + G.ty) * px + (G.x0 + G.tx);
@@ -415,6 +455,13 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
     return v + alpha * (double)p[e];
   };
   auto group = [&](int k, double *out) {  // x_new of this thread's nodes in plane k
+    if (per) {  // lanes and rows past the grid hold their images
+      const int kw = wz(k), jw = wy(G.y0 + G.ty);
+#pragma unroll
+      for (int u = 0; u < NV; u++)
+        out[u] = G.in_tile ? xn((size_t)kw * plane + (size_t)jw * px + wx(G.x0 + G.tx + u)) : 0.0;
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < NV; u++)
       out[u] = ((G.vmask >> u) & 1u) && k >= 0 && k < I.nz ? xn((size_t)k * plane + ec0 + u) : 0.0;
@@ -425,7 +472,7 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
   const int rsz = RGW * (H + 2);
   if (G.in_tile)
     for (int u = 0; u < NV; u++) ring[cg + u] = xc[u];
-  if (Hh.role) ring[hg] = hvalid ? xn((size_t)G.z0 * plane + eh0) : 0.0;
+  if (Hh.role) ring[hg] = hvalid ? xn((size_t)wz(G.z0) * plane + eh0) : 0.0;
   int cur = 0;
   T rr_t = 0, rz_t = 0;
   for (int k = G.z0; k < G.z1; ++k) {
@@ -434,7 +481,7 @@ __device__ __forceinline__ void resid_tile(const Inst &I, const TileScal &S, int
     group(k + 1, xnx);
     if (G.in_tile)
       for (int u = 0; u < NV; u++) rn[cg + u] = xnx[u];
-    if (Hh.role) rn[hg] = hvalid && k + 1 < I.nz ? xn((size_t)(k + 1) * plane + eh0) : 0.0;
+    if (Hh.role) rn[hg] = hvalid && (per || k + 1 < I.nz) ? xn((size_t)wz(k + 1) * plane + eh0) : 0.0;
     __syncthreads();
     const double *rc = ring + (size_t)cur * rsz;
 #pragma unroll

@@ -73,9 +73,9 @@ cudaError_t launch_unpack(const double *padded, double *dense, int nx, int ny, i
 cudaError_t launch_apply(const Inst &I, const Inst *dI, const void *u, void *au, int dtype,
                          cudaStream_t st);
 // phi: nz x ny rows of px elements (px = nx: dense).  An atom whose
-// trilinear cell leaves the grid makes the energy NaN.
-cudaError_t launch_energy(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, int px, double h,
-                          double ox, double oy, double oz, const double *phi, double *scratch,
-                          double *out, cudaStream_t st);
+// trilinear cell leaves the grid makes the energy NaN (periodic: corners wrap).
+cudaError_t launch_energy(const dbl4 *xyzq, int n_atoms, int nx, int ny, int nz, int px,
+                          int periodic, double h, double ox, double oy, double oz,
+                          const double *phi, double *scratch, double *out, cudaStream_t st);
 
 }  // namespace pb

@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 5: "ERR_NOT_
 #: Every symbol include/pb.h declares (checked by the CPU tests).
 EXPORTED = ["pb_last_error", "pb_create", "pb_destroy", "pb_ctx_stats", "pb_setup_grid", "pb_free_grid",
             "pb_grid_update_atoms", "pb_apply_operator", "pb_pcg_solve", "pb_energy",
-            "pb_grid_export", "pb_grid_bytes"]
+            "pb_grid_export", "pb_grid_bytes", "pb_solvation_energy"]
 
 
 class PbError(RuntimeError):
@@ -48,7 +48,7 @@ class GridDesc(ctypes.Structure):
                 ("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double),
                 ("ionic_strength", ctypes.c_double), ("temperature", ctypes.c_double),
                 ("kappa_mask", ctypes.c_int), ("coef", ctypes.c_int),
-                ("dh_precision", ctypes.c_int)]
+                ("dh_precision", ctypes.c_int), ("periodic", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -68,6 +68,11 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Solvation(ctypes.Structure):
+    _fields_ = [("dG", ctypes.c_double), ("e_solv", ctypes.c_double), ("e_ref", ctypes.c_double),
+                ("solv", SolveInfo), ("ref", SolveInfo)]
 
 
 class Request(ctypes.Structure):
@@ -123,6 +128,8 @@ def load(path: str = LIB_PATH):
     lib.pb_apply_operator.argtypes = [_P, _P, _P, ctypes.c_int]
     lib.pb_pcg_solve.argtypes = [_P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]
     lib.pb_energy.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_double)]
+    lib.pb_solvation_energy.argtypes = [_P, ctypes.POINTER(GridDesc), ctypes.c_int, _P, _P, _P,
+                                        ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(Solvation)]
     lib.pb_grid_export.argtypes = [_P, ctypes.c_int, _P, ctypes.c_size_t]
     lib.pb_grid_bytes.restype = ctypes.c_size_t
     lib.pb_grid_bytes.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int]
@@ -171,6 +178,7 @@ def grid_desc(g) -> GridDesc:
     d.kappa_mask = 1 if g.kappa_mask else 0
     d.coef = COEF[g.coef]
     d.dh_precision = PB_F32 if g.dh == "f32" else PB_F64
+    d.periodic = 1 if getattr(g, "periodic", False) else 0
     return d
 
 
@@ -249,6 +257,23 @@ def pb_energy(grid: int, phi) -> float:
     return e.value
 
 
+def pb_solvation_energy(ctx: int, spec, atoms, phi, check: bool = True, **opts) -> Solvation:
+    """dG = E(solvated) - E(reference: eps_in everywhere, no salt); phi is the
+    device array of the solvated potential (phi0 if warm_start)."""
+    d = grid_desc(spec)
+    o = solve_opts(**opts)
+    xyz = np.ascontiguousarray(atoms.xyz, dtype=np.float64)
+    q = np.ascontiguousarray(atoms.q, dtype=np.float64)
+    r = np.ascontiguousarray(atoms.r, dtype=np.float64)
+    out = Solvation()
+    st = load().pb_solvation_energy(_P(ctx), ctypes.byref(d), int(q.shape[0]), xyz.ctypes.data_as(_P),
+                                    q.ctypes.data_as(_P), r.ctypes.data_as(_P), ctypes.byref(o),
+                                    _P(_dptr(phi)), ctypes.byref(out))
+    if check:
+        _check(st)
+    return out
+
+
 def pb_energy_noalloc(xyzq, spec, phi, energy, stream=None):
     """Energy without device allocation: xyzq (n x 4 doubles), phi and the
     one-double `energy` output are device arrays; queued on `stream`."""
@@ -276,6 +301,9 @@ class Context:
 
     def stats(self):
         return pb_ctx_stats(self.handle)
+
+    def solvation(self, spec, atoms, phi, check: bool = True, **opts) -> Solvation:
+        return pb_solvation_energy(self.handle, spec, atoms, phi, check=check, **opts)
 
     def close(self):
         if self.handle:
