@@ -14,6 +14,8 @@ Functions and the passage each follows:
 * ``pcg``            -- O3/O4: CG and Jacobi-preconditioned CG (Sec. 2.2, 2.4)
 * ``energy``         -- O5: 1/2 * 332.0637 * sum q phi (the energies compared in Sec. 3.1)
 * ``dense_matrix`` / ``cholesky_solve`` -- O6: explicit A and a dense solve, small grids
+* ``dielectric``     -- also the weighted harmonic-average boundary dielectric of Sec. 2.7
+  (``eps_model="harmonic"``: each edge from the fraction of it inside the atoms)
 * ``solvation_energy`` -- the electrostatic solvation energy of Sec. 3.1 (Figs. 1-2):
   energy of the solvated system minus that of the reference system
 
@@ -70,6 +72,7 @@ def _load():
         G = ctypes.POINTER(_Grid)
         lib.or_dielectric.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
         lib.or_dielectric_periodic.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+        lib.or_dielectric_harmonic.argtypes = [G, ctypes.c_int, _P, _P, _P, _P, _P, _P]
         lib.or_spread_charge.restype = ctypes.c_int
         lib.or_spread_charge.argtypes = [G, ctypes.c_int, _P, _P, _P]
         lib.or_dh_ghost.argtypes = [G, ctypes.c_int, _P, _P, _P]
@@ -138,7 +141,11 @@ def dielectric(grid, atoms):
     lam = np.empty((nz, ny, nx), dtype=np.uint8)
     xyz = np.ascontiguousarray(atoms.xyz, dtype=np.float64)
     r = np.ascontiguousarray(atoms.r, dtype=np.float64)
-    fn = lib.or_dielectric_periodic if g.periodic else lib.or_dielectric
+    harmonic = getattr(grid, "eps_model", "midpoint") == "harmonic"
+    if harmonic and g.periodic:
+        raise OracleArgError("the harmonic-average dielectric is defined for the free-space boundary")
+    fn = (lib.or_dielectric_harmonic if harmonic else
+          lib.or_dielectric_periodic if g.periodic else lib.or_dielectric)
     fn(ctypes.byref(g), atoms.n, _ptr(xyz), _ptr(r), _ptr(ex), _ptr(ey), _ptr(ez), _ptr(lam))
     return ex, ey, ez, lam
 

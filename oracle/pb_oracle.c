@@ -202,6 +202,77 @@ void or_dielectric_periodic(const or_grid *g, int n_atoms, const double *xyz, co
         for (long i = 0; i < nx; i++) ez[ezid(g, i, j, -1)] = ez[ezid(g, i, j, nz - 1)];
 }
 
+/* Weighted harmonic average boundary dielectric (Sec. 2.7): each edge takes
+ * 1 / (w/eps_in + (1-w)/eps_out), w the fraction of the edge (the segment
+ * between its two nodes) strictly inside the union of the atom spheres;
+ * w = 0 gives eps_out and w = 1 gives eps_in exactly.  Per edge, every atom
+ * contributes the open interval of the segment parameter t in [0, 1] where
+ * the segment is inside its sphere; the intervals are sorted by start (then
+ * end) and merged, touching ones joined, and their lengths summed in order.
+ * lambda as in or_dielectric.  Free-space boundary only. */
+typedef struct { double lo, hi; } or_iv;
+static int iv_cmp(const void *a, const void *b) {
+    const or_iv *x = a, *y = b;
+    if (x->lo != y->lo) return x->lo < y->lo ? -1 : 1;
+    if (x->hi != y->hi) return x->hi < y->hi ? -1 : 1;
+    return 0;
+}
+/* Fraction inside of the segment from (px, py, pz) along axis `ax` (0, 1, 2)
+ * over one spacing h. */
+static double edge_fraction(const or_grid *g, int n_atoms, const double *xyz, const double *rad,
+                            double px, double py, double pz, int ax, or_iv *buf) {
+    const double p[3] = {px, py, pz};
+    int n = 0;
+    for (int a = 0; a < n_atoms; a++) {
+        const double *c = xyz + 3 * a;
+        const int u = (ax + 1) % 3, v = (ax + 2) % 3;  /* the two other axes */
+        double du = p[u] - c[u], dv = p[v] - c[v];
+        double d2 = du * du + dv * dv;
+        double s = rad[a] * rad[a] - d2;
+        if (!(s > 0.0)) continue;
+        double q = sqrt(s);
+        double t0 = ((c[ax] - q) - p[ax]) / g->h, t1 = ((c[ax] + q) - p[ax]) / g->h;
+        double lo = t0 > 0.0 ? t0 : 0.0, hi = t1 < 1.0 ? t1 : 1.0;
+        if (lo < hi) { buf[n].lo = lo; buf[n].hi = hi; n++; }
+    }
+    if (n == 0) return 0.0;
+    qsort(buf, (size_t)n, sizeof(or_iv), iv_cmp);
+    double w = 0.0, lo = buf[0].lo, hi = buf[0].hi;
+    for (int t = 1; t < n; t++) {
+        if (buf[t].lo <= hi) { if (buf[t].hi > hi) hi = buf[t].hi; }
+        else { w = w + (hi - lo); lo = buf[t].lo; hi = buf[t].hi; }
+    }
+    return w + (hi - lo);
+}
+static double harmonic_eps(const or_grid *g, double w) {
+    if (w == 0.0) return g->eps_out;
+    if (w == 1.0) return g->eps_in;
+    return 1.0 / (w / g->eps_in + (1.0 - w) / g->eps_out);
+}
+void or_dielectric_harmonic(const or_grid *g, int n_atoms, const double *xyz, const double *rad,
+                            double *ex, double *ey, double *ez, uint8_t *lam) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const double h = g->h;
+    or_dielectric(g, n_atoms, xyz, rad, ex, ey, ez, lam); /* lambda (and a binary map, replaced) */
+    or_iv *buf = malloc(sizeof(or_iv) * (size_t)(n_atoms > 0 ? n_atoms : 1));
+    for (long k = 0; k < nz; k++)
+        for (long j = 0; j < ny; j++)
+            for (long i = -1; i < nx; i++)
+                ex[exid(g, i, j, k)] = harmonic_eps(g, edge_fraction(g, n_atoms, xyz, rad,
+                    g->ox + (double)i * h, g->oy + (double)j * h, g->oz + (double)k * h, 0, buf));
+    for (long k = 0; k < nz; k++)
+        for (long j = -1; j < ny; j++)
+            for (long i = 0; i < nx; i++)
+                ey[eyid(g, i, j, k)] = harmonic_eps(g, edge_fraction(g, n_atoms, xyz, rad,
+                    g->ox + (double)i * h, g->oy + (double)j * h, g->oz + (double)k * h, 1, buf));
+    for (long k = -1; k < nz; k++)
+        for (long j = 0; j < ny; j++)
+            for (long i = 0; i < nx; i++)
+                ez[ezid(g, i, j, k)] = harmonic_eps(g, edge_fraction(g, n_atoms, xyz, rad,
+                    g->ox + (double)i * h, g->oy + (double)j * h, g->oz + (double)k * h, 2, buf));
+    free(buf);
+}
+
 /* Grid charges q(i,j,k) (Eq. 3: the charge within the cube centred on the
  * node) by trilinear spreading of each atom onto the 8 nodes of its cell:
  * f = (x - o)/h, i0 = floor(f), w = f - i0; corner weights w or 1 - w per axis,

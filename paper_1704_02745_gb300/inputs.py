@@ -45,6 +45,9 @@ class GridSpec:
     dielectric coefficients ("packed", "f32", "bf16", "f64"); ``dh`` chooses the
     precision of the Debye-Hueckel boundary sum ("f64" or "f32").  ``periodic``
     makes every axis periodic with period n*h (no ghost layer, no boundary sum).
+    ``eps_model`` chooses the boundary dielectric: "midpoint" (eps_in when the
+    edge midpoint is inside an atom) or "harmonic" (the weighted harmonic
+    average over the fraction of the edge inside the atoms).
     """
 
     nx: int
@@ -60,6 +63,7 @@ class GridSpec:
     coef: str = "packed"
     dh: str = "f64"
     periodic: bool = False
+    eps_model: str = "midpoint"
 
     @property
     def n(self) -> int:
