@@ -90,7 +90,17 @@ typedef struct {
                                  spread modulo n, no boundary sum.  Needs n >= 3 per axis and
                                  ionic_strength > 0 (without salt, or with every node inside
                                  an atom under kappa_mask, A is singular) */
+    int eps_model;            /* PB_EPS_*: the boundary dielectric (Sec. 2.7) */
 } pb_grid_desc;
+
+/* Boundary dielectric.  MIDPOINT: an edge takes eps_in when its midpoint is
+ * strictly inside an atom sphere, else eps_out (the packed one-byte map).
+ * HARMONIC: the weighted harmonic average Sec. 2.7 uses, 1 / (w/eps_in +
+ * (1-w)/eps_out) with w the fraction of the edge strictly inside the union of
+ * the spheres; needs explicit coefficients (coef F32, BF16 or F64: the FP32
+ * inner solve keeps FP32 or BF16 copies, the FP64 residual and FP64 solves
+ * the FP64 edges) and the free-space boundary; not served by pb_server. */
+enum { PB_EPS_MIDPOINT = 0, PB_EPS_HARMONIC = 1 };
 
 typedef struct {
     int precond;      /* PB_PRECOND_* (Sec. 2.4: Jacobi, M = diag A) */

@@ -140,6 +140,12 @@ pb_status pb_check_desc(const pb_grid_desc *d) {
     return pb_fail(PB_ERR_ARG, "a periodic grid needs at least 3 nodes per axis");
   if (d->periodic && !(d->ionic_strength > 0))
     return pb_fail(PB_ERR_ARG, "a periodic grid needs salt (ionic_strength > 0): without it A is singular");
+  if (d->eps_model != PB_EPS_MIDPOINT && d->eps_model != PB_EPS_HARMONIC)
+    return pb_fail(PB_ERR_ARG, "bad eps_model");
+  if (d->eps_model == PB_EPS_HARMONIC && d->coef == PB_COEF_PACKED)
+    return pb_fail(PB_ERR_ARG, "the harmonic-average dielectric needs explicit coefficients (coef f32, bf16 or f64)");
+  if (d->eps_model == PB_EPS_HARMONIC && d->periodic)
+    return pb_fail(PB_ERR_ARG, "the harmonic-average dielectric is for the free-space boundary");
   return PB_OK;
 }
 
@@ -155,6 +161,7 @@ void pb_grid_release(pb_grid *g) {
                   g->own_scal ? (void *)g->scal : nullptr, g->dinst, g->st_items, g->ch_items, g->st_part,
                   g->ch_part, g->rs_part};
   for (void *p : ptrs) dfree(p);
+  dfree(g->cell_buf);
   if (g->h_atoms) cudaFreeHost(g->h_atoms);
   delete g;
 }
@@ -168,10 +175,15 @@ extern "C" pb_status pb_free_grid(pb_grid *g) {
 }
 
 // Stencil tiles: the fewest x tiles of width <= WMAX, then the tallest H with
-// W*H <= NV*NT, then z chunks so that all tiles fit in one wave of resident CTAs.
+// W*H <= NV*NT, then z chunks so that a single grid's tiles fill
+// PB_PLAN_PER_SM CTAs per SM in one wave (a tile per CTA; fewer, longer
+// tiles than the resident limit allows balance better across the SMs).
 // batch = true (grids of a server): z chunks of at least 32 planes and update
 // chunks of at least 16*CH elements, since many grids share each launch and
 // each chunk ends with a CTA-wide reduction.
+#ifndef PB_PLAN_PER_SM
+#define PB_PLAN_PER_SM 2
+#endif
 void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
   g->tiles_x = (nx + WMAX - 1) / WMAX;
@@ -180,7 +192,8 @@ void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   g->tiles_y = (ny + hmax - 1) / hmax;
   g->H = (ny + g->tiles_y - 1) / g->tiles_y;
   const int cols = g->tiles_x * g->tiles_y;
-  const int resident = std::max(kg.stencil_blocks, 2 * g->ctx->num_sms);
+  const int resident = batch ? std::max(kg.stencil_blocks, 2 * g->ctx->num_sms)
+                             : std::min(kg.stencil_blocks, PB_PLAN_PER_SM * g->ctx->num_sms);
   int zc = std::max(1, resident / cols);
   zc = std::min(zc, std::max(1, nz / (batch ? 32 : 4)));
   g->tz = (nz + zc - 1) / zc;
@@ -262,14 +275,37 @@ pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double 
   }
   a.kappa_mask = desc->kappa_mask ? 1 : 0;
   a.dh_f32 = desc->dh_precision == PB_F32;
+  const bool harmonic = desc->eps_model == PB_EPS_HARMONIC;
+  if (harmonic) {  // edge fractions from a cell list of the atoms
+    double r_max = 0;
+    for (int t = 0; t < n_atoms; t++) r_max = std::max(r_max, radius[t]);
+    const size_t bytes = cell_buffer_bytes(cell_plan(g->g, r_max), n_atoms);
+    if (bytes > g->cell_cap) {
+      dfree(g->cell_buf);
+      g->cell_buf = nullptr;
+      g->cell_cap = 0;
+      pb_status st;
+      if ((st = pb_dalloc(&g->cell_buf, bytes))) return st;
+      g->cell_cap = bytes;
+    }
+    a.ex64 = (double *)g->ex64; a.ey64 = (double *)g->ey64; a.ez64 = (double *)g->ez64;
+    a.cell_buf = g->cell_buf;
+    a.r_max = r_max;
+  }
   CK(launch_setup(a, s));
-  if (desc->coef == PB_COEF_F64)
+  if (harmonic)
+    CK(launch_harmonic_finish(g->code, g->g, g->kbh2, (const double *)g->ex64, (const double *)g->ey64,
+                              (const double *)g->ez64, (double *)g->diag64,
+                              desc->coef == PB_COEF_BF16 ? COEF_BF16 : COEF_F32, g->ex, g->ey,
+                              g->ez, g->diag, s));
+  else if (desc->coef == PB_COEF_F64)
     CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, COEF_F64, g->ex64,
                      g->ey64, g->ez64, g->diag64, s));
   else if (desc->coef != PB_COEF_PACKED)
     CK(launch_expand(g->code, g->g, desc->eps_in, desc->eps_out, g->kbh2, desc->coef, g->ex, g->ey,
                      g->ez, g->diag, s));
-  g->ctx->stats->launches += 3 + (n_atoms > 0 ? 3 : 0) + (desc->coef != PB_COEF_PACKED ? 1 : 0);
+  g->ctx->stats->launches += 3 + (n_atoms > 0 ? 3 : 0) +
+                             (harmonic ? 5 + (n_atoms > 0 ? 3 : 0) : desc->coef != PB_COEF_PACKED ? 1 : 0);
   g->ctx->stats->h2d += 2 * (unsigned long long)n_atoms * sizeof(dbl4);
   if (!sync) return PB_OK;  // the error word and ||b||^2 stay on the device
   int *hbuf = (int *)g->ctx->host_scal;  // pinned staging: error word, then ||b||^2
@@ -333,10 +369,12 @@ pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_g
   }
   if (desc->coef != PB_COEF_PACKED) {
     const size_t nc = (size_t)px * (desc->ny + 1) * (desc->nz + 1);
-    if (desc->coef == PB_COEF_F64) {
+    const bool harmonic = desc->eps_model == PB_EPS_HARMONIC;
+    if (desc->coef == PB_COEF_F64 || harmonic) {
       ALLOC(g->ex64, g->n_pad * 8); ALLOC(g->ey64, nc * 8); ALLOC(g->ez64, nc * 8);
       ALLOC(g->diag64, g->n_pad * 8);
-    } else {
+    }
+    if (desc->coef != PB_COEF_F64 || harmonic) {  // the FP32 inner solve's copies
       const size_t es = desc->coef == PB_COEF_BF16 ? 2 : 4;
       ALLOC(g->ex, g->n_pad * es); ALLOC(g->ey, nc * es); ALLOC(g->ez, nc * es);
       ALLOC(g->diag, g->n_pad * 4);
@@ -385,6 +423,8 @@ extern "C" size_t pb_grid_bytes(const pb_grid_desc *d, int precision) {
 // Instance descriptor of a grid for a solve of (mode, coef).
 
 int pb_inner_coef(const pb_grid *g, int mode) {
+  if (g->d.eps_model == PB_EPS_HARMONIC)  // FP64 edges, and FP32 / BF16 copies
+    return mode == MODE_F64 ? COEF_F64 : g->d.coef == PB_COEF_BF16 ? COEF_BF16 : COEF_F32;
   if (mode == MODE_F64) return g->d.coef == PB_COEF_F64 ? COEF_F64 : COEF_PACKED;
   if (g->d.coef == PB_COEF_F32 || g->d.coef == PB_COEF_BF16) return g->d.coef;
   return COEF_PACKED;
@@ -495,6 +535,11 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
     I.ex = g->ex64; I.ey = g->ey64; I.ez = g->ez64; I.diag = g->diag64;
   } else if (coef == COEF_F32 || coef == COEF_BF16) {
     I.ex = g->ex; I.ey = g->ey; I.ez = g->ez; I.diag = g->diag;
+  }
+  I.rx = I.ry = I.rz = I.rdiag = nullptr;
+  if (g->d.eps_model == PB_EPS_HARMONIC && coef != COEF_F64) {
+    I.rx = (const double *)g->ex64; I.ry = (const double *)g->ey64; I.rz = (const double *)g->ez64;
+    I.rdiag = (const double *)g->diag64;
   }
   I.x64 = g->x64; I.x64b = g->x64b;
   I.b = g->b;
@@ -871,6 +916,12 @@ extern "C" pb_status pb_grid_export(pb_grid *g, int what, void *dst, size_t byte
     else if (what == PB_EXPORT_EPS_Y) { width = nx; height = (ny + 1) * nz; }
     else { width = nx; height = ny * (nz + 1); }
     if (!need(width * height * 8)) return pb_fail(PB_ERR_ARG, "export: size mismatch");
+    if (g->d.eps_model == PB_EPS_HARMONIC) {  // the FP64 edge arrays themselves
+      const void *src = what == PB_EXPORT_EPS_X ? g->ex64 : what == PB_EXPORT_EPS_Y ? g->ey64 : g->ez64;
+      CK(cudaMemcpy2DAsync(dst, width * 8, src, px * 8, width * 8, height, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      return PB_OK;
+    }
     double *ex = nullptr, *ey = nullptr, *ez = nullptr;
     pb_status st;
     if ((st = pb_dalloc((void **)&ex, nc * 8))) return st;

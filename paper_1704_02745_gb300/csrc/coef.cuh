@@ -67,6 +67,15 @@ __device__ __forceinline__ T zval(const Inst &I, size_t e, T r) {
 template <int CM>
 __device__ __forceinline__ NodeCoef<double> node_coef64(const Inst &I, size_t e, int k) {
   if (CM == COEF_F64) return node_coef<double, COEF_F64>(I, e, k);
+  if (CM != COEF_PACKED && I.rx) {  // FP64 edges behind rounded inner copies
+    NodeCoef<double> c;
+    const size_t px = I.px, ey0 = e + (size_t)k * px, plane = px * I.ny;
+    c.exm = I.rx[e]; c.exp = I.rx[e + 1];
+    c.eym = I.ry[ey0]; c.eyp = I.ry[ey0 + px];
+    c.ezm = I.rz[e]; c.ezp = I.rz[e + plane];
+    c.diag = I.rdiag[e];
+    return c;
+  }
   return node_coef<double, COEF_PACKED>(I, e, k);
 }
 

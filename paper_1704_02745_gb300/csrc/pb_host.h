@@ -44,6 +44,8 @@ struct pb_grid {
   bool own_scal = true;
   int *counts = nullptr;     // device: stencil and update item counts of the single-grid batch
   bool batch = false;        // a server's grid: its work lists and scalars are the server's
+  void *cell_buf = nullptr;  // harmonic-average setup: cell list of the atoms
+  size_t cell_cap = 0;
   pb::Inst *dinst = nullptr;
   pb::Item *st_items = nullptr, *ch_items = nullptr;
   double *st_part = nullptr, *ch_part = nullptr, *rs_part = nullptr;

@@ -88,6 +88,9 @@ struct alignas(64) Inst {
   size_t n_pad;                       // nz*ny*px
   const uint8_t *code;
   const void *ex, *ey, *ez, *diag;    // explicit coefficient arrays (inner precision)
+  const double *rx, *ry, *rz, *rdiag; // FP64 arrays for the residual pass when the inner
+                                      // arrays are rounded copies (harmonic-average
+                                      // dielectric); NULL: the codes are exact
   double *x64, *x64b;                 // solution, double-buffered across RESID passes
   const double *b;
   void *d, *z, *p0, *p1, *ap;         // inner work vectors (z = M^-1 r)

@@ -909,6 +909,8 @@ extern "C" pb_status pb_batch_submit(pb_server *s, const pb_request *req, uint64
   if (!s || !req || !ticket) return pb_fail(PB_ERR_ARG, "pb_batch_submit: NULL argument");
   pb_status st = pb_check_desc(&req->desc);
   if (st) return st;
+  if (req->desc.eps_model != PB_EPS_MIDPOINT)
+    return pb_fail(PB_ERR_ARG, "pb_batch_submit: the server solves with the packed midpoint dielectric");
   if ((st = pb_check_atoms(req->n_atoms, req->xyz, req->q, req->radius))) return st;
   Request rq;
   rq.traj = req->trajectory_id < 0 ? -1 : req->trajectory_id;

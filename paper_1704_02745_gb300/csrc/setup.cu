@@ -6,6 +6,8 @@
 // o + (i + 0.5)*h, and the inside test |m - x_a|^2 < r_a^2 as
 // (dx*dx + dy*dy) + dz*dz, each operation rounded on its own (__d*_rn), so
 // the dielectric map is the same bit pattern whatever the evaluation order.
+#include <cmath>
+
 #include "pb_internal.cuh"
 #include "setup.cuh"
 
@@ -268,11 +270,14 @@ __global__ void __launch_bounds__(DH_NT) k_dh_f32(const dbl4 *xyzq, int n_atoms,
 // point) and b may alias: each element is read before it is written.
 // scale = 4 pi / h / (fixed-point scale): the latter is a power of two, so
 // qn * scale rounds as (qn / fixed-point scale) * (4 pi / h) does.
+// ex64/ey64/ez64 (harmonic-average grids, else NULL): the ghost edges' eps;
+// otherwise eps_in or eps_out from the code bits.
 constexpr int FOLD_CTAS = 256, FOLD_NT = 256;
 __global__ void __launch_bounds__(FOLD_NT) k_fold_rhs(const long long *qn, const uint8_t *code,
                                                       const double *ghost, Geom g, double scale,
-                                                      double ein, double eout, double *b,
-                                                      double *part) {
+                                                      double ein, double eout, const double *ex64,
+                                                      const double *ey64, const double *ez64,
+                                                      double *b, double *part) {
   __shared__ double red[FOLD_NT];
   const int rows = g.ny * g.nz, per = (rows + FOLD_CTAS - 1) / FOLD_CTAS;
   const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
@@ -290,15 +295,26 @@ __global__ void __launch_bounds__(FOLD_NT) k_fold_rhs(const long long *qn, const
       }
       double v = __dmul_rn((double)qn[e], scale);
       const uint32_t c = code[e];
-      if (i == 0) v = __dadd_rn(v, __dmul_rn((c & 1u) ? ein : eout, ghost[(long)k * g.ny + j]));
-      if (i == g.nx - 1) v = __dadd_rn(v, __dmul_rn((c & 2u) ? ein : eout, ghost[fx + (long)k * g.ny + j]));
-      if (j == 0) v = __dadd_rn(v, __dmul_rn((c & 4u) ? ein : eout, ghost[2 * fx + (long)k * g.nx + i]));
+      // eps of the six ghost edges (read only on boundary nodes)
+      auto eps = [&](int bit, size_t idx, const double *arr) {
+        return arr ? arr[idx] : ((c & bit) ? ein : eout);
+      };
+      const size_t pxs = g.px, nys = g.ny;
+      if (i == 0)
+        v = __dadd_rn(v, __dmul_rn(eps(1, e, ex64), ghost[(long)k * g.ny + j]));
+      if (i == g.nx - 1)
+        v = __dadd_rn(v, __dmul_rn(eps(2, e + 1, ex64), ghost[fx + (long)k * g.ny + j]));
+      if (j == 0)
+        v = __dadd_rn(v, __dmul_rn(eps(4, ((size_t)k * (nys + 1)) * pxs + i, ey64),
+                                   ghost[2 * fx + (long)k * g.nx + i]));
       if (j == g.ny - 1)
-        v = __dadd_rn(v, __dmul_rn((c & 8u) ? ein : eout, ghost[2 * fx + fy + (long)k * g.nx + i]));
+        v = __dadd_rn(v, __dmul_rn(eps(8, ((size_t)k * (nys + 1) + nys) * pxs + i, ey64),
+                                   ghost[2 * fx + fy + (long)k * g.nx + i]));
       if (k == 0)
-        v = __dadd_rn(v, __dmul_rn((c & 16u) ? ein : eout, ghost[2 * fx + 2 * fy + (long)j * g.nx + i]));
+        v = __dadd_rn(v, __dmul_rn(eps(16, (size_t)j * pxs + i, ez64),
+                                   ghost[2 * fx + 2 * fy + (long)j * g.nx + i]));
       if (k == g.nz - 1)
-        v = __dadd_rn(v, __dmul_rn((c & 32u) ? ein : eout,
+        v = __dadd_rn(v, __dmul_rn(eps(32, ((size_t)g.nz * nys + j) * pxs + i, ez64),
                                    ghost[2 * fx + 2 * fy + fz + (long)j * g.nx + i]));
       b[e] = v;
       s = fma(v, v, s);
@@ -391,11 +407,236 @@ __global__ void k_sum_final(const double *part, int n, double *out) {
 }
 
 // ---------------------------------------------------------------------------
+// Weighted harmonic-average boundary dielectric (Sec. 2.7).  Every edge takes
+// 1 / (w/eps_in + (1-w)/eps_out), w the fraction of the edge (the segment
+// between its two nodes, coordinates o + i*h) strictly inside the union of
+// the atom spheres; w = 0 and w = 1 give eps_out and eps_in exactly.  Each
+// atom whose sphere meets the segment contributes the parameter interval
+//   s = r*r - (du*du + dv*dv),  q = sqrt(s),
+//   t0 = ((c - q) - p) / h,  t1 = ((c + q) - p) / h,  clipped to [0, 1],
+// (u, v the other two axes, every operation rounded on its own); the
+// intervals are sorted by start, then end, merged (touching ones joined) and
+// their lengths summed in order.  Candidate atoms come from a cell list; an
+// FP32 test with a wide margin discards atoms that cannot meet the segment.
+
+// Cell of coordinate v on one axis: cubes of side cs from c0.
+__device__ __forceinline__ int cell_index(double v, double c0, double cs, int n) {
+  const int i = (int)floor((v - c0) / cs);
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+struct Cells {
+  double x0, y0, z0, cs;
+  int ncx, ncy, ncz;
+};
+__device__ __forceinline__ int atom_cell(const Cells &c, const dbl4 &a) {
+  return (cell_index(a.z, c.z0, c.cs, c.ncz) * c.ncy + cell_index(a.y, c.y0, c.cs, c.ncy)) * c.ncx +
+         cell_index(a.x, c.x0, c.cs, c.ncx);
+}
+__global__ void k_cell_count(const dbl4 *atoms, int n_atoms, Cells c, int *count) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n_atoms) atomicAdd(count + atom_cell(c, atoms[a]), 1);
+}
+// Exclusive prefix sum of n counts into start[0..n] (one CTA of 1024 threads,
+// each a contiguous chunk), and the fill cursors.
+__global__ void __launch_bounds__(1024) k_cell_scan(const int *count, int n, int *start, int *cursor) {
+  __shared__ int part[1024];
+  const int per = (n + 1023) / 1024, lo = threadIdx.x * per, hi = min(n, lo + per);
+  int s = 0;
+  for (int t = lo; t < hi; t++) s += count[t];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the chunk sums
+    const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int t = lo; t < hi; t++) {
+    start[t] = run;
+    cursor[t] = run;
+    run += count[t];
+  }
+  if (threadIdx.x == 1023) start[n] = part[1023];
+}
+// list[slot]: the atom; rel[slot]: its position relative to the grid origin
+// and its radius in FP32 (for the pre-test).
+__global__ void k_cell_fill(const dbl4 *atoms, int n_atoms, Cells c, Geom g, int *cursor, int *list,
+                            float4 *rel) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_atoms) return;
+  const dbl4 A = atoms[a];
+  const int slot = atomicAdd(cursor + atom_cell(c, A), 1);
+  list[slot] = a;
+  rel[slot] = make_float4((float)(A.x - g.ox), (float)(A.y - g.oy), (float)(A.z - g.oz), (float)A.w);
+}
+__global__ void k_fill_one(double *a, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    a[e] = 1.0;
+}
+
+constexpr int HARMONIC_MAX_IV = 48;  // intervals one edge may collect
+constexpr int HARMONIC_NT = 128;
+__global__ void __launch_bounds__(HARMONIC_NT)
+    k_harmonic_eps(const dbl4 *atoms, const int *start, const int *list, const float4 *rel, Cells c,
+                   Geom g, double r_max, double ein, double eout, double *ex, double *ey, double *ez,
+                   int *err) {
+  const long nxe = (long)(g.nx + 1) * g.ny * g.nz, nye = (long)g.nx * (g.ny + 1) * g.nz;
+  const long nze = (long)g.nx * g.ny * (g.nz + 1);
+  long t = blockIdx.x * (long)HARMONIC_NT + threadIdx.x;
+  if (t >= nxe + nye + nze) return;
+  int ax;
+  long i, j, k;  // start node of the edge (-1 on the edge axis is the ghost layer)
+  double *out;
+  if (t < nxe) {
+    ax = 0;
+    i = t % (g.nx + 1) - 1; j = (t / (g.nx + 1)) % g.ny; k = t / ((long)(g.nx + 1) * g.ny);
+    out = ex + ((size_t)k * g.ny + j) * g.px + (i + 1);
+  } else if ((t -= nxe) < nye) {
+    ax = 1;
+    i = t % g.nx; j = (t / g.nx) % (g.ny + 1) - 1; k = t / ((long)g.nx * (g.ny + 1));
+    out = ey + ((size_t)k * (g.ny + 1) + (j + 1)) * g.px + i;
+  } else {
+    t -= nye;
+    ax = 2;
+    i = t % g.nx; j = (t / g.nx) % g.ny; k = t / ((long)g.nx * g.ny) - 1;
+    out = ez + ((size_t)(k + 1) * g.ny + j) * g.px + i;
+  }
+  const double p[3] = {__dadd_rn(g.ox, __dmul_rn((double)i, g.h)),
+                       __dadd_rn(g.oy, __dmul_rn((double)j, g.h)),
+                       __dadd_rn(g.oz, __dmul_rn((double)k, g.h))};
+  const double c0[3] = {c.x0, c.y0, c.z0};
+  const int nc[3] = {c.ncx, c.ncy, c.ncz};
+  int lo_c[3], hi_c[3];
+  for (int d = 0; d < 3; d++) {
+    lo_c[d] = cell_index(p[d] - r_max, c0[d], c.cs, nc[d]);
+    hi_c[d] = cell_index(p[d] + (d == ax ? g.h : 0.0) + r_max, c0[d], c.cs, nc[d]);
+  }
+  const int u = (ax + 1) % 3, v = (ax + 2) % 3;
+  // FP32 pre-test relative to the grid origin: the perpendicular distance and
+  // the extent along the axis, with a margin far above their FP32 error
+  const float hf = (float)g.h, MARGIN = 1e-3f;
+  const float pf[3] = {(float)i * hf, (float)j * hf, (float)k * hf};
+  double lo_iv[HARMONIC_MAX_IV], hi_iv[HARMONIC_MAX_IV];
+  int n_iv = 0;
+  bool full = false, overflow = false;
+  for (int cz = lo_c[2]; cz <= hi_c[2] && !full; cz++)
+    for (int cy = lo_c[1]; cy <= hi_c[1] && !full; cy++)
+      for (int cx = lo_c[0]; cx <= hi_c[0] && !full; cx++) {
+        const int cell = (cz * c.ncy + cy) * c.ncx + cx;
+        for (int s = start[cell]; s < start[cell + 1]; s++) {
+          const float4 R = rel[s];
+          const float rc[3] = {R.x, R.y, R.z};
+          const float fu = pf[u] - rc[u], fv = pf[v] - rc[v], fa = rc[ax] - pf[ax];
+          if (fu * fu + fv * fv > R.w * R.w + MARGIN) continue;
+          if (fa + R.w < -MARGIN || fa - R.w > hf + MARGIN) continue;
+          // exact FP64 interval
+          const dbl4 A = atoms[list[s]];
+          const double cc[3] = {A.x, A.y, A.z};
+          const double du = __dsub_rn(p[u], cc[u]), dv = __dsub_rn(p[v], cc[v]);
+          const double d2 = __dadd_rn(__dmul_rn(du, du), __dmul_rn(dv, dv));
+          const double sq = __dsub_rn(__dmul_rn(A.w, A.w), d2);
+          if (!(sq > 0.0)) continue;
+          const double q = __dsqrt_rn(sq);
+          const double t0 = __ddiv_rn(__dsub_rn(__dsub_rn(cc[ax], q), p[ax]), g.h);
+          const double t1 = __ddiv_rn(__dsub_rn(__dadd_rn(cc[ax], q), p[ax]), g.h);
+          const double lo = t0 > 0.0 ? t0 : 0.0, hi = t1 < 1.0 ? t1 : 1.0;
+          if (!(lo < hi)) continue;
+          if (lo == 0.0 && hi == 1.0) {  // one sphere covers the whole edge: w = 1
+            full = true;
+            break;
+          }
+          if (n_iv == HARMONIC_MAX_IV) {
+            overflow = true;
+            continue;
+          }
+          // insertion in (lo, hi) order
+          int at = n_iv++;
+          while (at > 0 && (lo_iv[at - 1] > lo || (lo_iv[at - 1] == lo && hi_iv[at - 1] > hi))) {
+            lo_iv[at] = lo_iv[at - 1];
+            hi_iv[at] = hi_iv[at - 1];
+            at--;
+          }
+          lo_iv[at] = lo;
+          hi_iv[at] = hi;
+        }
+      }
+  if (overflow && !full) atomicOr(err, 4);
+  double w;
+  if (full) {
+    w = 1.0;
+  } else if (n_iv == 0) {
+    w = 0.0;
+  } else {
+    w = 0.0;
+    double lo = lo_iv[0], hi = hi_iv[0];
+    for (int q = 1; q < n_iv; q++) {
+      if (lo_iv[q] <= hi) {
+        if (hi_iv[q] > hi) hi = hi_iv[q];
+      } else {
+        w = __dadd_rn(w, __dsub_rn(hi, lo));
+        lo = lo_iv[q];
+        hi = hi_iv[q];
+      }
+    }
+    w = __dadd_rn(w, __dsub_rn(hi, lo));
+  }
+  *out = w == 0.0 ? eout
+         : w == 1.0 ? ein
+                    : __ddiv_rn(1.0, __dadd_rn(__ddiv_rn(w, ein), __ddiv_rn(__dsub_rn(1.0, w), eout)));
+}
+
+// diag64 (six edges in the order x-, x+, y-, y+, z-, z+, then + kbh2 lambda)
+// and the inner solve's rounded copies; pads hold 1.
+template <typename C>
+__global__ void k_harmonic_finish(const uint8_t *code, Geom g, double kbh2, const double *ex64,
+                                  const double *ey64, const double *ez64, double *diag64, C *ex,
+                                  C *ey, C *ez, float *diag) {
+  const size_t px = g.px, ny = g.ny, nz = g.nz, nx = g.nx;
+  const size_t n_ex = px * ny * nz, n_ey = px * (ny + 1) * nz, n_ez = px * ny * (nz + 1);
+  const size_t n_all = n_ey > n_ez ? n_ey : n_ez;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n_all;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < n_ex) {
+      const size_t i = e % px, row = e / px;
+      const size_t j = row % ny, k = row / ny;
+      double d = 1.0;
+      if (i < nx) {
+        d = ex64[e];
+        d = __dadd_rn(d, ex64[e + 1]);
+        d = __dadd_rn(d, ey64[(k * (ny + 1) + j) * px + i]);
+        d = __dadd_rn(d, ey64[(k * (ny + 1) + j + 1) * px + i]);
+        d = __dadd_rn(d, ez64[(k * ny + j) * px + i]);
+        d = __dadd_rn(d, ez64[((k + 1) * ny + j) * px + i]);
+        d = __dadd_rn(d, __dmul_rn(kbh2, (code[e] & 64u) ? 0.0 : 1.0));
+      }
+      diag64[e] = d;
+      if (diag) diag[e] = (float)d;
+      if (ex) ex[e] = (C)ex64[e];
+    }
+    if (ex && e < n_ey) ey[e] = (C)ey64[e];
+    if (ex && e < n_ez) ez[e] = (C)ez64[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 
 static int grid_for(size_t n, int nt) {
   size_t b = (n + nt - 1) / nt;
   return (int)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
+}
+
+CellPlan cell_plan(const Geom &g, double r_max) {
+  CellPlan p;
+  p.size = r_max + g.h;
+  p.ncx = (int)std::ceil((g.nx + 1) * g.h / p.size) + 3;
+  p.ncy = (int)std::ceil((g.ny + 1) * g.h / p.size) + 3;
+  p.ncz = (int)std::ceil((g.nz + 1) * g.h / p.size) + 3;
+  return p;
+}
+size_t cell_buffer_bytes(const CellPlan &p, int n_atoms) {
+  return sizeof(int) * (3 * (size_t)p.n() + 1 + (size_t)n_atoms) + 16 + sizeof(float4) * (size_t)n_atoms;
 }
 
 cudaError_t launch_setup(const SetupArgs &a, cudaStream_t st) {
@@ -420,8 +661,35 @@ cudaError_t launch_setup(const SetupArgs &a, cudaStream_t st) {
   } else {
     cudaMemsetAsync(a.ghost, 0, sizeof(double) * n_ghost, st);
   }
+  if (a.ex64) {  // harmonic-average dielectric: the FP64 edge arrays, needed by the fold
+    const CellPlan cp = cell_plan(g, a.r_max);
+    const Cells c{g.ox - g.h - cp.size, g.oy - g.h - cp.size, g.oz - g.h - cp.size, cp.size,
+                  cp.ncx, cp.ncy, cp.ncz};
+    const long ncell = cp.n();
+    int *count = (int *)a.cell_buf, *start = count + ncell, *cursor = start + ncell + 1;
+    int *list = cursor + ncell;
+    float4 *rel = (float4 *)(((uintptr_t)(list + a.n_atoms) + 15) & ~(uintptr_t)15);
+    const size_t n_ex = (size_t)g.px * g.ny * g.nz, n_c = (size_t)g.px * (g.ny + 1) * (g.nz + 1);
+    k_fill_one<<<grid_for(n_ex, 256), 256, 0, st>>>(a.ex64, n_ex);
+    k_fill_one<<<grid_for(n_c, 256), 256, 0, st>>>(a.ey64, n_c);
+    k_fill_one<<<grid_for(n_c, 256), 256, 0, st>>>(a.ez64, n_c);
+    cudaMemsetAsync(count, 0, sizeof(int) * ncell, st);
+    if (a.n_atoms > 0) {
+      k_cell_count<<<(a.n_atoms + 255) / 256, 256, 0, st>>>(a.atoms_xyzr, a.n_atoms, c, count);
+      k_cell_scan<<<1, 1024, 0, st>>>(count, (int)ncell, start, cursor);
+      k_cell_fill<<<(a.n_atoms + 255) / 256, 256, 0, st>>>(a.atoms_xyzr, a.n_atoms, c, g, cursor,
+                                                           list, rel);
+    } else {
+      cudaMemsetAsync(start, 0, sizeof(int) * (ncell + 1), st);
+    }
+    const long n_edges = (long)(g.nx + 1) * g.ny * g.nz + (long)g.nx * (g.ny + 1) * g.nz +
+                         (long)g.nx * g.ny * (g.nz + 1);
+    k_harmonic_eps<<<(unsigned)((n_edges + HARMONIC_NT - 1) / HARMONIC_NT), HARMONIC_NT, 0, st>>>(
+        a.atoms_xyzr, start, list, rel, c, g, a.r_max, a.ein, a.eout, a.ex64, a.ey64, a.ez64, a.err);
+  }
   k_fold_rhs<<<FOLD_CTAS, FOLD_NT, 0, st>>>((const long long *)a.b, a.code, a.ghost, g,
-                                            a.c4pi_h / a.q_scale, a.ein, a.eout, a.b, a.scratch);
+                                            a.c4pi_h / a.q_scale, a.ein, a.eout, a.ex64, a.ey64,
+                                            a.ez64, a.b, a.scratch);
   k_sum_final<<<1, 256, 0, st>>>(a.scratch, FOLD_CTAS, a.bnorm2);
   return cudaGetLastError();
 }
@@ -441,6 +709,22 @@ cudaError_t launch_expand(const uint8_t *code, const Geom &g, double ein, double
     k_expand_coef<double, double><<<blocks, 256, 0, st>>>(code, g, ein, eout, kbh2, (double *)ex,
                                                           (double *)ey, (double *)ez,
                                                           (double *)diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_harmonic_finish(const uint8_t *code, const Geom &g, double kbh2, const double *ex64,
+                                   const double *ey64, const double *ez64, double *diag64, int coef,
+                                   void *ex, void *ey, void *ez, void *diag, cudaStream_t st) {
+  const size_t n = (size_t)g.px * (g.ny + 1) * (g.nz + 1);
+  const int blocks = grid_for(n, 256);
+  if (coef == COEF_BF16)
+    k_harmonic_finish<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+        code, g, kbh2, ex64, ey64, ez64, diag64, (__nv_bfloat16 *)ex, (__nv_bfloat16 *)ey,
+        (__nv_bfloat16 *)ez, (float *)diag);
+  else
+    k_harmonic_finish<float><<<blocks, 256, 0, st>>>(code, g, kbh2, ex64, ey64, ez64, diag64,
+                                                      (float *)ex, (float *)ey, (float *)ez,
+                                                      (float *)diag);
   return cudaGetLastError();
 }
 

@@ -971,6 +971,7 @@ static size_t stencil_smem() {  // ring + stages, + alignment slack
 }
 static size_t resid_smem() { return 128 + ring_bytes(sizeof(double)); }
 
+
 // Launch with the programmatic-stream-serialization attribute, so a kernel
 // may be scheduled while its predecessor drains (each waits with
 // griddepcontrol.wait before touching the predecessor's results).

@@ -48,7 +48,8 @@ class GridDesc(ctypes.Structure):
                 ("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double),
                 ("ionic_strength", ctypes.c_double), ("temperature", ctypes.c_double),
                 ("kappa_mask", ctypes.c_int), ("coef", ctypes.c_int),
-                ("dh_precision", ctypes.c_int), ("periodic", ctypes.c_int)]
+                ("dh_precision", ctypes.c_int), ("periodic", ctypes.c_int),
+                ("eps_model", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -179,6 +180,7 @@ def grid_desc(g) -> GridDesc:
     d.coef = COEF[g.coef]
     d.dh_precision = PB_F32 if g.dh == "f32" else PB_F64
     d.periodic = 1 if getattr(g, "periodic", False) else 0
+    d.eps_model = 1 if getattr(g, "eps_model", "midpoint") == "harmonic" else 0
     return d
 
 
