@@ -56,6 +56,16 @@ WORKLOADS = {
 #   stencil pass: read z = M^-1 r, p_old, d (4 B each) and the code byte; write p, Ap, d
 #   update pass:  read z, Ap and the code byte; write z
 BYTES_PER_NODE = {"stencil": 4 + 4 + 4 + 1 + 4 + 4 + 4, "update": 4 + 4 + 1 + 4}
+
+
+def bytes_per_node(coef):
+    """Algorithmic bytes per node of the two passes for a coefficient storage:
+    the packed code byte, or explicit eps_x, eps_y, eps_z (4 or 2 B) and an
+    FP32 diagonal in place of it (the update pass then reads the diagonal)."""
+    if coef == "packed":
+        return dict(BYTES_PER_NODE)
+    c = 2 if coef == "bf16" else 4
+    return {"stencil": 4 + 4 + 4 + 3 * c + 4 + 4 + 4 + 4, "update": 4 + 4 + 4 + 4}
 # DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
 # profiles/ (None until a capture of the current kernel exists).
 NCU_TRAFFIC_PER_NODE = {"stencil": None}
@@ -459,7 +469,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     problem = WORKLOADS[args.workload]()
-    spec = problem.grid.replace(coef=args.coef, dh=args.dh, periodic=args.periodic)
+    spec = problem.grid.replace(coef=args.coef, dh=args.dh, periodic=args.periodic,
+                                eps_model=args.eps_model)
+    if args.eps_model == "harmonic" and args.coef == "packed":
+        spec = spec.replace(coef="f32")  # non-binary edges need explicit coefficients
     n_nodes = spec.n
     snaps = snapshots(problem, 8, seed=100 + rank)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -508,8 +521,9 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     t_st = prof.ms_stencil / max(prof.n_stencil, 1) / 1e3
     t_up = prof.ms_update / max(prof.n_update, 1) / 1e3
-    ach_st = BYTES_PER_NODE["stencil"] * n_nodes / t_st / 1e9
-    ach_up = BYTES_PER_NODE["update"] * n_nodes / t_up / 1e9
+    bpn = bytes_per_node(spec.coef)
+    ach_st = bpn["stencil"] * n_nodes / t_st / 1e9
+    ach_up = bpn["update"] * n_nodes / t_up / 1e9
     trf = NCU_TRAFFIC_PER_NODE["stencil"]
     out = {
         "metric": METRIC,
@@ -529,6 +543,7 @@ def run_ours(args):
                    "solver": "jacobi-pcg fp32 inner + fp64 refinement",
                    "inner_tol": args.inner_tol, "coef": args.coef,
                    "boundary": "periodic" if args.periodic else "Debye-Hueckel",
+                   "eps_model": args.eps_model, "coef_storage": spec.coef,
                    "debye_hueckel_sum": args.dh,
                    "snapshot_sigma_A": SNAPSHOT_SIGMA,
                    "l2": "256 MB buffer written between timed steps",
@@ -539,13 +554,13 @@ def run_ours(args):
         "fp64_plain": {"value": k64 / (sum(d64) / 1e3), "unit": "solves/s",
                        "latency_ms": {"p50": pct(d64, 50), "p99": pct(d64, 99)},
                        "iterations_mean": float(np.mean(it64)), "steps": k64},
-        "roofline": {"bound": "hbm", "kernel": "k_stencil<float,packed> (CG stencil pass)",
+        "roofline": {"bound": "hbm", "kernel": f"k_stencil<float,{spec.coef}> (CG stencil pass)",
                      "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
                      "peak_kind": peak_kind,
-                     "traffic": None if trf is None else trf * n_nodes,
-                     "bytes_per_node": BYTES_PER_NODE["stencil"], "launch_ms": t_st * 1e3,
+                     "traffic": None if trf is None or spec.coef != "packed" else trf * n_nodes,
+                     "bytes_per_node": bpn["stencil"], "launch_ms": t_st * 1e3,
                      "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
-                                     "bytes_per_node": BYTES_PER_NODE["update"],
+                                     "bytes_per_node": bpn["update"],
                                      "launch_ms": t_up * 1e3},
                      "resid_pass_ms": prof.ms_resid / max(prof.n_resid, 1)},
         "e2e": {"value": world * args.steps / total_wall_s, "unit": "solves/s",
@@ -877,11 +892,15 @@ def main():
                     help="serving: requests of the Poisson stream (each arm)")
     ap.add_argument("--coef", default="packed", choices=["packed", "f32", "bf16"])
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--inner-tol", type=float, default=None,
+                    help="inner FP32 tolerance of the refinement (default: 1e-4 for the warm-started "
+                         "serving stream and the batch, 1e-3 for cold single grids)")
     ap.add_argument("--cpu-sample-iters", type=int, default=20)
     ap.add_argument("--dh", default="f32", choices=["f32", "f64"],
                     help="precision of the Debye-Hueckel boundary sum in the grid setup")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eps-model", default="midpoint", choices=["midpoint", "harmonic"],
+                    help="single-grid workloads: boundary dielectric (harmonic: weighted harmonic average)")
     ap.add_argument("--periodic", action="store_true",
                     help="single-grid workloads: periodic boundary instead of Debye-Hueckel")
     ap.add_argument("--profile-range", action="store_true",
@@ -890,6 +909,8 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed loop only (no FP64 comparator, profiled solve or CPU baseline)")
     args = ap.parse_args()
+    if args.inner_tol is None:
+        args.inner_tol = 1e-4 if args.workload in (SERVING, BATCH) else 1e-3
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
