@@ -18,6 +18,8 @@ Functions and the passage each follows:
   (``eps_model="harmonic"``: each edge from the fraction of it inside the atoms)
 * ``solvation_energy`` -- the electrostatic solvation energy of Sec. 3.1 (Figs. 1-2):
   energy of the solvated system minus that of the reference system
+* ``gmg``            -- geometric-multigrid preconditioned CG (Sec. 2 lists GMG, Sec. 4 names
+  multigrid as the next step), numpy, on top of ``apply`` and ``operator_from``
 
 Every function is pinned by the CPU tests (``tests/test_oracle_*.py``) against
 closed forms, special cases and brute force; none is "parity unpinned".
