@@ -71,7 +71,13 @@ enum {
                                residual b - A x, accumulation x += d (not in the paper) */
 };
 
-enum { PB_PRECOND_NONE = 0, PB_PRECOND_JACOBI = 1 };
+/* NONE: plain CG; JACOBI: M = diag A (Sec. 2.4); GMG: a geometric-multigrid
+ * V-cycle (Sec. 2 lists GMG; Sec. 4 names multigrid as the next step): coarse
+ * levels rediscretised at 2h with series-combined edges, trilinear transfer,
+ * two damped-Jacobi sweeps before and after, the outer CG in FP64 and the
+ * V-cycle in FP32 whatever opts->precision says; free-space boundary only,
+ * not served by pb_server. */
+enum { PB_PRECOND_NONE = 0, PB_PRECOND_JACOBI = 1, PB_PRECOND_GMG = 2 };
 
 /* Grid and physical parameters (Sec. 2.7: h = 0.5 A, eps 1 / 80, phi0 = 0). */
 typedef struct {
@@ -103,7 +109,7 @@ typedef struct {
 enum { PB_EPS_MIDPOINT = 0, PB_EPS_HARMONIC = 1 };
 
 typedef struct {
-    int precond;      /* PB_PRECOND_* (Sec. 2.4: Jacobi, M = diag A) */
+    int precond;      /* PB_PRECOND_* (Sec. 2.4: Jacobi, M = diag A; or multigrid) */
     int precision;    /* PB_PREC_* */
     double rel_tol;   /* stop when ||r|| / ||b|| < rel_tol (Sec. 2.2 stopping rule) */
     int max_iter;     /* cap on CG iterations summed over all inner solves */

@@ -28,14 +28,6 @@ pb_status pb_fail(pb_status s, const std::string &msg) {
 
 extern "C" const char *pb_last_error(void) { return g_err.c_str(); }
 
-#define CK(call)                                                                            \
-  do {                                                                                      \
-    cudaError_t e_ = (call);                                                                \
-    if (e_ != cudaSuccess)                                                                  \
-      return pb_fail(e_ == cudaErrorMemoryAllocation ? PB_ERR_OOM : PB_ERR_CUDA,            \
-                     std::string(#call) + ": " + cudaGetErrorString(e_));                   \
-  } while (0)
-
 pb_status pb_dalloc(void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -162,6 +154,7 @@ void pb_grid_release(pb_grid *g) {
                   g->ch_part, g->rs_part};
   for (void *p : ptrs) dfree(p);
   dfree(g->cell_buf);
+  pb_mg_release(g->mg);
   if (g->h_atoms) cudaFreeHost(g->h_atoms);
   delete g;
 }
@@ -240,6 +233,11 @@ pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double 
     g->atom_cap = n_atoms;
   }
   g->n_atoms = n_atoms;
+  if (g->mg) {  // the operator changes: the multigrid hierarchy is rebuilt on the next GMG solve
+    cudaStreamSynchronize(s);
+    pb_mg_release(g->mg);
+    g->mg = nullptr;
+  }
   // The staging is rewritten only by a later setup of this grid, which comes
   // after the grid's solve (a server) or after a synchronisation.
   dbl4 *hq = g->h_atoms, *hr = g->h_atoms + g->atom_cap + 1;
@@ -625,7 +623,7 @@ static pb_status check_opts(const pb_solve_opts *o) {
   if (!o) return pb_fail(PB_ERR_ARG, "opts is NULL");
   if (o->precision < PB_PREC_F64 || o->precision > PB_PREC_F32_REFINE)
     return pb_fail(PB_ERR_ARG, "bad precision");
-  if (o->precond != PB_PRECOND_NONE && o->precond != PB_PRECOND_JACOBI)
+  if (o->precond != PB_PRECOND_NONE && o->precond != PB_PRECOND_JACOBI && o->precond != PB_PRECOND_GMG)
     return pb_fail(PB_ERR_ARG, "bad precond");
   if (!(o->rel_tol > 0) || o->max_iter < 0) return pb_fail(PB_ERR_ARG, "bad tolerance or max_iter");
   if (o->precision == PB_PREC_F32_REFINE && (!(o->inner_tol > 0) || o->max_outer < 1))
@@ -751,6 +749,10 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   pb_status st = check_opts(o);
   if (st) return st;
   CK(cudaSetDevice(g->ctx->device));
+  if (o->precond == PB_PRECOND_GMG) {
+    if (g->d.periodic) return pb_fail(PB_ERR_ARG, "the multigrid preconditioner is for the free-space boundary");
+    return pb_gmg_solve(g, o, phi, info);
+  }
   cudaStream_t s = g->ctx->stream;
   const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
   if (g->bnorm == 0.0) {  // A phi = 0 has the solution phi = 0

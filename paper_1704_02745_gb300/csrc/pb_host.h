@@ -46,6 +46,7 @@ struct pb_grid {
   bool batch = false;        // a server's grid: its work lists and scalars are the server's
   void *cell_buf = nullptr;  // harmonic-average setup: cell list of the atoms
   size_t cell_cap = 0;
+  struct pb_mg *mg = nullptr;  // multigrid hierarchy (built by the first GMG solve)
   pb::Inst *dinst = nullptr;
   pb::Item *st_items = nullptr, *ch_items = nullptr;
   double *st_part = nullptr, *ch_part = nullptr, *rs_part = nullptr;
@@ -66,6 +67,18 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
 pb::Scal pb_initial_scal(double bnorm);
 pb_status pb_check_desc(const pb_grid_desc *d);
 pb_status pb_check_atoms(int n_atoms, const double *xyz, const double *q, const double *radius);
+// Return a pb_status from a CUDA error (in functions returning pb_status).
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return pb_fail(e_ == cudaErrorMemoryAllocation ? PB_ERR_OOM : PB_ERR_CUDA,            \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+// gmg.cu: geometric-multigrid preconditioned CG, and the hierarchy's release.
+pb_status pb_gmg_solve(pb_grid *g, const pb_solve_opts *o, double *phi, pb_solve_info *info);
+void pb_mg_release(struct pb_mg *m);
 pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_grid **out);
 pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
                        const double *radius, bool sync);

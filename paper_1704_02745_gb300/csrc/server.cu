@@ -813,6 +813,8 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   if (o.precision < PB_PREC_F64 || o.precision > PB_PREC_F32_REFINE || !(o.rel_tol > 0) ||
       (o.precision == PB_PREC_F32_REFINE && (!(o.inner_tol > 0) || o.max_outer < 1)))
     return pb_fail(PB_ERR_ARG, "pb_server_create: bad solve options");
+  if (o.precond != PB_PRECOND_NONE && o.precond != PB_PRECOND_JACOBI)
+    return pb_fail(PB_ERR_ARG, "pb_server_create: the server runs CG or Jacobi-PCG");
   if (o.precision != PB_PREC_F32_REFINE) o.max_outer = 1;
   if (o.max_iter <= 0) o.max_iter = 100000;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return pb_fail(PB_ERR_CUDA, "cudaSetDevice");

@@ -25,7 +25,7 @@ PB_ERR_NOT_CONVERGED, PB_ERR_BREAKDOWN, PB_ERR_TIMEOUT, PB_ERR_BUSY, PB_ERR_NOT_
 COEF = {"packed": 0, "f32": 1, "bf16": 2, "f64": 3}
 PB_F64, PB_F32 = 0, 1
 PREC = {"f64": 0, "f32": 1, "f32_refine": 2}
-PRECOND = {"none": 0, "jacobi": 1}
+PRECOND = {"none": 0, "jacobi": 1, "gmg": 2}
 EXPORT = {"eps_x": 0, "eps_y": 1, "eps_z": 2, "lambda": 3, "b": 4, "ghost": 5}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 5: "ERR_NOT_CONVERGED",
                 6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_BUSY", 9: "ERR_NOT_FOUND"}
