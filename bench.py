@@ -52,23 +52,28 @@ WORKLOADS = {
     "globule257": inputs.globule_257,
 }
 # Algorithmic HBM bytes per grid node of one launch of each phase kernel
-# (FP32 inner solve, packed one-byte coefficients):
-#   stencil pass: read z = M^-1 r, p_old, d (4 B each) and the code byte; write p, Ap, d
-#   update pass:  read z, Ap and the code byte; write z
-BYTES_PER_NODE = {"stencil": 4 + 4 + 4 + 1 + 4 + 4 + 4, "update": 4 + 4 + 1 + 4}
+# (FP32 inner solve, packed one-byte coefficients).  Grids of a server batch:
+#   stencil pass: read z = M^-1 r, p_old, d (4 B each) and the code byte; write p, d
+#   update pass (over the stencil tiles): read p (Ap is formed again from it), z
+#   and the code byte; write z
+BYTES_PER_NODE = {"stencil": 4 + 4 + 4 + 1 + 4 + 4, "update": 4 + 4 + 1 + 4}
+# A single grid: the stencil pass also writes Ap, which the update pass (over
+# row chunks) reads in place of p.
+BYTES_PER_NODE_GRID = {"stencil": 4 + 4 + 4 + 1 + 4 + 4 + 4, "update": 4 + 4 + 1 + 4}
 
 
 def bytes_per_node(coef):
-    """Algorithmic bytes per node of the two passes for a coefficient storage:
-    the packed code byte, or explicit eps_x, eps_y, eps_z (4 or 2 B) and an
-    FP32 diagonal in place of it (the update pass then reads the diagonal)."""
+    """Algorithmic bytes per node of the two passes of a single-grid solve for a
+    coefficient storage: the packed code byte, or explicit eps_x, eps_y, eps_z
+    (4 or 2 B) and an FP32 diagonal in place of it (the update pass then reads
+    the diagonal)."""
     if coef == "packed":
-        return dict(BYTES_PER_NODE)
+        return dict(BYTES_PER_NODE_GRID)
     c = 2 if coef == "bf16" else 4
     return {"stencil": 4 + 4 + 4 + 3 * c + 4 + 4 + 4 + 4, "update": 4 + 4 + 4 + 4}
 # DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
 # profiles/ (None until a capture of the current kernel exists).
-NCU_TRAFFIC_PER_NODE = {"stencil": None}
+NCU_TRAFFIC_PER_NODE = {"stencil_batch": None, "stencil_grid": None}
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
 
 
@@ -386,7 +391,7 @@ def run_serving(args):
     t_up = kp.ms_update / max(kp.launches_update, 1) / 1e3
     ach_st = kp.bytes_stencil / max(kp.ms_stencil, 1e-12) / 1e6
     ach_up = kp.bytes_update / max(kp.ms_update, 1e-12) / 1e6
-    trf = NCU_TRAFFIC_PER_NODE["stencil"]
+    trf = NCU_TRAFFIC_PER_NODE["stencil_batch"]
     out = {
         "metric": METRIC,
         "value": world * n_req / total,
@@ -426,7 +431,7 @@ def run_serving(args):
                      "kernel": "k_stencil<float,packed>: batched stencil pass over the active grids",
                      "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
                      "peak_kind": peak_kind,
-                     "traffic": None if trf is None else trf * kp.bytes_stencil / 25.0 /
+                     "traffic": None if trf is None else trf * kp.bytes_stencil / BYTES_PER_NODE["stencil"] /
                      max(kp.launches_stencil, 1),
                      "bytes_per_launch": kp.bytes_stencil / max(kp.launches_stencil, 1),
                      "bytes_per_node": BYTES_PER_NODE["stencil"], "launch_ms": t_st * 1e3,
@@ -530,7 +535,7 @@ def run_ours(args):
     bpn = bytes_per_node(spec.coef)
     ach_st = bpn["stencil"] * n_nodes / t_st / 1e9
     ach_up = bpn["update"] * n_nodes / t_up / 1e9
-    trf = NCU_TRAFFIC_PER_NODE["stencil"]
+    trf = NCU_TRAFFIC_PER_NODE["stencil_grid"]
     out = {
         "metric": METRIC,
         "value": world * args.steps / total_dev_s,

@@ -181,7 +181,7 @@ void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
   g->tiles_x = (nx + WMAX - 1) / WMAX;
   g->W = round_up((nx + g->tiles_x - 1) / g->tiles_x, NV);
-  const int hmax = std::min(HMAX, NV * NT / g->W);
+  const int hmax = std::min(HMAX, TILE_NODES / g->W);
   g->tiles_y = (ny + hmax - 1) / hmax;
   g->H = (ny + g->tiles_y - 1) / g->tiles_y;
   const int cols = g->tiles_x * g->tiles_y;
@@ -379,7 +379,7 @@ pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_g
     }
   }
 #undef ALLOC
-  pb_tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms), batch);
+  pb_tile_plan(g, kernel_grid(MODE_F32, COEF_PACKED, ctx->num_sms, !batch), batch);
   g->batch = batch;
   *out = g;
   return PB_OK;
@@ -445,14 +445,15 @@ pb_status pb_ensure_workspace(pb_grid *g, int mode) {
     if ((st = alloc0((void **)&g->z64, n * 8))) return st;
     if ((st = alloc0((void **)&g->p064, n * 8))) return st;
     if ((st = alloc0((void **)&g->p164, n * 8))) return st;
-    if ((st = alloc0((void **)&g->ap64, n * 8))) return st;
+    if (!g->batch && (st = alloc0((void **)&g->ap64, n * 8))) return st;
   } else {
     if ((st = alloc0(&g->d32, n * 4))) return st;
     if ((st = alloc0(&g->z32, n * 4))) return st;
     if ((st = alloc0(&g->p032, n * 4))) return st;
     if ((st = alloc0(&g->p132, n * 4))) return st;
-    if ((st = alloc0(&g->ap32, n * 4))) return st;
+    if (!g->batch && (st = alloc0(&g->ap32, n * 4))) return st;
   }
+  // (a server's grids hold no Ap: its update pass forms Ap again from p)
   if (g->batch) return PB_OK;  // scalars, descriptor and work lists are the server's
   if ((st = alloc0((void **)&g->scal, sizeof(Scal)))) return st;
   if ((st = alloc0((void **)&g->dinst, sizeof(Inst)))) return st;
@@ -574,6 +575,7 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   I.off_c = L.off_c;
   I.off_x = L.off_x;
   I.tma_bytes = L.tma_bytes;
+  I.tma_bytes_upd = L.tma_bytes_upd;
   if (!o) return PB_OK;  // operator application needs no descriptors
   const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -584,7 +586,8 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
       !encode_map(&I.tm_p1, I.p1, dt, es, g, L.rw, L.rows) ||
       !encode_map(&I.tm_code, g->code, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, L.cw, L.rows) ||
       !encode_map(&I.tm_x0, x0, dt, es, g, g->W, g->H) ||
-      !encode_map(&I.tm_x1, x1, dt, es, g, g->W, g->H))
+      !encode_map(&I.tm_x1, x1, dt, es, g, g->W, g->H) ||
+      !encode_map(&I.tm_zc, I.z, dt, es, g, g->W, g->H))
     return pb_fail(PB_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return PB_OK;
 }
@@ -663,7 +666,7 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
       cudaGraphExecDestroy(g->graph);
       g->graph = nullptr;
     }
-    KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms);
+    KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms, true);
     kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
     kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
     Batch B = pb_single_batch(g);
@@ -693,7 +696,7 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
 // with a synchronisation after each so that its work kind is known.
 static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, pb_solve_info *info) {
   cudaStream_t s = g->ctx->stream;
-  KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms);
+  KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms, true);
   kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
   kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
   Batch B = pb_single_batch(g);

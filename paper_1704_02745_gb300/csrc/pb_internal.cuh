@@ -37,6 +37,10 @@ constexpr int NT = 256;        // threads per stencil CTA
 constexpr int NV = 4;          // x columns per thread (16-byte vectors of FP32)
 constexpr int WMAX = 64;       // widest tile
 constexpr int HMAX = 24;       // tallest tile
+#ifndef PB_TILE_NODES
+#define PB_TILE_NODES 1024
+#endif
+constexpr int TILE_NODES = PB_TILE_NODES;  // W*H at most (<= NV*NT)
 constexpr int NT_UPD = 256;    // threads per update CTA
 constexpr int CH = 2048;       // fewest elements per chunk of the update pass
 constexpr int RESID_TZ = 4;    // z planes per item of the residual pass
@@ -72,9 +76,11 @@ struct Scal {
 // The TMA descriptors come first (64-byte aligned).
 struct alignas(64) Inst {
   CUtensorMap tm_z, tm_p0, tm_p1, tm_code, tm_x0, tm_x1;  // z, p buffers, codes, inner x
+  CUtensorMap tm_zc;                  // z, centre box (the update pass)
   int W, H;                           // stencil tile
   int cw;                             // width of the code box (bytes, multiple of 16)
   int stage_bytes, off_p, off_c, off_x, tma_bytes;  // TMA stage layout and bytes per stage
+  int tma_bytes_upd;                  // ... per stage of the update pass (no second halo box)
   int rows_per_chunk;                 // update-pass chunk
   uint32_t vx_magic;                  // ceil(2^32 / vectors per row), for row = f*magic >> 32
   int nx, ny, nz, px;

@@ -191,9 +191,9 @@ struct pb_server {
   Inst *d_inst = nullptr;
   int *d_counts = nullptr, *d_list = nullptr, *d_err = nullptr;
   int *d_rlist = nullptr;  // instances waiting for a residual pass
-  Item *d_st = nullptr, *d_ch = nullptr;
-  double *d_st_part = nullptr, *d_ch_part = nullptr, *d_rs_part = nullptr;
-  size_t cap_st = 0, cap_ch = 0, cap_rs = 0;
+  Item *d_st = nullptr;
+  double *d_st_part = nullptr, *d_rs_part = nullptr;
+  size_t cap_st = 0, cap_rs = 0;
   double *d_dense = nullptr;
   size_t cap_dense = 0;
   cudaGraphExec_t graph = nullptr;
@@ -383,24 +383,22 @@ bool stage_items(Stage &st, size_t n) {
 }
 
 bool rebuild_batch(pb_server *s, Stage &sg, bool *graph_stale) {
-  std::vector<Item> st, ch;
+  std::vector<Item> st;
   std::vector<int> active;
   for (int j = 0; j < (int)s->slots.size(); j++)
     if (s->slots[j].g && s->slots[j].busy) active.push_back(j);
-  int st_off = 0, ch_off = 0, rs_off = 0, hi = 0;
+  int st_off = 0, rs_off = 0, hi = 0;
   for (int j : active) {
     pb_grid *g = s->slots[j].g;
     Inst &I = sg.inst[j];
     if (pb_make_inst(g, &s->opts, s->mode, s->coef, I)) return false;
     I.s = s->d_scal + j;
+    I.ap = nullptr;  // the update pass forms Ap again from p (k_update_tile)
     I.st_base = st_off;
-    I.ch_base = ch_off;
     I.rs_base = rs_off;
     rs_off += g->n_rs;
     for (int t = 0; t < g->n_st; t++) st.push_back(Item{j, t});
-    for (int t = 0; t < g->n_ch; t++) ch.push_back(Item{j, t});
     st_off += g->n_st;
-    ch_off += g->n_ch;
     hi = j + 1;
   }
   // descriptors of slots [0, hi): the idle ones among them are never read
@@ -418,29 +416,20 @@ bool rebuild_batch(pb_server *s, Stage &sg, bool *graph_stale) {
     const int bz = it.tile / (g->tiles_x * g->tiles_y);
     return (long)g->W * g->H * (std::min(g->tz, g->d.nz - bz * g->tz) + 2);
   };
-  auto ch_cost = [&](const Item &it) {
-    const pb_grid *g = s->slots[it.inst].g;
-    const long rows = (long)g->d.ny * g->d.nz;
-    return std::min<long>(g->rows_per_chunk, rows - (long)it.tile * g->rows_per_chunk) * g->d.nx;
-  };
   std::stable_sort(st.begin(), st.end(),
                    [&](const Item &a, const Item &b) { return st_cost(a) > st_cost(b); });
-  std::stable_sort(ch.begin(), ch.end(),
-                   [&](const Item &a, const Item &b) { return ch_cost(a) > ch_cost(b); });
   const double *old_rs = s->d_rs_part;
   if (!grow(&s->d_rs_part, &s->cap_rs, 2 * (size_t)std::max(rs_off, 1))) {
     s->worker_error = "out of device memory for the partial sums";
     return false;
   }
   if (s->d_rs_part != old_rs) *graph_stale = true;
-  const size_t old_st = s->cap_st, old_ch = s->cap_ch;
-  Item *ost = s->d_st, *och = s->d_ch;
-  if (!grow(&s->d_st, &s->cap_st, std::max<size_t>(st.size(), 1)) ||
-      !grow(&s->d_ch, &s->cap_ch, std::max<size_t>(ch.size(), 1))) {
+  const size_t old_st = s->cap_st;
+  Item *ost = s->d_st;
+  if (!grow(&s->d_st, &s->cap_st, std::max<size_t>(st.size(), 1))) {
     s->worker_error = "out of device memory for the work lists";
     return false;
   }
-  size_t cst = old_st, cch = old_ch;
   // partials follow the item capacity
   if (s->cap_st != old_st || s->d_st != ost) {
     cudaFree(s->d_st_part);
@@ -448,35 +437,24 @@ bool rebuild_batch(pb_server *s, Stage &sg, bool *graph_stale) {
     pb_dalloc((void **)&s->d_st_part, 2 * sizeof(double) * s->cap_st);
     *graph_stale = true;
   }
-  if (s->cap_ch != old_ch || s->d_ch != och) {
-    cudaFree(s->d_ch_part);
-    s->d_ch_part = nullptr;
-    pb_dalloc((void **)&s->d_ch_part, 2 * sizeof(double) * s->cap_ch);
-    *graph_stale = true;
-  }
-  (void)cst; (void)cch;
-  if (!s->d_st_part || !s->d_ch_part) {
+  if (!s->d_st_part) {
     s->worker_error = "out of device memory for the partial sums";
     return false;
   }
-  if (!stage_items(sg, st.size() + ch.size())) {
+  if (!stage_items(sg, st.size())) {
     s->worker_error = "out of pinned host memory for the work lists";
     return false;
   }
   std::copy(st.begin(), st.end(), sg.items);
-  std::copy(ch.begin(), ch.end(), sg.items + st.size());
   sg.counts[0] = (int)st.size();
-  sg.counts[1] = (int)ch.size();
+  sg.counts[1] = 0;
   if (!st.empty() && !cuda_ok(cudaMemcpyAsync(s->d_st, sg.items, st.size() * sizeof(Item),
-                                              cudaMemcpyHostToDevice, s->stream), s, "items"))
-    return false;
-  if (!ch.empty() && !cuda_ok(cudaMemcpyAsync(s->d_ch, sg.items + st.size(), ch.size() * sizeof(Item),
                                               cudaMemcpyHostToDevice, s->stream), s, "items"))
     return false;
   if (!cuda_ok(cudaMemcpyAsync(s->d_counts, sg.counts, 2 * sizeof(int), cudaMemcpyHostToDevice,
                                s->stream), s, "counts"))
     return false;
-  s->ctx->stats->h2d += (st.size() + ch.size()) * sizeof(Item) + 2 * sizeof(int);
+  s->ctx->stats->h2d += st.size() * sizeof(Item) + 2 * sizeof(int);
   return true;
 }
 
@@ -489,14 +467,14 @@ bool run_graph(pb_server *s, bool stale) {
     Batch B;
     B.inst = s->d_inst;
     B.st_items = s->d_st;
-    B.ch_items = s->d_ch;
+    B.ch_items = nullptr;
     B.n_items = s->d_counts;
     B.work = (unsigned *)(s->d_counts + 4);
     B.resid_pending = s->d_counts + 2;
     B.resid_list = s->d_rlist;
     B.rs_part = s->d_rs_part;
     B.st_part = s->d_st_part;
-    B.ch_part = s->d_ch_part;
+    B.ch_part = nullptr;
     B.error = s->d_err;
     cudaGraph_t g;
     if (!cuda_ok(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), s, "capture"))
@@ -628,9 +606,9 @@ double launch_bytes(pb_server *s, const std::vector<int> &active, int which) {
     if (which == 4) {
       if (ph == PH_RESID) b += n * 37;
     } else if (which == 1) {
-      if (ph == PH_INNER || ph == PH_START) b += n * (f64 ? 49 : 25);
+      if (ph == PH_INNER || ph == PH_START) b += n * (f64 ? 41 : 21);
     } else if (ph == PH_INNER) {
-      b += n * (f64 ? 25 : 13);
+      b += n * (f64 ? 25 : 13);  // p, code, z read; z written
     }
   }
   return b;
@@ -642,14 +620,14 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
   Batch B;
   B.inst = s->d_inst;
   B.st_items = s->d_st;
-  B.ch_items = s->d_ch;
+  B.ch_items = nullptr;
   B.n_items = s->d_counts;
   B.work = (unsigned *)(s->d_counts + 4);
   B.resid_pending = s->d_counts + 2;
   B.resid_list = s->d_rlist;
   B.rs_part = s->d_rs_part;
   B.st_part = s->d_st_part;
-  B.ch_part = s->d_ch_part;
+  B.ch_part = nullptr;
   B.error = s->d_err;
   const int hi = *std::max_element(active.begin(), active.end()) + 1;
   for (int t = 0; t < 3 * s->ticks; t++) {
@@ -825,7 +803,8 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   s->mode = o.precision == PB_PREC_F64 ? MODE_F64 : o.precision == PB_PREC_F32 ? MODE_F32
                                                                                 : MODE_F32_REFINE;
   s->coef = COEF_PACKED;
-  s->kg = kernel_grid(s->mode, s->coef, ctx->num_sms);
+  s->kg = kernel_grid(s->mode, s->coef, ctx->num_sms, false);
+  s->kg.tile_update = 1;
   s->slots.resize(MAX_SLOTS);
   for (int j = MAX_SLOTS - 1; j >= 0; j--) s->free_slots.push_back(j);
   bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
@@ -884,8 +863,8 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
       s->slots[j].g = nullptr;
     }
   if (s->graph) cudaGraphExecDestroy(s->graph);
-  void *ptrs[] = {s->d_scal, s->d_inst, s->d_counts, s->d_list, s->d_err, s->d_st, s->d_ch,
-                  s->d_st_part, s->d_ch_part, s->d_rs_part, s->d_rlist, s->d_dense};
+  void *ptrs[] = {s->d_scal, s->d_inst, s->d_counts, s->d_list, s->d_err, s->d_st,
+                  s->d_st_part, s->d_rs_part, s->d_rlist, s->d_dense};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->h_scal) cudaFreeHost(s->h_scal);

@@ -10,10 +10,11 @@
 //       x_{l-1} = x_{l-2} + alpha_{l-1} p_{l-2}     (the previous step's x update,
 //                                                    deferred to this pass)
 //     finaliser: alpha_l = (r.z) / (p.Ap)
-//   update pass (k_update):
+//   update pass (k_update over row chunks, reading the Ap the stencil pass
+//   stored; or k_update_tile over the stencil tiles, forming Ap again):
 //       r_l = r_{l-1} - alpha_l Ap_{l-1}; z_l = M^-1 r_l; partial r.z, r.r
 //     finaliser: beta_l = (r.z)_l / (r.z)_{l-1}; ||r_l|| / ||rhs|| < tol -> stop
-// The same stencil kernel runs the RESID phase, FP64 throughout:
+// The residual pass (k_resid, RESID phase, the x and b - A x arithmetic FP64):
 //       x_new = x64 + d + alpha p   (the last deferred update folded in)
 //       r64 = b - A x_new; inner rhs r = (T) r64; partial ||r64||^2, r.z
 //     finaliser: FP64 true residual test, then DONE or a new inner solve
@@ -25,13 +26,13 @@
 // tile) items and skips instances in another phase (convergence masks).
 //
 // Stencil-pass data movement: a CTA owns a W x H column tile and marches over
-// its z range.  One thread issues TMA tile loads (cp.async.bulk.tensor) of r,
+// its z range.  One thread issues TMA tile loads (cp.async.bulk.tensor) of z,
 // p_old (tile + one-node halo, x widened to the 16-byte rule), the code bytes
 // and the centre tile of x, NSTAGE planes ahead of the plane being computed,
 // each stage completing on its own mbarrier.  The grid boundary needs no test:
 // TMA fills out-of-range elements with zeros, which is exactly the zero ghost
-// of the operator.  New directions p are built in a triple-buffered shared
-// plane with halo; the z neighbours stay in registers.
+// of the operator.  New directions p are built in a ring of four shared
+// planes with halo, from which the seven-point stencil reads.
 #include <cuda_bf16.h>
 
 #include <type_traits>
@@ -61,12 +62,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
+#ifdef PB_WAIT_HINT
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(PB_WAIT_HINT)
+      : "memory");
+#else
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
+#endif
   return ok != 0;
 }
 // Wait for phase `parity` of a barrier, giving up after ~1 s of clock.
@@ -194,22 +204,35 @@ struct StageRing {
 };
 
 // ---------------------------------------------------------------------------
-// INNER phase, stencil pass of one tile (TMA pipeline).  Returns this
-// thread's p.Ap; sets `abort` if a pipeline wait timed out.
+// INNER phase, one tile of either pass of a CG iteration (TMA pipeline, a
+// ring of p planes in shared memory, Ap from the ring):
 //
-// The update pass stores z = M^-1 r, so the new direction p = z + beta p_old
-// is one fused multiply-add per node, halo included.  dtab: the diagonal of
-// the FP32/FP64 operator for every code byte, in shared memory per item.
+//   PASS 0 (direction): p = z + beta p_old (one fused multiply-add per node,
+//     halo included, since the stored vector is z = M^-1 r), Ap, this
+//     thread's p.Ap in v0; stores p and the deferred x update, and Ap when
+//     I.ap is set (for the row-chunk update pass).
+//   PASS 1 (update, batches): loads the p just stored, forms Ap again -- the
+//     same operations in the same order, so bit for bit the Ap of pass 0 --
+//     then r = M z - alpha Ap, z = M^-1 r; stores z; r.z in v0, r.r in v1.
+//
+// Recomputing Ap costs the p read of pass 1 (4 B per node) and saves the Ap
+// write of pass 0 and read of pass 1 (8 B), but a tile pass runs at a fixed
+// time per plane and tile, whatever its bytes: it pays where many grids fill
+// every SM with tiles (a server batch), not on one grid, where the row-chunk
+// update pass streams at close to the copy rate.  dtab: the operator's diagonal,
+// mtab: {M, M^-1}, by code byte, in shared memory per item.  Sets `abort`
+// if a pipeline wait timed out.
 //
 // Periodic grids: the z planes before and after the grid are the last and
 // the first (the TMA loads wrap the plane index), and every ring cell that
 // lies outside the grid in x or y -- halo cells and the overhanging lanes and
 // rows of the last tiles -- takes the wrapped node's value from global memory.
-template <typename T, int CM, int NS>
-__device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int tile,
-                                          uint8_t *stages, T *ring, const T *dtab,
-                                          uint64_t *full, StageRing &SR, bool &abort) {
+template <typename T, int CM, int NS, int PASS>
+__device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int tile, uint8_t *stages,
+                                        T *ring, const T *dtab, const Pair<T> *mtab, uint64_t *full,
+                                        StageRing &SR, bool &abort, double &v0, double &v1) {
   constexpr bool SEP = sizeof(T) == 4;  // FP32 inner solves accumulate into d
+  constexpr bool UPD = PASS == 1;
   const TileG G = tile_g(I, tile, I.tz);
   const HaloG Hh = halo_g(I);
   const int W = I.W, H = I.H, RW = W + 2 * NV, CW = I.cw, RGW = W + 2 * NV;
@@ -217,19 +240,22 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
   // descriptor fields used in the plane loop, held in registers (the asm
   // statements of the pipeline clobber memory, which would force reloads)
   const uint32_t stage_bytes = I.stage_bytes, off_p = I.off_p, off_c = I.off_c, off_x = I.off_x;
-  const uint32_t tma_bytes = I.tma_bytes;
+  const uint32_t tma_bytes = UPD ? I.tma_bytes_upd : I.tma_bytes;
   const int cx0 = ((G.x0 - 1) >> 4) << 4;  // code box start: 16-byte aligned, <= x0 - 1
   const int Q = (G.z1 - G.z0) + 2;         // planes z0-1 .. z1
   const bool first = S.phase == PH_START;
   const T beta = first ? (T)0 : (T)S.beta, alpha = (T)S.alpha;
   const T ei = e_in<T>(I), eo = e_out<T>(I);
+  // pass 0: p_old; pass 1: the p pass 0 stored (its finaliser flipped pbuf)
   const CUtensorMap *m_pold = S.pbuf ? &I.tm_p1 : &I.tm_p0;
   const CUtensorMap *m_x = SEP ? &I.tm_x0 : (S.xbuf ? &I.tm_x1 : &I.tm_x0);
   const size_t plane = (size_t)I.px * I.ny;
   const size_t ec0 = (size_t)(G.y0 + G.ty) * I.px + (G.x0 + G.tx);
   // output pointers walk plane by plane (first written plane: z0)
   T *pnew = (T *)(S.pbuf ? I.p0 : I.p1) + (size_t)G.z0 * plane + ec0;
-  T *ap = (T *)I.ap + (size_t)G.z0 * plane + ec0;
+  T *zout = (T *)I.z + (size_t)G.z0 * plane + ec0;
+  const bool store_ap = !UPD && I.ap != nullptr;  // the row-chunk update pass reads Ap
+  T *ap = store_ap ? (T *)I.ap + (size_t)G.z0 * plane + ec0 : pnew;
   T *x = (SEP ? (T *)I.d : (T *)(S.xbuf ? I.x64b : I.x64)) + (size_t)G.z0 * plane + ec0;
   const bool per = I.periodic != 0;
   const int nzg = I.nz;
@@ -238,8 +264,10 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
   auto wrapped_p = [&](int gx, int gy, int zt) -> T {
     const int xw = gx % I.nx, yw = gy < 0 ? gy + I.ny : gy % I.ny;
     const size_t e = (size_t)zt * plane + (size_t)yw * I.px + xw;
+    const T pv = ((const T *)(S.pbuf ? I.p1 : I.p0))[e];
+    if (UPD) return pv;
     const T zv = ((const T *)I.z)[e];
-    return first ? zv : zv + beta * ((const T *)(S.pbuf ? I.p1 : I.p0))[e];
+    return first ? zv : zv + beta * pv;
   };
 
   // thread 0 issues plane z0-1+q into stage st
@@ -247,10 +275,16 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
     uint8_t *sb = stages + st * stage_bytes;
     const int z = zwrap(G.z0 - 1 + q);
     mbar_expect_tx(&full[st], tma_bytes);
-    tma_load_3d(sb, &I.tm_z, &full[st], G.x0 - NV, G.y0 - 1, z);
-    tma_load_3d(sb + off_p, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
-    tma_load_3d(sb + off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
-    tma_load_3d(sb + off_x, m_x, &full[st], G.x0, G.y0, z);
+    if (UPD) {  // p (halo box) in the first slot, the z centre box in the x slot
+      tma_load_3d(sb, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
+      tma_load_3d(sb + off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
+      tma_load_3d(sb + off_x, &I.tm_zc, &full[st], G.x0, G.y0, z);
+    } else {
+      tma_load_3d(sb, &I.tm_z, &full[st], G.x0 - NV, G.y0 - 1, z);
+      tma_load_3d(sb + off_p, m_pold, &full[st], G.x0 - NV, G.y0 - 1, z);
+      tma_load_3d(sb + off_c, &I.tm_code, &full[st], cx0, G.y0 - 1, z);
+      tma_load_3d(sb + off_x, m_x, &full[st], G.x0, G.y0, z);
+    }
   };
   if (threadIdx.x == 0) {
     uint32_t st = SR.st;
@@ -269,7 +303,8 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
   const int hg = (Hh.hy + 1) * RGW + NV + Hh.hx;
 
   uint32_t code_prev = 0;
-  T acc = 0;
+  T acc = 0, rz = 0, rr = 0;
+  Vec<T> z_prev = {};  // pass 1: z of the plane whose Ap is formed next
   // ring slot of plane q; planes q-1 and q-2 sit in the two slots before it.
   // A thread writes slot q while a slower one, still in its pass q-1, may
   // read the slots of q-2 and q-3: hence four slots with one barrier a plane.
@@ -289,15 +324,16 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
     T *rg = ring + rq * ring_plane;
     const int rq1 = (rq + CG_RING_PLANES - 1) % CG_RING_PLANES, rq2 = (rq + CG_RING_PLANES - 2) % CG_RING_PLANES;
     const int z = G.z0 - 1 + q;
-    Vec<T> pn = {};
+    Vec<T> pn = {}, zc = {};
     uint32_t codes = 0;
     // z and p_old are zero outside the grid (TMA fill, zero pads), and so is
     // p; the first direction is z itself, whatever p_old holds
     if (ok && G.in_tile) {
-      pn = ldv(sz + cr);
-      const Vec<T> po = ldv(sp + cr);
+      pn = ldv(sz + cr);  // pass 1: p itself
+      const Vec<T> po = UPD ? Vec<T>{} : ldv(sp + cr);
       codes = *(const uint32_t *)(sc + cc);
-      if (!first) {
+      if (UPD) zc = ldv(sx + cx);
+      if (!UPD && !first) {
 #pragma unroll
         for (int u = 0; u < NV; u++) pn.v[u] += beta * po.v[u];
       }
@@ -310,7 +346,7 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
       stv(rg + cg, pn);
       // deferred update of the previous iteration: x += alpha p_old (the
       // first inner iteration starts the FP32 increment d from zero)
-      if (G.vmask && q >= 1 && q < Q - 1) {
+      if (!UPD && G.vmask && q >= 1 && q < Q - 1) {
         Vec<T> xn = {};
         if (!first) {
           xn = ldv(sx + cx);
@@ -320,13 +356,13 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
         if (SEP || !first) stv(x, xn);
       }
     }
-    if (q >= 1 && q < Q - 1) x += plane;
+    if (!UPD && q >= 1 && q < Q - 1) x += plane;
     if (ok && Hh.role) {
       const int gx = G.x0 + Hh.hx, gy = G.y0 + Hh.hy;
       if (per && (gx < 0 || gx >= I.nx || gy < 0 || gy >= I.ny))
         rg[hg] = wrapped_p(gx < 0 ? gx + I.nx : gx, gy, zwrap(z));
       else
-        rg[hg] = first ? sz[hr] : sz[hr] + beta * sp[hr];
+        rg[hg] = UPD || first ? sz[hr] : sz[hr] + beta * sp[hr];
     }
     if (__syncthreads_or(!ok)) {
       // A wait gave up: let the copies already issued land, each for a
@@ -342,7 +378,8 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
         SR.st = s2;
       }
       abort = true;
-      return 0.0;
+      v0 = v1 = 0.0;
+      return;
     }
     if (threadIdx.x == 0 && q + NS < Q) {
       issue(q + NS, st_issue);
@@ -394,9 +431,29 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
           }
           if (!((G.vmask >> u) & 1u)) av = 0;  // pad columns keep Ap = 0
           a.v[u] = av;
-          acc += pc.v[u] * av;
+          if (!UPD) acc += pc.v[u] * av;
         }
-        if (per) {  // pad lanes of the ring hold wrapped values; p keeps zero pads
+        if (UPD) {
+          // r = M z - alpha Ap, z = M^-1 r (pads: z = Ap = 0 stay 0)
+          Vec<T> zn;
+#pragma unroll
+          for (int u = 0; u < NV; u++) {
+            T m, mi = (T)1;
+            if (CM == COEF_PACKED) {
+              const Pair<T> t = mtab[(code_prev >> (8 * u)) & 127u];
+              m = t.d;
+              mi = t.i;
+            } else {
+              m = I.precond && ((G.vmask >> u) & 1u)
+                      ? ((const T *)I.diag)[(size_t)(z - 1) * plane + ec0 + u] : (T)1;
+            }
+            const T r = m * z_prev.v[u] - alpha * a.v[u];
+            zn.v[u] = CM == COEF_PACKED ? r * mi : r / m;
+            rz += r * zn.v[u];
+            rr += r * r;
+          }
+          stv(zout, zn);
+        } else if (per) {  // pad lanes of the ring hold wrapped values; p keeps zero pads
           Vec<T> pst = pc;
 #pragma unroll
           for (int u = 0; u < NV; u++)
@@ -405,14 +462,21 @@ __device__ __forceinline__ double cg_tile(const Inst &I, const TileScal &S, int 
         } else {
           stv(pnew, pc);
         }
-        stv(ap, a);
+        if (store_ap) stv(ap, a);
       }
-      pnew += plane; ap += plane;
+      if (UPD) {
+        zout += plane;
+      } else {
+        pnew += plane;
+        ap += plane;
+      }
     }
+    z_prev = zc;
     code_prev = codes;
     rq = (rq + 1) % CG_RING_PLANES;
   }
-  return (double)acc;
+  v0 = UPD ? (double)rz : (double)acc;
+  v1 = UPD ? (double)rr : 0.0;
 }
 
 // RESID phase (FP64, plain loads): fold the deferred update, true residual,
@@ -635,19 +699,31 @@ __host__ __device__ constexpr size_t ring_bytes(size_t es, int planes = 3) {
 }
 // Stencil pass configurations: TMA pipeline depth in z planes, and resident
 // CTAs per SM the register budget targets.  The FP32 packed-code pass (the one
-// of served and refined solves) runs three CTAs of 256 threads per SM; the
-// passes that also read coefficient arrays need more registers; the FP64
-// pass is held to one CTA per SM by its shared memory.
+// of served and refined solves) runs three CTAs of 256 threads per SM over a
+// server batch (G = 0: many tiles, the largest first, so the SMs stay evenly
+// loaded).  On a single grid (G = 1: about two tiles per SM) it runs two CTAs
+// per SM at most (its shared memory is padded so that a third does not fit):
+// with room for three, the CTA scheduler may stack three tiles on one SM
+// while another holds one, and the stacked SM sets the pace.  (Measured on a
+// 257^3 grid: 20 solves/s against 16 with three; four stages were slower
+// than three.)  The passes that also read coefficient arrays need more
+// registers; the FP64 pass is held to one CTA per SM by its shared memory.
 #ifndef PB_STAGES_F32
 #define PB_STAGES_F32 3
 #endif
 #ifndef PB_MINB_F32
 #define PB_MINB_F32 3
 #endif
-template <typename T, int CM> struct StencilCfg {
+#ifndef PB_STAGES_GRID
+#define PB_STAGES_GRID 3
+#endif
+#ifndef PB_MINB_GRID
+#define PB_MINB_GRID 2
+#endif
+template <typename T, int CM, int G> struct StencilCfg {
   static constexpr bool lean = sizeof(T) == 4 && CM == COEF_PACKED;
-  static constexpr int stages = lean ? PB_STAGES_F32 : sizeof(T) == 4 ? 4 : 3;
-  static constexpr int minb = lean ? PB_MINB_F32 : sizeof(T) == 4 ? 2 : 1;
+  static constexpr int stages = lean ? (G ? PB_STAGES_GRID : PB_STAGES_F32) : sizeof(T) == 4 ? 4 : 3;
+  static constexpr int minb = lean ? (G ? PB_MINB_GRID : PB_MINB_F32) : sizeof(T) == 4 ? 2 : 1;
 };
 
 // Diagonal of the operator of precision T by code byte (shared memory).
@@ -679,14 +755,22 @@ __device__ __forceinline__ void leave_items(unsigned *next, unsigned *done) {
   }
 }
 
-template <typename T, int CM>
-__global__ void __launch_bounds__(NT, StencilCfg<T, CM>::minb) k_stencil(Batch B) {
-  constexpr int NS = StencilCfg<T, CM>::stages;
+// One pass of a CG iteration over the stencil tiles of every instance in the
+// batch (PASS 0: direction, p.Ap, then alpha; PASS 1: update, r.z and r.r,
+// then beta and the stop test).  Work counters 0/1 (pass 0) or 2/3 (pass 1);
+// the tile partials of both passes share st_part (pass 1 starts after pass 0
+// has finished with them).
+template <typename T, int CM, int PASS, int G>
+__device__ __forceinline__ void cg_pass(const Batch &B) {
+  constexpr int NS = StencilCfg<T, CM, G>::stages;
+  constexpr bool UPD = PASS == 1;
   extern __shared__ __align__(128) uint8_t dyn[];
   __shared__ __align__(8) uint64_t full[NS];
   __shared__ double red[2 * (NT / 32)];
   __shared__ T dtab[128];
+  __shared__ Pair<T> mtab[UPD ? 128 : 1];
   __shared__ int s_phase, s_last, s_inst, s_item;
+  unsigned *next = &B.work[UPD ? 2 : 0], *done = &B.work[UPD ? 3 : 1];
   // TMA destinations must be 16-byte aligned; align the whole region to 128:
   // the ring of p planes, then the stages.
   uint8_t *base = (uint8_t *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
@@ -699,7 +783,7 @@ __global__ void __launch_bounds__(NT, StencilCfg<T, CM>::minb) k_stencil(Batch B
   }
   pdl_launch_dependents();
   pdl_wait();
-  if (threadIdx.x == 0) s_item = take_item(&B.work[0]);
+  if (threadIdx.x == 0) s_item = take_item(next);
   __syncthreads();
   StageRing SR{0u, 0u};
   bool abort = false;
@@ -714,24 +798,28 @@ __global__ void __launch_bounds__(NT, StencilCfg<T, CM>::minb) k_stencil(Batch B
       s_phase = *(volatile int *)&Sp->phase;
       s_inst = item.inst;
     }
-    if (new_inst) build_dtab<T>(I, dtab);
+    if (new_inst) {
+      build_dtab<T>(I, dtab);
+      if (UPD) build_mtab<T>(I, mtab);
+    }
     __syncthreads();
     const int ph = s_phase;
-    if (ph == PH_INNER || ph == PH_START) {
+    if (ph == PH_INNER || (!UPD && ph == PH_START)) {
       const TileScal S = tile_scal(Sp);
-      double v0 = cg_tile<T, CM, NS>(I, S, item.tile, stages, ring, dtab, full, SR, abort), v1 = 0;
+      double v0, v1;
+      cg_tile<T, CM, NS, PASS>(I, S, item.tile, stages, ring, dtab, mtab, full, SR, abort, v0, v1);
       if (abort) {
         if (threadIdx.x == 0) atomicOr(B.error, 2);  // a pipeline wait timed out
         break;
       }
-      if (threadIdx.x == 0) s_item = take_item(&B.work[0]);
+      if (threadIdx.x == 0) s_item = take_item(next);
       block_sum2<NT>(v0, v1, red);
       if (threadIdx.x == 0) {
         double *part = B.st_part + 2 * (size_t)(I.st_base + item.tile);
         part[0] = v0;
         part[1] = v1;
         __threadfence();
-        const unsigned prev = atomicAdd(&Sp->cnt2, 1u);
+        const unsigned prev = atomicAdd(UPD ? &Sp->cnt3 : &Sp->cnt2, 1u);
         s_last = prev == (unsigned)(I.n_st - 1);
       }
       __syncthreads();
@@ -739,14 +827,26 @@ __global__ void __launch_bounds__(NT, StencilCfg<T, CM>::minb) k_stencil(Batch B
         __threadfence();
         double s0, s1;
         sum_partials<NT>(B.st_part + 2 * (size_t)I.st_base, I.n_st, s0, s1, red);
-        if (threadIdx.x == 0) fin_cg(I, Sp, s0);
+        if (threadIdx.x == 0) {
+          if (UPD) fin_update(I, Sp, s0, s1, item.inst, B.resid_pending, B.resid_list);
+          else fin_cg(I, Sp, s0);
+        }
       }
     } else if (threadIdx.x == 0) {
-      s_item = take_item(&B.work[0]);
+      s_item = take_item(next);
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) leave_items(&B.work[0], &B.work[1]);
+  if (threadIdx.x == 0) leave_items(next, done);
+}
+
+template <typename T, int CM, int G>
+__global__ void __launch_bounds__(NT, StencilCfg<T, CM, G>::minb) k_stencil(Batch B) {
+  cg_pass<T, CM, 0, G>(B);
+}
+template <typename T, int CM>
+__global__ void __launch_bounds__(NT, StencilCfg<T, CM, 0>::minb) k_update_tile(Batch B) {
+  cg_pass<T, CM, 1, 0>(B);
 }
 
 // RESID pass of the instances that asked for one (FP64, plain loads).  Its
@@ -820,6 +920,8 @@ __global__ void __launch_bounds__(NT) k_resid(Batch B) {
   }
 }
 
+// Update pass over row chunks (the form for a single grid, whose stencil pass
+// stored Ap): r = M z - alpha Ap, z = M^-1 r, partial r.z and r.r per chunk.
 template <typename T, int CM>
 __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
   constexpr int V = 16 / sizeof(T);
@@ -964,10 +1066,12 @@ cudaError_t launch_start(const Inst *inst, const int *list, int n, int *resid_pe
 // ---------------------------------------------------------------------------
 // Host side
 
-template <typename T, int CM>
+constexpr size_t SMEM_TWO_PER_SM = 80 * 1024;  // > 228 KB / 3: two CTAs per SM at most
+template <typename T, int CM, int G>
 static size_t stencil_smem() {  // ring + stages, + alignment slack
-  return 128 + ring_bytes(sizeof(T), CG_RING_PLANES) +
-         (size_t)StencilCfg<T, CM>::stages * max_stage_bytes(sizeof(T));
+  const size_t b = 128 + ring_bytes(sizeof(T), CG_RING_PLANES) +
+                   (size_t)StencilCfg<T, CM, G>::stages * max_stage_bytes(sizeof(T));
+  return G && b < SMEM_TWO_PER_SM ? SMEM_TWO_PER_SM : b;
 }
 static size_t resid_smem() { return 128 + ring_bytes(sizeof(double)); }
 
@@ -995,9 +1099,20 @@ template <typename T, int CM>
 static cudaError_t phase_impl(const Batch &B, const KernelGrid &kg, int which, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (which & 4) e = launch_pdl(k_resid<T, CM>, kg.resid_blocks, NT, resid_smem(), st, B);
-  if (e == cudaSuccess && (which & 1))
-    e = launch_pdl(k_stencil<T, CM>, kg.stencil_blocks, NT, stencil_smem<T, CM>(), st, B);
-  if (e == cudaSuccess && (which & 2)) e = launch_pdl(k_update<T, CM>, kg.update_blocks, NT_UPD, 0, st, B);
+  if (e == cudaSuccess && (which & 1)) {
+    if constexpr (StencilCfg<T, CM, 0>::lean) {
+      if (kg.single)
+        e = launch_pdl(k_stencil<T, CM, 1>, kg.stencil_blocks, NT, stencil_smem<T, CM, 1>(), st, B);
+      else
+        e = launch_pdl(k_stencil<T, CM, 0>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B);
+    } else {
+      e = launch_pdl(k_stencil<T, CM, 0>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B);
+    }
+  }
+  if (e == cudaSuccess && (which & 2))
+    e = kg.tile_update
+            ? launch_pdl(k_update_tile<T, CM>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B)
+            : launch_pdl(k_update<T, CM>, kg.update_blocks, NT_UPD, 0, st, B);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1017,29 +1132,39 @@ cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg
 }
 
 template <typename T, int CM>
-static void occ(int &s, int &u, int &r) {
-  const size_t sm = stencil_smem<T, CM>(), rm = resid_smem();
-  cudaFuncSetAttribute(k_stencil<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+static void occ(int &s, int &u, int &r, bool single) {
+  const size_t sm = stencil_smem<T, CM, 0>(), rm = resid_smem();
+  cudaFuncSetAttribute(k_stencil<T, CM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_update_tile<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_resid<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rm);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM>, NT, sm);
+  if constexpr (StencilCfg<T, CM, 0>::lean) {
+    const size_t sm1 = stencil_smem<T, CM, 1>();
+    cudaFuncSetAttribute(k_stencil<T, CM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (single) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM, 1>, NT, sm1);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM, 0>, NT, sm);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM, 0>, NT, sm);
+  }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&u, k_update<T, CM>, NT_UPD, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_resid<T, CM>, NT, rm);
 }
 
-KernelGrid kernel_grid(int mode, int coef, int num_sms) {
+KernelGrid kernel_grid(int mode, int coef, int num_sms, bool single) {
   int s = 1, u = 1, r = 1;
   if (mode == MODE_F64) {
-    if (coef == COEF_F64) occ<double, COEF_F64>(s, u, r);
-    else occ<double, COEF_PACKED>(s, u, r);
-  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u, r);
-  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u, r);
-  else occ<float, COEF_PACKED>(s, u, r);
+    if (coef == COEF_F64) occ<double, COEF_F64>(s, u, r, single);
+    else occ<double, COEF_PACKED>(s, u, r, single);
+  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u, r, single);
+  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u, r, single);
+  else occ<float, COEF_PACKED>(s, u, r, single);
   KernelGrid kg;
   kg.stencil_per_sm = s > 0 ? s : 1;
   kg.update_per_sm = u > 0 ? u : 1;
   kg.stencil_blocks = num_sms * kg.stencil_per_sm;
   kg.update_blocks = num_sms * kg.update_per_sm;
   kg.resid_blocks = num_sms * (r > 0 ? r : 1);
+  kg.tile_update = 0;
+  kg.single = single ? 1 : 0;
   return kg;
 }
 

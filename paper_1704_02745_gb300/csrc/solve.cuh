@@ -8,6 +8,11 @@ namespace pb {
 struct KernelGrid {  // persistent grid sizes of the phase kernels
   int stencil_blocks, update_blocks, resid_blocks;
   int stencil_per_sm, update_per_sm;  // resident CTAs per SM
+  int tile_update;  // 1: the update pass runs over the stencil tiles and forms Ap
+                    // again (k_update_tile; the stencil pass stores no Ap, Inst.ap
+                    // is NULL); 0: over row chunks, reading the stored Ap (k_update)
+  int single;       // 1: launches over one grid (the lean stencil pass then runs its
+                    // single-grid configuration)
 };
 
 // Shared-memory layout of one TMA stage of the stencil pass for a W x H tile
@@ -15,7 +20,7 @@ struct KernelGrid {  // persistent grid sizes of the phase kernels
 // NV columns left of the tile (16-byte aligned for FP32 and FP64), the code box
 // cw x (H + 2) bytes, the x box W x H; every box 128-byte aligned.
 struct StageLayout {
-  int rw, cw, rows, off_p, off_c, off_x, stage_bytes, tma_bytes;
+  int rw, cw, rows, off_p, off_c, off_x, stage_bytes, tma_bytes, tma_bytes_upd;
 };
 inline StageLayout stage_layout(int W, int H, int es) {
   StageLayout L;
@@ -28,13 +33,14 @@ inline StageLayout stage_layout(int W, int H, int es) {
   L.off_x = L.off_c + round_up(cbytes, 128);
   L.stage_bytes = L.off_x + round_up(xbytes, 128);
   L.tma_bytes = 2 * rbytes + cbytes + xbytes;
+  L.tma_bytes_upd = rbytes + cbytes + xbytes;  // update pass: p, codes, z centre
   return L;
 }
 // Largest stage over every tile the planner may choose.
 inline int max_stage_bytes(int es) {
   int m = 0;
   for (int W = NV; W <= WMAX; W += NV)
-    for (int H = 1; H <= HMAX && W * H <= NV * NT; H++) {
+    for (int H = 1; H <= HMAX && W * H <= TILE_NODES; H++) {
       const int b = stage_layout(W, H, es).stage_bytes;
       m = b > m ? b : m;
     }
@@ -44,7 +50,7 @@ inline int max_stage_bytes(int es) {
 constexpr int max_ring_cells() {
   int m = 0;
   for (int W = NV; W <= WMAX; W += NV)
-    for (int H = 1; H <= HMAX && W * H <= NV * NT; H++) {
+    for (int H = 1; H <= HMAX && W * H <= TILE_NODES; H++) {
       const int c = (W + 2 * NV) * (H + 2);
       m = c > m ? c : m;
     }
@@ -58,7 +64,7 @@ cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg
 // (launched in that order).
 cudaError_t launch_phase(const Batch &B, int mode, int coef, const KernelGrid &kg, int which,
                          cudaStream_t st);
-KernelGrid kernel_grid(int mode, int coef, int num_sms);
+KernelGrid kernel_grid(int mode, int coef, int num_sms, bool single);
 // Start solves on the listed instances from their device-side setup state
 // (each one that has work asks for a residual pass: appended to resid_list,
 // counted in *resid_pending).
