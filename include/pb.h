@@ -266,8 +266,19 @@ typedef struct {
     int n_atoms;
     const double *xyz, *q, *radius; /* HOST arrays, copied by pb_batch_submit */
     double *phi_out;         /* optional HOST buffer of nx*ny*nz doubles that receives phi;
-                                borrowed until pb_batch_poll returns the result */
+                                borrowed until pb_batch_poll returns the result.  Page-
+                                locked memory (pb_pinned_alloc, cudaHostAlloc) takes the
+                                device's copy directly, beside the next solves; pageable
+                                memory is filled from a pinned staging copy by the
+                                server's worker thread */
 } pb_request;
+
+/* Page-locked host memory for phi_out buffers (cudaHostAlloc; the paper has
+ * no counterpart).  pb_pinned_alloc: *out = bytes of page-locked memory,
+ * PB_ERR_OOM if none is left.  pb_pinned_free: releases a pointer that
+ * pb_pinned_alloc returned (NULL: no-op). */
+pb_status pb_pinned_alloc(size_t bytes, void **out);
+pb_status pb_pinned_free(void *p);
 
 typedef struct {
     int status;              /* pb_status of the request */

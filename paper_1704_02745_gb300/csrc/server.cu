@@ -120,6 +120,7 @@ struct Request {
   pb_grid_desc desc;
   std::vector<double> xyz, q, r;
   double *phi_out;
+  bool phi_pinned = false;  // phi_out is page-locked: the device copies into it directly
   std::chrono::steady_clock::time_point t_submit;
   size_t bytes;
 };
@@ -144,7 +145,7 @@ struct Finishing {
   Scal S;
   bool warm = false;
   double *energy = nullptr;  // pinned
-  double *phi = nullptr;     // pinned, n doubles (phi requested)
+  double *phi = nullptr;     // pinned staging, n doubles (phi requested into pageable memory)
   size_t n = 0;
   bool zero_phi = false;     // phi requested and the solution is 0 (b = 0)
 };
@@ -160,7 +161,11 @@ struct Stage {
   double *energy = nullptr;
   double *phi = nullptr;
   size_t cap_phi = 0;
+  double *d_energy = nullptr;      // device: the energies of the round's finished solves
+  double *d_dense = nullptr;       // device: their phi, unpacked (requested ones)
+  size_t cap_dense = 0;
   cudaEvent_t ev_graph = nullptr;  // after the graph and the scalar copy
+  cudaEvent_t ev_kern = nullptr;   // after the unpack and energy kernels
   cudaEvent_t ev_done = nullptr;   // after the energy (and phi) copies
 };
 
@@ -194,8 +199,7 @@ struct pb_server {
   Item *d_st = nullptr;
   double *d_st_part = nullptr, *d_rs_part = nullptr;
   size_t cap_st = 0, cap_rs = 0;
-  double *d_dense = nullptr;
-  size_t cap_dense = 0;
+  cudaStream_t copy_stream = nullptr;  // result copies, beside the next round's graph
   cudaGraphExec_t graph = nullptr;
   int ticks = 8;
   Stage stage[2];
@@ -490,27 +494,41 @@ bool run_graph(pb_server *s, bool stale) {
   return true;
 }
 
-// Queue, behind the running graph, the energy (and phi) of the solves that
-// finished in the previous round's graph, and free their slots.
+// Queue the energy (and phi) of the solves that finished in the previous
+// round's graph, and free their slots: the unpack and energy kernels run on
+// the compute stream behind the running graph; the device-to-host copies run
+// on the copy stream, beside the next round's graph.  Phi goes straight into
+// page-locked caller memory, else through the round's pinned staging.
 // snap: the scalars the previous round's graph left; sg: this round's
 // staging set (idle: its last copies were waited for).
 bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector<int> &fin,
                     std::vector<Finishing> &out) {
-  size_t phi_total = 0;
-  for (int j : fin)
-    if (s->slots[j].req.phi_out) phi_total += (size_t)s->slots[j].g->d.nx * s->slots[j].g->d.ny * s->slots[j].g->d.nz;
-  if (phi_total > sg.cap_phi) {
+  size_t dense_total = 0, stage_total = 0;
+  for (int j : fin) {
+    const Slot &sl = s->slots[j];
+    if (!sl.req.phi_out) continue;
+    const size_t n = (size_t)sl.g->d.nx * sl.g->d.ny * sl.g->d.nz;
+    dense_total += n;
+    if (!sl.req.phi_pinned) stage_total += n;
+  }
+  if (stage_total > sg.cap_phi) {
     if (sg.phi) cudaFreeHost(sg.phi);
     sg.phi = nullptr;
     sg.cap_phi = 0;
-    if (cudaMallocHost((void **)&sg.phi, phi_total * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&sg.phi, stage_total * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       s->worker_error = "out of pinned host memory for phi";
       return false;
     }
-    sg.cap_phi = phi_total;
+    sg.cap_phi = stage_total;
   }
-  size_t phi_off = 0;
+  if (!grow(&sg.d_dense, &sg.cap_dense, std::max<size_t>(dense_total, 1))) {
+    s->worker_error = "out of device memory for phi";
+    return false;
+  }
+  struct Copy { double *dst; const double *src; size_t n; };
+  std::vector<Copy> copies;
+  size_t dense_off = 0, stage_off = 0;
   for (size_t k = 0; k < fin.size(); k++) {
     Slot &sl = s->slots[fin[k]];
     pb_grid *g = sl.g;
@@ -520,39 +538,38 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
     f.warm = sl.warm;
     f.energy = sg.energy + k;
     *f.energy = 0.0;
+    const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
     if (S.status != PB_ERR_ARG && S.outer == -1 && sl.req.phi_out) {  // phi = 0, energy 0
       f.zero_phi = true;
-      f.n = (size_t)g->d.nx * g->d.ny * g->d.nz;
+      f.n = n;
     }
     if (S.status != PB_ERR_ARG && S.outer != -1) {
       const double *x = S.xbuf ? g->x64b : g->x64;
-      const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
       const double *phi = x;  // the padded solution itself, unless phi is wanted dense
       int pitch = g->g.px;
       if (sl.req.phi_out) {
-        if (!grow(&s->d_dense, &s->cap_dense, n)) {
-          s->worker_error = "out of device memory for phi";
-          return false;
-        }
-        launch_unpack(x, s->d_dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->stream);
+        double *dense = sg.d_dense + dense_off;
+        dense_off += n;
+        launch_unpack(x, dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->stream);
         s->ctx->stats->launches += 1;
-        phi = s->d_dense;
+        phi = dense;
         pitch = g->d.nx;
+        if (sl.req.phi_pinned) {
+          copies.push_back(Copy{sl.req.phi_out, dense, n});
+        } else {
+          f.phi = sg.phi + stage_off;
+          f.n = n;
+          stage_off += n;
+          copies.push_back(Copy{f.phi, dense, n});
+        }
+        s->ctx->stats->d2h += n * sizeof(double);
       }
       launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, pitch, g->d.periodic, g->d.h,
                     g->d.origin[0], g->d.origin[1], g->d.origin[2], phi,
-                    g->scratch + SCR_ENERGY_PART, g->scratch + SCR_ENERGY, s->stream);
-      cudaMemcpyAsync(f.energy, g->scratch + SCR_ENERGY, sizeof(double), cudaMemcpyDeviceToHost,
-                      s->stream);
+                    g->scratch + SCR_ENERGY_PART, sg.d_energy + k, s->stream);
       s->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;
-      s->ctx->stats->d2h += sizeof(double);
-      if (sl.req.phi_out) {
-        f.phi = sg.phi + phi_off;
-        f.n = n;
-        phi_off += n;
-        cudaMemcpyAsync(f.phi, s->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-        s->ctx->stats->d2h += n * sizeof(double);
-      }
+    } else {
+      cudaMemsetAsync(sg.d_energy + k, 0, sizeof(double), s->stream);
     }
     f.req = std::move(sl.req);
     out.push_back(std::move(f));
@@ -563,7 +580,15 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
     sl.solved_at = sl.last_used;
     sl.req = Request();
   }
-  return cuda_ok(cudaEventRecord(sg.ev_done, s->stream), s, "event");
+  if (!cuda_ok(cudaEventRecord(sg.ev_kern, s->stream), s, "event") ||
+      !cuda_ok(cudaStreamWaitEvent(s->copy_stream, sg.ev_kern, 0), s, "event"))
+    return false;
+  cudaMemcpyAsync(sg.energy, sg.d_energy, fin.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                  s->copy_stream);
+  s->ctx->stats->d2h += fin.size() * sizeof(double);
+  for (const Copy &c : copies)
+    cudaMemcpyAsync(c.dst, c.src, c.n * sizeof(double), cudaMemcpyDeviceToHost, s->copy_stream);
+  return cuda_ok(cudaEventRecord(sg.ev_done, s->copy_stream), s, "event");
 }
 
 // Hand out the results of finished solves (their copies have landed).
@@ -745,6 +770,7 @@ void worker_main(pb_server *s) {
   }
   // hand out what was queued, fail what is left
   cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->copy_stream);
   publish(s, finishing);
   std::lock_guard<std::mutex> lk(s->mu);
   for (auto &rq : s->queue) {
@@ -828,13 +854,16 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMemset(s->d_scal, 0, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
   ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
   for (Stage &sg : s->stage) {
     ok = ok && cudaMallocHost((void **)&sg.inst, MAX_SLOTS * sizeof(Inst)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sg.counts, 4 * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sg.start, MAX_SLOTS * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sg.scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sg.energy, MAX_SLOTS * sizeof(double)) == cudaSuccess;
+    ok = ok && !pb_dalloc((void **)&sg.d_energy, MAX_SLOTS * sizeof(double));
     ok = ok && cudaEventCreateWithFlags(&sg.ev_graph, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&sg.ev_kern, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&sg.ev_done, cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
@@ -843,6 +872,22 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   }
   s->worker = std::thread(worker_main, s);
   *out = s;
+  return PB_OK;
+}
+
+extern "C" pb_status pb_pinned_alloc(size_t bytes, void **out) {
+  if (!out) return pb_fail(PB_ERR_ARG, "pb_pinned_alloc: NULL out");
+  *out = nullptr;
+  if (cudaHostAlloc(out, bytes > 0 ? bytes : 1, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return pb_fail(PB_ERR_OOM, "pb_pinned_alloc: cudaHostAlloc failed");
+  }
+  return PB_OK;
+}
+
+extern "C" pb_status pb_pinned_free(void *p) {
+  if (p && cudaFreeHost(p) != cudaSuccess) return pb_fail(PB_ERR_CUDA, "pb_pinned_free: cudaFreeHost failed");
   return PB_OK;
 }
 
@@ -856,6 +901,7 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->parent->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
   for (int j = 0; j < (int)s->slots.size(); j++)
     if (s->slots[j].g) {
       s->slots[j].g->scal = nullptr;
@@ -864,7 +910,7 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
     }
   if (s->graph) cudaGraphExecDestroy(s->graph);
   void *ptrs[] = {s->d_scal, s->d_inst, s->d_counts, s->d_list, s->d_err, s->d_st,
-                  s->d_st_part, s->d_rs_part, s->d_rlist, s->d_dense};
+                  s->d_st_part, s->d_rs_part, s->d_rlist};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->h_scal) cudaFreeHost(s->h_scal);
@@ -872,12 +918,16 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
     void *hp[] = {sg.inst, sg.items, sg.counts, sg.start, sg.scal, sg.energy, sg.phi};
     for (void *p : hp)
       if (p) cudaFreeHost(p);
+    if (sg.d_energy) cudaFree(sg.d_energy);
+    if (sg.d_dense) cudaFree(sg.d_dense);
     if (sg.ev_graph) cudaEventDestroy(sg.ev_graph);
+    if (sg.ev_kern) cudaEventDestroy(sg.ev_kern);
     if (sg.ev_done) cudaEventDestroy(sg.ev_done);
   }
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ctx) {
     if (s->ctx->host_scal) cudaFreeHost(s->ctx->host_scal);
     delete s->ctx;
@@ -901,6 +951,13 @@ extern "C" pb_status pb_batch_submit(pb_server *s, const pb_request *req, uint64
   rq.q.assign(req->q, req->q + req->n_atoms);
   rq.r.assign(req->radius, req->radius + req->n_atoms);
   rq.phi_out = req->phi_out;
+  if (rq.phi_out) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, rq.phi_out) == cudaSuccess)
+      rq.phi_pinned = pa.type == cudaMemoryTypeHost;
+    else
+      cudaGetLastError();
+  }
   rq.t_submit = std::chrono::steady_clock::now();
   rq.bytes = pb_grid_bytes(&rq.desc, s->opts.precision);
   if (rq.bytes > s->budget) return pb_fail(PB_ERR_ARG, "request larger than the memory budget");

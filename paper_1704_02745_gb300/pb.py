@@ -143,6 +143,10 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_uint64)]
     lib.pb_energy_noalloc.argtypes = [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P, _P, _P]
+    lib.pb_pinned_alloc.restype = ctypes.c_int
+    lib.pb_pinned_alloc.argtypes = [ctypes.c_size_t, ctypes.POINTER(_P)]
+    lib.pb_pinned_free.restype = ctypes.c_int
+    lib.pb_pinned_free.argtypes = [_P]
     lib.pb_server_profile_begin.argtypes = [_P]
     lib.pb_server_profile_end.argtypes = [_P, ctypes.POINTER(KernelProfile)]
     lib.pb_plan_admission.restype = ctypes.c_int
@@ -430,6 +434,60 @@ def pb_plan_admission(budget: int, slots, reqs):
     return admit[:nr].tolist(), evict[:ns].tolist()
 
 
+class _PinnedBlock:
+    """One pb_pinned_alloc block; back to its pool when no array views it."""
+
+    def __init__(self, pool, nbytes: int, ptr: int):
+        self.pool, self.nbytes, self.ptr = pool, nbytes, ptr
+
+    def __del__(self):
+        self.pool._release(self.nbytes, self.ptr)
+
+
+class PinnedPool:
+    """Page-locked float64 arrays for phi_out buffers (the server's device
+    copies land in them directly).  Blocks are reused by size: allocating
+    page-locked memory costs far more than a copy into it."""
+
+    def __init__(self):
+        self._free = {}
+        self._closed = False
+
+    def empty(self, shape) -> np.ndarray:
+        n = int(np.prod(shape))
+        nbytes = max(8 * n, 8)
+        ptrs = self._free.get(nbytes)
+        if ptrs:
+            ptr = ptrs.pop()
+        else:
+            p = _P()
+            _check(load().pb_pinned_alloc(nbytes, ctypes.byref(p)))
+            ptr = p.value
+        buf = (ctypes.c_char * nbytes).from_address(ptr)
+        buf._block = _PinnedBlock(self, nbytes, ptr)
+        return np.frombuffer(buf, dtype=np.float64, count=n).reshape(shape)
+
+    def _release(self, nbytes: int, ptr: int):
+        if self._closed or _lib is None:
+            return
+        self._free.setdefault(nbytes, []).append(ptr)
+
+    def trim(self):
+        """Free the blocks no array views."""
+        for ptrs in self._free.values():
+            for ptr in ptrs:
+                load().pb_pinned_free(_P(ptr))
+        self._free.clear()
+
+
+_pinned_pool = PinnedPool()
+
+
+def pinned_empty(shape) -> np.ndarray:
+    """An uninitialised float64 array in page-locked host memory (pooled)."""
+    return _pinned_pool.empty(shape)
+
+
 class Server:
     """pb_server_create / pb_server_destroy around submit and poll."""
 
@@ -441,10 +499,12 @@ class Server:
 
     def submit(self, trajectory_id: int, spec, atoms, want_phi: bool = False, phi_out=None) -> int:
         """phi_out: a C-contiguous float64 host array of spec.shape that receives
-        phi (held until the poll that returns it); want_phi allocates one."""
+        phi (held until the poll that returns it; page-locked memory, as from
+        pinned_empty, takes the device's copy directly); want_phi allocates a
+        page-locked one."""
         out = phi_out
         if out is None and want_phi:
-            out = np.empty(spec.shape, dtype=np.float64)
+            out = pinned_empty(tuple(spec.shape))
         if out is not None and (out.dtype != np.float64 or out.shape != tuple(spec.shape)
                                 or not out.flags.c_contiguous):
             raise ValueError("phi_out must be a C-contiguous float64 array of the grid's shape")

@@ -169,3 +169,27 @@ def test_zero_charge_request(pbm, ctx):
     assert r.status == 0 and r.energy == 0.0 and r.info.iterations == 0
     assert not phi.any()
     assert ok.status == 0 and np.abs(phi2).max() > 0
+
+
+def test_phi_into_pageable_and_pinned_memory(pbm, ctx):
+    """phi_out in pageable memory (pinned staging, host copy) and in page-locked
+    memory (direct device copy on the copy stream) receive the same phi, bit
+    for bit, whichever finishes in which round."""
+    probs = mixed_requests(6, seed=21)
+    with pbm.Server(ctx, 8 * GB, warm_start=False) as srv:
+        outs, tickets = [], []
+        for i, p in enumerate(probs):
+            for pinned in (False, True):
+                out = pbm.pinned_empty(tuple(p.grid.shape)) if pinned else \
+                    np.empty(p.grid.shape, dtype=np.float64)
+                out.fill(np.nan)
+                tickets.append(srv.submit(2 * i + int(pinned), p.grid, p.atoms, phi_out=out))
+                outs.append(out)
+        res = [srv.poll(t, 60000) for t in tickets]
+    for i in range(len(probs)):
+        (r0, phi0), (r1, phi1) = res[2 * i], res[2 * i + 1]
+        assert r0.status == 0 and r1.status == 0
+        assert phi0 is outs[2 * i] and phi1 is outs[2 * i + 1]
+        assert np.isfinite(phi0).all()
+        assert np.array_equal(phi0, phi1)
+        assert r0.energy == r1.energy
