@@ -73,7 +73,9 @@ def bytes_per_node(coef):
     return {"stencil": 4 + 4 + 4 + 3 * c + 4 + 4 + 4 + 4, "update": 4 + 4 + 4 + 4}
 # DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
 # profiles/ (None until a capture of the current kernel exists).
-NCU_TRAFFIC_PER_NODE = {"stencil_batch": None, "stencil_grid": None}
+NCU_TRAFFIC_PER_NODE = {"stencil_batch": None,
+                        # k_stencil<float, packed, single grid> on 257^3: 406.3 MB / 16,974,593
+                        "stencil_grid": 406.346e6 / 16974593}
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
 
 
@@ -579,7 +581,7 @@ def run_ours(args):
                                      "kernel profile)" if args.precond == "gmg" else "the timed solver"),
                      "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
                      "peak_kind": peak_kind,
-                     "traffic": None if trf is None or spec.coef != "packed" else trf * n_nodes,
+                     "traffic": None if trf is None or spec.coef != "packed" or spec.periodic else trf * n_nodes,
                      "bytes_per_node": bpn["stencil"], "launch_ms": t_st * 1e3,
                      "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
                                      "bytes_per_node": bpn["update"],
