@@ -841,7 +841,12 @@ def run_batch(args):
     st0 = ctx.stats()
     clocks = ClockSampler(local)
     clocks.start()
+    if args.profile_range:
+        torch.cuda.profiler.start()
     total, lats, res = serve_steps(srv, [reqs] * args.steps)
+    if args.profile_range:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     clk = clocks.stop()
     st1 = ctx.stats()
     bad = [r.status for r in res if r.status != 0]

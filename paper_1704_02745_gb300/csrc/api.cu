@@ -576,6 +576,9 @@ pb_status pb_make_inst(const pb_grid *g, const pb_solve_opts *o, int mode, int c
   I.off_x = L.off_x;
   I.tma_bytes = L.tma_bytes;
   I.tma_bytes_upd = L.tma_bytes_upd;
+  I.stage_bytes_upd = L.stage_bytes_upd;
+  I.off_c_upd = L.off_c_upd;
+  I.off_x_upd = L.off_x_upd;
   if (!o) return PB_OK;  // operator application needs no descriptors
   const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;

@@ -81,6 +81,7 @@ struct alignas(64) Inst {
   int cw;                             // width of the code box (bytes, multiple of 16)
   int stage_bytes, off_p, off_c, off_x, tma_bytes;  // TMA stage layout and bytes per stage
   int tma_bytes_upd;                  // ... per stage of the update pass (no second halo box)
+  int stage_bytes_upd, off_c_upd, off_x_upd;  // its stage layout: p box, codes, z centre
   int rows_per_chunk;                 // update-pass chunk
   uint32_t vx_magic;                  // ceil(2^32 / vectors per row), for row = f*magic >> 32
   int nx, ny, nz, px;

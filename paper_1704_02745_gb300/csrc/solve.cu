@@ -81,7 +81,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 // Wait for phase `parity` of a barrier, giving up after ~1 s of clock.
 constexpr long long WAIT_CYCLES = 2000000000LL;
-constexpr int CG_RING_PLANES = 4;  // p planes with halo held by a CG stencil pass
+constexpr int CG_RING_PLANES = 3;  // p planes with halo held by a CG stencil pass
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
@@ -239,7 +239,8 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
   const int ring_plane = RGW * (H + 2);
   // descriptor fields used in the plane loop, held in registers (the asm
   // statements of the pipeline clobber memory, which would force reloads)
-  const uint32_t stage_bytes = I.stage_bytes, off_p = I.off_p, off_c = I.off_c, off_x = I.off_x;
+  const uint32_t stage_bytes = UPD ? I.stage_bytes_upd : I.stage_bytes, off_p = I.off_p,
+                 off_c = UPD ? I.off_c_upd : I.off_c, off_x = UPD ? I.off_x_upd : I.off_x;
   const uint32_t tma_bytes = UPD ? I.tma_bytes_upd : I.tma_bytes;
   const int cx0 = ((G.x0 - 1) >> 4) << 4;  // code box start: 16-byte aligned, <= x0 - 1
   const int Q = (G.z1 - G.z0) + 2;         // planes z0-1 .. z1
@@ -302,12 +303,19 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
   const int hr = (Hh.hy + 1) * RW + NV + Hh.hx;
   const int hg = (Hh.hy + 1) * RGW + NV + Hh.hx;
 
+  // loop-invariant tests, hoisted
+  const bool wrap_lanes = per && G.in_tile && (G.x0 + G.tx + NV > I.nx || G.y0 + G.ty >= I.ny);
+  const int hgx = G.x0 + Hh.hx, hgy = G.y0 + Hh.hy;
+  const bool halo_wrap = per && Hh.role && (hgx < 0 || hgx >= I.nx || hgy < 0 || hgy >= I.ny);
+  const bool full_group = G.vmask == (1u << NV) - 1u;
+  const T m_unit = (T)1;
+
   uint32_t code_prev = 0;
   T acc = 0, rz = 0, rr = 0;
-  Vec<T> z_prev = {};  // pass 1: z of the plane whose Ap is formed next
-  // ring slot of plane q; planes q-1 and q-2 sit in the two slots before it.
-  // A thread writes slot q while a slower one, still in its pass q-1, may
-  // read the slots of q-2 and q-3: hence four slots with one barrier a plane.
+  Vec<T> z_prev = {};          // pass 1: z of the plane whose Ap is formed next
+  Vec<T> pc = {}, pm = {};     // this group's p on planes q-1 and q-2
+  // ring slot of plane q; a thread writes slot q while a slower one, still
+  // in its pass q-1, may read slot q-2: three slots, one barrier a plane.
   int rq = 0;
   uint32_t st_issue = SR.st;
   for (int u = 0; u < min(NS, Q); ++u) st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
@@ -322,7 +330,7 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
     const uint8_t *sc = sb + off_c;
     const T *sx = (const T *)(sb + off_x);
     T *rg = ring + rq * ring_plane;
-    const int rq1 = (rq + CG_RING_PLANES - 1) % CG_RING_PLANES, rq2 = (rq + CG_RING_PLANES - 2) % CG_RING_PLANES;
+    const int rq1 = rq == 0 ? CG_RING_PLANES - 1 : rq - 1;
     const int z = G.z0 - 1 + q;
     Vec<T> pn = {}, zc = {};
     uint32_t codes = 0;
@@ -337,7 +345,7 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
 #pragma unroll
         for (int u = 0; u < NV; u++) pn.v[u] += beta * po.v[u];
       }
-      if (per && (G.x0 + G.tx + NV > I.nx || G.y0 + G.ty >= I.ny)) {
+      if (wrap_lanes) {
 #pragma unroll
         for (int u = 0; u < NV; u++)
           if (G.x0 + G.tx + u >= I.nx || G.y0 + G.ty >= I.ny)
@@ -358,9 +366,8 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
     }
     if (!UPD && q >= 1 && q < Q - 1) x += plane;
     if (ok && Hh.role) {
-      const int gx = G.x0 + Hh.hx, gy = G.y0 + Hh.hy;
-      if (per && (gx < 0 || gx >= I.nx || gy < 0 || gy >= I.ny))
-        rg[hg] = wrapped_p(gx < 0 ? gx + I.nx : gx, gy, zwrap(z));
+      if (halo_wrap)
+        rg[hg] = wrapped_p(hgx < 0 ? hgx + I.nx : hgx, hgy, zwrap(z));
       else
         rg[hg] = UPD || first ? sz[hr] : sz[hr] + beta * sp[hr];
     }
@@ -391,11 +398,12 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
       // any valid node ends within it: pitch and group starts are multiples
       // of NV)
       if (G.vmask) {
+        // plane q-1: in-plane neighbours from the ring, z neighbours and the
+        // centre from this thread's registers
         const T *rm = ring + rq1 * ring_plane;
-        const Vec<T> pc = ldv(rm + cg), pm = ldv(ring + rq2 * ring_plane + cg);
         const Vec<T> ym = ldv(rm + cg - RGW), yp = ldv(rm + cg + RGW);
         const T xl = rm[cg - 1], xr = rm[cg + NV];
-        Vec<T> a;
+        Vec<T> a, dgs, mis;  // pass 1, packed: diag A and M^-1 by node
 #pragma unroll
         for (int u = 0; u < NV; u++) {
           const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
@@ -405,7 +413,15 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
             // whose edges all lie on one side (all but the nodes next to the
             // surface) takes a single coefficient times the neighbour sum
             const uint32_t b = (code_prev >> (8 * u)) & 0xffu, e6 = b & 63u;
-            const T dg = dtab[b & 127u];
+            T dg;
+            if (UPD) {
+              const Pair<T> t = mtab[b & 127u];
+              dg = t.d;
+              dgs.v[u] = t.d;
+              mis.v[u] = t.i;
+            } else {
+              dg = dtab[b & 127u];
+            }
             if (e6 == 0u || e6 == 63u) {
               const T s6 = ((pl + pr) + (ym.v[u] + yp.v[u])) + (pm.v[u] + pn.v[u]);
               av = dg * pc.v[u] - (e6 ? ei : eo) * s6;
@@ -429,23 +445,26 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
             s += c.ezp * pn.v[u];
             av = c.diag * pc.v[u] - s;
           }
-          if (!((G.vmask >> u) & 1u)) av = 0;  // pad columns keep Ap = 0
           a.v[u] = av;
-          if (!UPD) acc += pc.v[u] * av;
+        }
+        if (!full_group) {  // pad columns keep Ap = 0
+#pragma unroll
+          for (int u = 0; u < NV; u++)
+            if (!((G.vmask >> u) & 1u)) a.v[u] = 0;
         }
         if (UPD) {
-          // r = M z - alpha Ap, z = M^-1 r (pads: z = Ap = 0 stay 0)
+          // r = M z - alpha Ap, z = M^-1 r (pads: z = Ap = 0 stay 0); with
+          // the packed code, mtab holds {diag A, M^-1} by code byte
           Vec<T> zn;
 #pragma unroll
           for (int u = 0; u < NV; u++) {
-            T m, mi = (T)1;
+            T m, mi = m_unit;
             if (CM == COEF_PACKED) {
-              const Pair<T> t = mtab[(code_prev >> (8 * u)) & 127u];
-              m = t.d;
-              mi = t.i;
+              m = I.precond ? dgs.v[u] : m_unit;
+              mi = mis.v[u];
             } else {
               m = I.precond && ((G.vmask >> u) & 1u)
-                      ? ((const T *)I.diag)[(size_t)(z - 1) * plane + ec0 + u] : (T)1;
+                      ? ((const T *)I.diag)[(size_t)(z - 1) * plane + ec0 + u] : m_unit;
             }
             const T r = m * z_prev.v[u] - alpha * a.v[u];
             zn.v[u] = CM == COEF_PACKED ? r * mi : r / m;
@@ -453,16 +472,20 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
             rr += r * r;
           }
           stv(zout, zn);
-        } else if (per) {  // pad lanes of the ring hold wrapped values; p keeps zero pads
-          Vec<T> pst = pc;
-#pragma unroll
-          for (int u = 0; u < NV; u++)
-            if (!((G.vmask >> u) & 1u)) pst.v[u] = 0;
-          stv(pnew, pst);
         } else {
-          stv(pnew, pc);
+#pragma unroll
+          for (int u = 0; u < NV; u++) acc += pc.v[u] * a.v[u];
+          if (per && !full_group) {  // pad lanes hold wrapped values; p keeps zero pads
+            Vec<T> pst = pc;
+#pragma unroll
+            for (int u = 0; u < NV; u++)
+              if (!((G.vmask >> u) & 1u)) pst.v[u] = 0;
+            stv(pnew, pst);
+          } else {
+            stv(pnew, pc);
+          }
+          if (store_ap) stv(ap, a);
         }
-        if (store_ap) stv(ap, a);
       }
       if (UPD) {
         zout += plane;
@@ -471,9 +494,11 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
         ap += plane;
       }
     }
+    pm = pc;
+    pc = pn;
     z_prev = zc;
     code_prev = codes;
-    rq = (rq + 1) % CG_RING_PLANES;
+    rq = rq + 1 == CG_RING_PLANES ? 0 : rq + 1;
   }
   v0 = UPD ? (double)rz : (double)acc;
   v1 = UPD ? (double)rr : 0.0;
@@ -725,6 +750,18 @@ template <typename T, int CM, int G> struct StencilCfg {
   static constexpr int stages = lean ? (G ? PB_STAGES_GRID : PB_STAGES_F32) : sizeof(T) == 4 ? 4 : 3;
   static constexpr int minb = lean ? (G ? PB_MINB_GRID : PB_MINB_F32) : sizeof(T) == 4 ? 2 : 1;
 };
+// The tile update pass (server batches): a smaller stage (one halo box).
+#ifndef PB_STAGES_UPD
+#define PB_STAGES_UPD 3
+#endif
+#ifndef PB_MINB_UPD
+#define PB_MINB_UPD 3
+#endif
+template <typename T, int CM> struct UpdCfg {
+  static constexpr bool lean = sizeof(T) == 4 && CM == COEF_PACKED;
+  static constexpr int stages = lean ? PB_STAGES_UPD : StencilCfg<T, CM, 0>::stages;
+  static constexpr int minb = lean ? PB_MINB_UPD : StencilCfg<T, CM, 0>::minb;
+};
 
 // Diagonal of the operator of precision T by code byte (shared memory).
 template <typename T>
@@ -732,13 +769,14 @@ __device__ __forceinline__ void build_dtab(const Inst &I, T *dtab) {
   if (threadIdx.x < 128) dtab[threadIdx.x] = tab_d<T>(I, dtab_index(threadIdx.x));
 }
 
-// Jacobi preconditioner M by code byte: {M, M^-1} = {diag, 1/diag}, or {1, 1}
-// without preconditioner (shared memory).
+// The operator's diagonal and the Jacobi preconditioner's inverse by code
+// byte: {diag A, M^-1} = {diag, 1/diag}, or {diag, 1} without preconditioner
+// (then M = 1).  Shared memory.
 template <typename T>
 __device__ __forceinline__ void build_mtab(const Inst &I, Pair<T> *mtab) {
   if (threadIdx.x < 128) {
     const int k = dtab_index(threadIdx.x);
-    mtab[threadIdx.x].d = I.precond ? tab_d<T>(I, k) : (T)1;
+    mtab[threadIdx.x].d = tab_d<T>(I, k);
     mtab[threadIdx.x].i = I.precond ? tab_i<T>(I, k) : (T)1;
   }
 }
@@ -762,7 +800,7 @@ __device__ __forceinline__ void leave_items(unsigned *next, unsigned *done) {
 // has finished with them).
 template <typename T, int CM, int PASS, int G>
 __device__ __forceinline__ void cg_pass(const Batch &B) {
-  constexpr int NS = StencilCfg<T, CM, G>::stages;
+  constexpr int NS = PASS == 1 ? UpdCfg<T, CM>::stages : StencilCfg<T, CM, G>::stages;
   constexpr bool UPD = PASS == 1;
   extern __shared__ __align__(128) uint8_t dyn[];
   __shared__ __align__(8) uint64_t full[NS];
@@ -845,7 +883,7 @@ __global__ void __launch_bounds__(NT, StencilCfg<T, CM, G>::minb) k_stencil(Batc
   cg_pass<T, CM, 0, G>(B);
 }
 template <typename T, int CM>
-__global__ void __launch_bounds__(NT, StencilCfg<T, CM, 0>::minb) k_update_tile(Batch B) {
+__global__ void __launch_bounds__(NT, UpdCfg<T, CM>::minb) k_update_tile(Batch B) {
   cg_pass<T, CM, 1, 0>(B);
 }
 
@@ -986,7 +1024,7 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
             T m, mi = (T)1;
             if (CM == COEF_PACKED) {
               const Pair<T> t = mtab[(codes[k] >> (8 * u)) & 127u];
-              m = t.d;
+              m = I.precond ? t.d : (T)1;
               mi = t.i;
             } else {
               m = I.precond ? ((const T *)I.diag)[(size_t)row0 * px + e[k] + u] : (T)1;
@@ -1066,12 +1104,20 @@ cudaError_t launch_start(const Inst *inst, const int *list, int n, int *resid_pe
 // ---------------------------------------------------------------------------
 // Host side
 
-constexpr size_t SMEM_TWO_PER_SM = 80 * 1024;  // > 228 KB / 3: two CTAs per SM at most
+#ifndef PB_GRID_SMEM_MIN
+#define PB_GRID_SMEM_MIN (80 * 1024)
+#endif
+constexpr size_t SMEM_TWO_PER_SM = PB_GRID_SMEM_MIN;  // > 228 KB / 3: two CTAs per SM at most
 template <typename T, int CM, int G>
 static size_t stencil_smem() {  // ring + stages, + alignment slack
   const size_t b = 128 + ring_bytes(sizeof(T), CG_RING_PLANES) +
                    (size_t)StencilCfg<T, CM, G>::stages * max_stage_bytes(sizeof(T));
   return G && b < SMEM_TWO_PER_SM ? SMEM_TWO_PER_SM : b;
+}
+template <typename T, int CM>
+static size_t update_smem() {  // ring + compact stages of the tile update pass
+  return 128 + ring_bytes(sizeof(T), CG_RING_PLANES) +
+         (size_t)UpdCfg<T, CM>::stages * max_stage_bytes_upd(sizeof(T));
 }
 static size_t resid_smem() { return 128 + ring_bytes(sizeof(double)); }
 
@@ -1111,7 +1157,7 @@ static cudaError_t phase_impl(const Batch &B, const KernelGrid &kg, int which, c
   }
   if (e == cudaSuccess && (which & 2))
     e = kg.tile_update
-            ? launch_pdl(k_update_tile<T, CM>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B)
+            ? launch_pdl(k_update_tile<T, CM>, kg.update_tile_blocks, NT, update_smem<T, CM>(), st, B)
             : launch_pdl(k_update<T, CM>, kg.update_blocks, NT_UPD, 0, st, B);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1132,10 +1178,12 @@ cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg
 }
 
 template <typename T, int CM>
-static void occ(int &s, int &u, int &r, bool single) {
+static void occ(int &s, int &u, int &r, int &ut, bool single) {
   const size_t sm = stencil_smem<T, CM, 0>(), rm = resid_smem();
   cudaFuncSetAttribute(k_stencil<T, CM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_update_tile<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_update_tile<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)update_smem<T, CM>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ut, k_update_tile<T, CM>, NT, update_smem<T, CM>());
   cudaFuncSetAttribute(k_resid<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rm);
   if constexpr (StencilCfg<T, CM, 0>::lean) {
     const size_t sm1 = stencil_smem<T, CM, 1>();
@@ -1150,19 +1198,20 @@ static void occ(int &s, int &u, int &r, bool single) {
 }
 
 KernelGrid kernel_grid(int mode, int coef, int num_sms, bool single) {
-  int s = 1, u = 1, r = 1;
+  int s = 1, u = 1, r = 1, ut = 1;
   if (mode == MODE_F64) {
-    if (coef == COEF_F64) occ<double, COEF_F64>(s, u, r, single);
-    else occ<double, COEF_PACKED>(s, u, r, single);
-  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u, r, single);
-  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u, r, single);
-  else occ<float, COEF_PACKED>(s, u, r, single);
+    if (coef == COEF_F64) occ<double, COEF_F64>(s, u, r, ut, single);
+    else occ<double, COEF_PACKED>(s, u, r, ut, single);
+  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u, r, ut, single);
+  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u, r, ut, single);
+  else occ<float, COEF_PACKED>(s, u, r, ut, single);
   KernelGrid kg;
   kg.stencil_per_sm = s > 0 ? s : 1;
   kg.update_per_sm = u > 0 ? u : 1;
   kg.stencil_blocks = num_sms * kg.stencil_per_sm;
   kg.update_blocks = num_sms * kg.update_per_sm;
   kg.resid_blocks = num_sms * (r > 0 ? r : 1);
+  kg.update_tile_blocks = num_sms * (ut > 0 ? ut : 1);
   kg.tile_update = 0;
   kg.single = single ? 1 : 0;
   return kg;

@@ -6,7 +6,7 @@
 namespace pb {
 
 struct KernelGrid {  // persistent grid sizes of the phase kernels
-  int stencil_blocks, update_blocks, resid_blocks;
+  int stencil_blocks, update_blocks, resid_blocks, update_tile_blocks;
   int stencil_per_sm, update_per_sm;  // resident CTAs per SM
   int tile_update;  // 1: the update pass runs over the stencil tiles and forms Ap
                     // again (k_update_tile; the stencil pass stores no Ap, Inst.ap
@@ -21,6 +21,7 @@ struct KernelGrid {  // persistent grid sizes of the phase kernels
 // cw x (H + 2) bytes, the x box W x H; every box 128-byte aligned.
 struct StageLayout {
   int rw, cw, rows, off_p, off_c, off_x, stage_bytes, tma_bytes, tma_bytes_upd;
+  int off_c_upd, off_x_upd, stage_bytes_upd;  // update pass: p box, codes, z centre
 };
 inline StageLayout stage_layout(int W, int H, int es) {
   StageLayout L;
@@ -34,6 +35,9 @@ inline StageLayout stage_layout(int W, int H, int es) {
   L.stage_bytes = L.off_x + round_up(xbytes, 128);
   L.tma_bytes = 2 * rbytes + cbytes + xbytes;
   L.tma_bytes_upd = rbytes + cbytes + xbytes;  // update pass: p, codes, z centre
+  L.off_c_upd = round_up(rbytes, 128);
+  L.off_x_upd = L.off_c_upd + round_up(cbytes, 128);
+  L.stage_bytes_upd = L.off_x_upd + round_up(xbytes, 128);
   return L;
 }
 // Largest stage over every tile the planner may choose.
@@ -42,6 +46,15 @@ inline int max_stage_bytes(int es) {
   for (int W = NV; W <= WMAX; W += NV)
     for (int H = 1; H <= HMAX && W * H <= TILE_NODES; H++) {
       const int b = stage_layout(W, H, es).stage_bytes;
+      m = b > m ? b : m;
+    }
+  return m;
+}
+inline int max_stage_bytes_upd(int es) {
+  int m = 0;
+  for (int W = NV; W <= WMAX; W += NV)
+    for (int H = 1; H <= HMAX && W * H <= TILE_NODES; H++) {
+      const int b = stage_layout(W, H, es).stage_bytes_upd;
       m = b > m ? b : m;
     }
   return m;
