@@ -321,6 +321,10 @@ def run_serving(args):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     iters = [r.info.iterations for r in res]
+    # grid nodes x CG iterations of the timed steps: each iteration is one
+    # stencil pass over the grid (the denominator of the ncu DRAM traffic)
+    node_passes = int(sum(int(np.prod(g.shape)) * r.info.iterations
+                          for (_, g, _), r in zip([x for b in batches for x in b], res)))
     bad = [r.status for r in res if r.status != 0]
     if bad:
         raise RuntimeError(f"served requests failed: {bad[:5]}")
@@ -426,6 +430,7 @@ def run_serving(args):
                        "note": "steady state: 64 requests per step, the next step queued while "
                                "this one completes; submit -> result"},
         "iterations_mean": float(np.mean(iters)),
+        "stencil_node_passes": node_passes,
         "fp64_plain": {"value": plain_rate, "unit": "solves/s",
                        "latency_ms": {"p50": pct([1e3 * x for x in p_lat], 50),
                                       "p99": pct([1e3 * x for x in p_lat], 99)},

@@ -201,7 +201,10 @@ struct pb_server {
   size_t cap_st = 0, cap_rs = 0;
   cudaStream_t copy_stream = nullptr;  // result copies, beside the next round's graph
   cudaGraphExec_t graph = nullptr;
-  int ticks = 8;
+#ifndef PB_SERVER_TICKS
+#define PB_SERVER_TICKS 8
+#endif
+  int ticks = PB_SERVER_TICKS;
   Stage stage[2];
   uint64_t round = 0;
   // kernel measurement (pb_server_profile_begin/end)
