@@ -73,9 +73,11 @@ def bytes_per_node(coef):
     return {"stencil": 4 + 4 + 4 + 3 * c + 4 + 4 + 4 + 4, "update": 4 + 4 + 4 + 4}
 # DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
 # profiles/ (None until a capture of the current kernel exists).
-NCU_TRAFFIC_PER_NODE = {"stencil_batch": None,
-                        # k_stencil<float, packed, single grid> on 257^3: 406.3 MB / 16,974,593
-                        "stencil_grid": 406.346e6 / 16974593}
+NCU_TRAFFIC_PER_NODE = {# k_stencil<float, packed, batch> over two timed serving steps: 1650.6 GB of
+                        # DRAM traffic / 74,205,826,462 grid-node stencil passes
+                        "stencil_batch": (1054413987328 + 596184557824) / 74205826462,
+                        # k_stencil<float, packed, single grid> on 257^3: 405.1 MB / 16,974,593
+                        "stencil_grid": 405.113e6 / 16974593}
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
 
 
@@ -231,9 +233,17 @@ def serve_batch(srv, reqs, want_phi=False):
 
 
 def prewarm_pinned(pb, batches):
-    """Page-locked phi buffers for two steps in flight, allocated once before
-    the timed region (as a client would hold them), then back in the pool."""
-    bufs = [pb.pinned_empty(tuple(g.shape)) for b in batches[:2] for _, g, _ in b]
+    """Page-locked phi buffers, allocated once before the timed region (as a
+    client would hold them), then back in the pool: for each size class,
+    three times the most any step asks for (two steps in flight, one being
+    collected)."""
+    from collections import Counter
+    need = Counter()
+    for b in batches:
+        c = Counter(pb.PinnedPool.size_class(8 * int(np.prod(g.shape))) for _, g, _ in b)
+        for k, v in c.items():
+            need[k] = max(need[k], 3 * v)
+    bufs = [pb.pinned_empty((k // 8,)) for k, v in need.items() for _ in range(v)]
     del bufs
 
 
@@ -861,7 +871,7 @@ def run_batch(args):
         t = torch.tensor([total], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total = float(t[0])
-    prewarm_pinned(pb, [reqs] * 2)
+    prewarm_pinned(pb, [reqs])
     e0 = ctx.stats()
     e2e_wall, _, _ = serve_steps(srv, [reqs] * max(1, args.steps // 2), want_phi=True)
     e1 = ctx.stats()

@@ -453,9 +453,17 @@ class PinnedPool:
         self._free = {}
         self._closed = False
 
+    @staticmethod
+    def size_class(nbytes: int) -> int:
+        """Blocks come in classes a quarter of a power of two apart, so grids
+        of nearby sizes share them (at most 25% of a block unused)."""
+        nbytes = max(int(nbytes), 4096)
+        step = 1 << max(nbytes.bit_length() - 3, 12)
+        return (nbytes + step - 1) // step * step
+
     def empty(self, shape) -> np.ndarray:
         n = int(np.prod(shape))
-        nbytes = max(8 * n, 8)
+        nbytes = self.size_class(8 * n)
         ptrs = self._free.get(nbytes)
         if ptrs:
             ptr = ptrs.pop()
