@@ -206,8 +206,8 @@ void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
 
 // (Re)run the setup kernels of a grid for the given host atoms.
 pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
-                       const double *radius, bool sync) {
-  cudaStream_t s = g->ctx->stream;
+                       const double *radius, bool sync, cudaStream_t st_in) {
+  cudaStream_t s = st_in ? st_in : g->ctx->stream;
   const pb_grid_desc *desc = &g->d;
   if (!g->scratch || n_atoms > g->atom_cap) {  // first call (also with no atoms) or growth
     if (g->xyzq) cudaFree(g->xyzq);

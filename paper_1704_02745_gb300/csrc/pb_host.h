@@ -80,8 +80,9 @@ pb_status pb_check_atoms(int n_atoms, const double *xyz, const double *q, const 
 pb_status pb_gmg_solve(pb_grid *g, const pb_solve_opts *o, double *phi, pb_solve_info *info);
 void pb_mg_release(struct pb_mg *m);
 pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_grid **out);
+// st: the stream of the setup work (NULL: the grid's context stream)
 pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
-                       const double *radius, bool sync);
+                       const double *radius, bool sync, cudaStream_t st = nullptr);
 pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks);
 
 // Layout of a grid's FP64 scratch buffer.

@@ -7,19 +7,21 @@
 //      one per trajectory, reused snapshot after snapshot, so a solve starts
 //      from the trajectory's last solution -- evicting idle grids LRU when the
 //      device-memory budget requires;
-//   2. queues the setup kernels of the admitted snapshots and the start of
-//      their solves on the device (no host round trip);
-//   3. rebuilds the batch's work list when the active set changed: stencil
-//      tiles and update chunks of every active grid, each grid's partial sums
-//      at its own offset, so its reductions are summed in a fixed order
+//   2. queues the setup kernels of the admitted snapshots on four setup
+//      streams (each after the last work on its grid only, so they run beside
+//      the running graph and beside each other), then the start of their
+//      solves on the compute stream after them (no host round trip);
+//   3. rebuilds the batch's work list when the active set changed: the
+//      stencil tiles of every active grid, largest first, each grid's partial
+//      sums at its own offset, so its reductions are summed in a fixed order
 //      whatever else runs;
 //   4. queues a captured device graph of `ticks` phase ticks over the whole
 //      batch (finished grids are skipped by their convergence mask) and a copy
 //      of all grids' scalars;
 //   5. while that graph runs, reads the scalars the previous round's graph
-//      left, queues the energy (and phi) of the solves that finished in it
-//      behind the running graph, and hands out the results queued one round
-//      earlier.
+//      left, queues the energy (and phi) of the solves that finished in it on
+//      the copy stream, beside the running graph, and hands out the results
+//      queued one round earlier.
 // Everything the host uploads comes from pinned staging in two sets, one
 // per round in flight, so no copy waits for the graph ahead of it and the
 // GPU never idles on the host between rounds.
@@ -165,7 +167,6 @@ struct Stage {
   double *d_dense = nullptr;       // device: their phi, unpacked (requested ones)
   size_t cap_dense = 0;
   cudaEvent_t ev_graph = nullptr;  // after the graph and the scalar copy
-  cudaEvent_t ev_kern = nullptr;   // after the unpack and energy kernels
   cudaEvent_t ev_done = nullptr;   // after the energy (and phi) copies
 };
 
@@ -200,6 +201,12 @@ struct pb_server {
   double *d_st_part = nullptr, *d_rs_part = nullptr;
   size_t cap_st = 0, cap_rs = 0;
   cudaStream_t copy_stream = nullptr;  // result copies, beside the next round's graph
+  // setups of admitted snapshots, several at once and beside the running graph
+  static constexpr int SETUP_STREAMS = 4;
+  cudaStream_t setup_stream[SETUP_STREAMS] = {};
+  // per slot: after the last compute-stream work on its grid (creation, or the
+  // unpack and energy of its last solve); after its setup (setup stream)
+  std::vector<cudaEvent_t> ev_idle, ev_ready;
   cudaGraphExec_t graph = nullptr;
 #ifndef PB_SERVER_TICKS
 #define PB_SERVER_TICKS 8
@@ -317,6 +324,7 @@ std::vector<int> admit(pb_server *s) {
       s->free_slots.pop_back();
       g->scal = s->d_scal + j;
       g->own_scal = false;
+      cudaEventRecord(s->ev_idle[j], s->stream);  // its workspace clears
       Slot &sl = s->slots[j];
       sl.g = g;
       sl.traj = rq.traj;
@@ -324,6 +332,10 @@ std::vector<int> admit(pb_server *s) {
       sl.has_solution = false;
     }
     Slot &sl = s->slots[j];
+    // this snapshot's setup stream waits for the last compute-stream work on
+    // its grid, which finished long before in the steady state
+    cudaStream_t sst = s->setup_stream[started.size() % pb_server::SETUP_STREAMS];
+    cudaStreamWaitEvent(sst, s->ev_idle[j], 0);
     // a new grid of a trajectory starts from the trajectory's latest solution
     // held by an idle grid of the same dims, if any (device-to-device copy)
     if (adm[i] == -1 && s->opts.warm_start && rq.traj >= 0) {
@@ -338,8 +350,10 @@ std::vector<int> admit(pb_server *s) {
       if (src >= 0) {
         const Slot &o = s->slots[src];
         const double *from = o.xbuf ? o.g->x64b : o.g->x64;
+        cudaStreamWaitEvent(sst, s->ev_idle[j], 0);
+        cudaStreamWaitEvent(sst, s->ev_idle[src], 0);
         cudaMemcpyAsync(sl.g->x64, from, sl.g->n_pad * sizeof(double), cudaMemcpyDeviceToDevice,
-                        s->stream);
+                        sst);
         cudaMemsetAsync(s->d_scal + j, 0, sizeof(Scal), s->stream);
         sl.has_solution = true;
         sl.solved_at = o.solved_at;
@@ -349,20 +363,23 @@ std::vector<int> admit(pb_server *s) {
     sl.first_round = s->round;
     sl.last_used = ++s->clock;
     sl.warm = s->opts.warm_start && sl.has_solution;
-    if (pb_run_setup(sl.g, (int)rq.q.size(), rq.xyz.data(), rq.q.data(), rq.r.data(), false)) {
+    if (pb_run_setup(sl.g, (int)rq.q.size(), rq.xyz.data(), rq.q.data(), rq.r.data(), false, sst)) {
       sl.busy = false;
       fail_request(s, rq, PB_ERR_CUDA);
       taken.push_back(rq.ticket);
       continue;
     }
     if (!sl.warm) {  // cold start: phi0 = 0 in both solution buffers
-      cudaMemsetAsync(sl.g->x64, 0, sl.g->n_pad * sizeof(double), s->stream);
-      cudaMemsetAsync(sl.g->x64b, 0, sl.g->n_pad * sizeof(double), s->stream);
+      cudaMemsetAsync(sl.g->x64, 0, sl.g->n_pad * sizeof(double), sst);
+      cudaMemsetAsync(sl.g->x64b, 0, sl.g->n_pad * sizeof(double), sst);
     }
+    cudaEventRecord(s->ev_ready[j], sst);
     sl.req = std::move(rq);
     taken.push_back(sl.req.ticket);
     started.push_back(j);
   }
+  // the start kernel and the graph come after every setup of this round
+  for (int j : started) cudaStreamWaitEvent(s->stream, s->ev_ready[j], 0);
   if (!taken.empty()) {
     std::lock_guard<std::mutex> lk(s->mu);
     std::deque<Request> rest;
@@ -498,10 +515,12 @@ bool run_graph(pb_server *s, bool stale) {
 }
 
 // Queue the energy (and phi) of the solves that finished in the previous
-// round's graph, and free their slots: the unpack and energy kernels run on
-// the compute stream behind the running graph; the device-to-host copies run
-// on the copy stream, beside the next round's graph.  Phi goes straight into
-// page-locked caller memory, else through the round's pinned staging.
+// round's graph, and free their slots.  The host has seen that graph finish,
+// and the running graph only skips these grids (their phase is DONE), so the
+// unpack and energy kernels and the device-to-host copies all run on the copy
+// stream, beside the running graph; a grid's next setup waits for its
+// kernels only (ev_idle).  Phi goes straight into page-locked caller memory,
+// else through the round's pinned staging.
 // snap: the scalars the previous round's graph left; sg: this round's
 // staging set (idle: its last copies were waited for).
 bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector<int> &fin,
@@ -553,7 +572,7 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
       if (sl.req.phi_out) {
         double *dense = sg.d_dense + dense_off;
         dense_off += n;
-        launch_unpack(x, dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->stream);
+        launch_unpack(x, dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->copy_stream);
         s->ctx->stats->launches += 1;
         phi = dense;
         pitch = g->d.nx;
@@ -569,11 +588,12 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
       }
       launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, pitch, g->d.periodic, g->d.h,
                     g->d.origin[0], g->d.origin[1], g->d.origin[2], phi,
-                    g->scratch + SCR_ENERGY_PART, sg.d_energy + k, s->stream);
+                    g->scratch + SCR_ENERGY_PART, sg.d_energy + k, s->copy_stream);
       s->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;
     } else {
-      cudaMemsetAsync(sg.d_energy + k, 0, sizeof(double), s->stream);
+      cudaMemsetAsync(sg.d_energy + k, 0, sizeof(double), s->copy_stream);
     }
+    cudaEventRecord(s->ev_idle[fin[k]], s->copy_stream);  // after its unpack and energy
     f.req = std::move(sl.req);
     out.push_back(std::move(f));
     sl.busy = false;
@@ -583,9 +603,6 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
     sl.solved_at = sl.last_used;
     sl.req = Request();
   }
-  if (!cuda_ok(cudaEventRecord(sg.ev_kern, s->stream), s, "event") ||
-      !cuda_ok(cudaStreamWaitEvent(s->copy_stream, sg.ev_kern, 0), s, "event"))
-    return false;
   cudaMemcpyAsync(sg.energy, sg.d_energy, fin.size() * sizeof(double), cudaMemcpyDeviceToHost,
                   s->copy_stream);
   s->ctx->stats->d2h += fin.size() * sizeof(double);
@@ -858,6 +875,13 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto &x : s->setup_stream)
+    ok = ok && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+  s->ev_idle.assign(MAX_SLOTS, nullptr);
+  s->ev_ready.assign(MAX_SLOTS, nullptr);
+  for (int j = 0; ok && j < MAX_SLOTS; j++)
+    ok = cudaEventCreateWithFlags(&s->ev_idle[j], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_ready[j], cudaEventDisableTiming) == cudaSuccess;
   for (Stage &sg : s->stage) {
     ok = ok && cudaMallocHost((void **)&sg.inst, MAX_SLOTS * sizeof(Inst)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sg.counts, 4 * sizeof(int)) == cudaSuccess;
@@ -866,7 +890,6 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
     ok = ok && cudaMallocHost((void **)&sg.energy, MAX_SLOTS * sizeof(double)) == cudaSuccess;
     ok = ok && !pb_dalloc((void **)&sg.d_energy, MAX_SLOTS * sizeof(double));
     ok = ok && cudaEventCreateWithFlags(&sg.ev_graph, cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&sg.ev_kern, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&sg.ev_done, cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
@@ -905,6 +928,8 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
   cudaSetDevice(s->parent->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+  for (auto x : s->setup_stream)
+    if (x) cudaStreamSynchronize(x);
   for (int j = 0; j < (int)s->slots.size(); j++)
     if (s->slots[j].g) {
       s->slots[j].g->scal = nullptr;
@@ -924,13 +949,18 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
     if (sg.d_energy) cudaFree(sg.d_energy);
     if (sg.d_dense) cudaFree(sg.d_dense);
     if (sg.ev_graph) cudaEventDestroy(sg.ev_graph);
-    if (sg.ev_kern) cudaEventDestroy(sg.ev_kern);
     if (sg.ev_done) cudaEventDestroy(sg.ev_done);
   }
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  for (auto x : s->setup_stream)
+    if (x) cudaStreamDestroy(x);
+  for (auto e : s->ev_idle)
+    if (e) cudaEventDestroy(e);
+  for (auto e : s->ev_ready)
+    if (e) cudaEventDestroy(e);
   if (s->ctx) {
     if (s->ctx->host_scal) cudaFreeHost(s->ctx->host_scal);
     delete s->ctx;
