@@ -132,6 +132,7 @@ struct Slot {
   int64_t traj = -1;
   size_t bytes = 0;
   bool busy = false;
+  bool pending = false;       // busy, its setup queued and not yet seen complete
   bool has_solution = false;  // x64[xbuf] holds a solution of this trajectory
   uint64_t last_used = 0;
   uint64_t solved_at = 0;     // clock of that solution
@@ -272,7 +273,8 @@ void evict_slot(pb_server *s, int j) {
   s->free_slots.push_back(j);
 }
 
-// Admit queued requests; returns the slots whose solves start now.
+// Admit queued requests and queue their setups; returns their slots, which
+// stay pending (out of the batch) until their setups are seen complete.
 std::vector<int> admit(pb_server *s) {
   std::vector<Request> cand;
   {
@@ -360,7 +362,7 @@ std::vector<int> admit(pb_server *s) {
       }
     }
     sl.busy = true;
-    sl.first_round = s->round;
+    sl.pending = true;
     sl.last_used = ++s->clock;
     sl.warm = s->opts.warm_start && sl.has_solution;
     if (pb_run_setup(sl.g, (int)rq.q.size(), rq.xyz.data(), rq.q.data(), rq.r.data(), false, sst)) {
@@ -378,8 +380,6 @@ std::vector<int> admit(pb_server *s) {
     taken.push_back(sl.req.ticket);
     started.push_back(j);
   }
-  // the start kernel and the graph come after every setup of this round
-  for (int j : started) cudaStreamWaitEvent(s->stream, s->ev_ready[j], 0);
   if (!taken.empty()) {
     std::lock_guard<std::mutex> lk(s->mu);
     std::deque<Request> rest;
@@ -410,7 +410,7 @@ bool rebuild_batch(pb_server *s, Stage &sg, bool *graph_stale) {
   std::vector<Item> st;
   std::vector<int> active;
   for (int j = 0; j < (int)s->slots.size(); j++)
-    if (s->slots[j].g && s->slots[j].busy) active.push_back(j);
+    if (s->slots[j].g && s->slots[j].busy && !s->slots[j].pending) active.push_back(j);
   int st_off = 0, rs_off = 0, hi = 0;
   for (int j : active) {
     pb_grid *g = s->slots[j].g;
@@ -712,6 +712,7 @@ void worker_main(pb_server *s) {
   bool prev_graph = false;             // the previous round ran a graph: its scalars are unread
   std::vector<int> prev_active;        // ... over these slots
   std::vector<Finishing> finishing;    // results queued in the previous round
+  std::vector<int> pending;            // admitted, setups not yet seen complete
   while (true) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -723,7 +724,29 @@ void worker_main(pb_server *s) {
       if (s->stop) break;
     }
     Stage &sg = s->stage[s->round & 1], &sp = s->stage[(s->round & 1) ^ 1];
-    const std::vector<int> started = admit(s);
+    for (int j : admit(s)) pending.push_back(j);
+    // Snapshots whose setups have completed join the batch now; the others
+    // stay out of it, so the running solves never wait for a setup.  With
+    // nothing else to run, wait for the oldest setup.
+    std::vector<int> started;
+    if (!pending.empty() && !prev_graph && finishing.empty() &&
+        std::none_of(s->slots.begin(), s->slots.end(),
+                     [](const Slot &x) { return x.g && x.busy && !x.pending; }))
+      cudaEventSynchronize(s->ev_ready[pending.front()]);
+    for (size_t k = 0; k < pending.size();) {
+      const int j = pending[k];
+      const cudaError_t q = cudaEventQuery(s->ev_ready[j]);
+      if (q == cudaErrorNotReady) {
+        k++;
+        continue;
+      }
+      if (q != cudaSuccess) cuda_ok(q, s, "setup");
+      s->slots[j].pending = false;
+      s->slots[j].first_round = s->round;
+      started.push_back(j);
+      pending.erase(pending.begin() + k);
+    }
+    if (!s->worker_error.empty()) break;
     if (!started.empty()) active_changed = true;
     if (active_changed) {
       // descriptors first: the start kernel reads each grid's error word and
@@ -742,7 +765,7 @@ void worker_main(pb_server *s) {
     }
     std::vector<int> active;
     for (int j = 0; j < (int)s->slots.size(); j++)
-      if (s->slots[j].g && s->slots[j].busy) active.push_back(j);
+      if (s->slots[j].g && s->slots[j].busy && !s->slots[j].pending) active.push_back(j);
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->n_active = (int)active.size();
