@@ -363,6 +363,7 @@ std::vector<int> admit(pb_server *s) {
     }
     sl.busy = true;
     sl.pending = true;
+    sl.first_round = s->round;  // reset again when the solve starts
     sl.last_used = ++s->clock;
     sl.warm = s->opts.warm_start && sl.has_solution;
     if (pb_run_setup(sl.g, (int)rq.q.size(), rq.xyz.data(), rq.q.data(), rq.r.data(), false, sst)) {
@@ -799,7 +800,9 @@ void worker_main(pb_server *s) {
       std::vector<int> fin;
       for (int j : prev_active) {
         const Slot &sl = s->slots[j];
-        if (sl.g && sl.busy && sl.first_round < s->round && sp.scal[j].phase == PH_DONE)
+        // a pending slot's scalars are those of its previous solve
+        if (sl.g && sl.busy && !sl.pending && sl.first_round < s->round &&
+            sp.scal[j].phase == PH_DONE)
           fin.push_back(j);
       }
       if (!fin.empty()) {

@@ -543,6 +543,12 @@ class Server:
             pb_server_destroy(self.handle)
             self.handle = 0
 
+    def __del__(self):  # a server left open stops its worker before the process exits
+        try:
+            self.close()
+        except Exception:
+            pass
+
     def __enter__(self):
         return self
 

@@ -193,3 +193,40 @@ def test_phi_into_pageable_and_pinned_memory(pbm, ctx):
         assert np.isfinite(phi0).all()
         assert np.array_equal(phi0, phi1)
         assert r0.energy == r1.energy
+
+
+def test_steady_stream_every_result_is_its_own(pbm, ctx):
+    """Bursts of snapshots from a few trajectories, each burst submitted before
+    the previous one is collected (the bench's steady state): slots finish, are
+    re-admitted while the graph runs, and wait for their setups.  Every result
+    is the solve of its own snapshot (energy against the oracle), none is lost
+    or handed out twice."""
+    base = [inputs.random_small(500 + t, 29 + 4 * t, 25, 27, n_atoms=20) for t in range(3)]
+    rng = np.random.default_rng(8)
+    bursts = []
+    for _ in range(5):
+        burst = []
+        for t, p in enumerate(base):
+            for _ in range(3):
+                a = p.atoms.copy()
+                a.xyz = a.xyz + rng.normal(0, 0.05, a.xyz.shape)
+                burst.append((t, p, a))
+        bursts.append(burst)
+    got = []
+    with pbm.Server(ctx, 8 * GB, tol=1e-6) as srv:
+        pend = [(srv.submit(t, p.grid, a), p, a) for t, p, a in bursts[0]]
+        for i in range(len(bursts)):
+            nxt = [(srv.submit(t, p.grid, a), p, a) for t, p, a in bursts[i + 1]] \
+                if i + 1 < len(bursts) else []
+            for tk, p, a in pend:
+                out = srv.poll(tk, 60000)
+                assert out is not None, "a result never arrived"
+                got.append((out[0], p, a))
+            pend = nxt
+        assert srv.stats()["completed"] == sum(len(b) for b in bursts)
+    for r, p, a in got:
+        assert r.status == 0, r.info.as_dict()
+        s = oracle.setup(p.grid, a)
+        e_ref = oracle.energy(s, oracle.pcg(s, tol=1e-10).phi)
+        assert abs(r.energy - e_ref) <= 1e-6 * abs(e_ref)
+        assert r.info.iterations > 0 and r.info.relres_true < 1e-6
