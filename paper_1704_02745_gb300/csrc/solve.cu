@@ -403,38 +403,56 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
         const T *rm = ring + rq1 * ring_plane;
         const Vec<T> ym = ldv(rm + cg - RGW), yp = ldv(rm + cg + RGW);
         const T xl = rm[cg - 1], xr = rm[cg + NV];
-        Vec<T> a, dgs, mis;  // pass 1, packed: diag A and M^-1 by node
+        Vec<T> a, dgs, mis;  // packed: diag A (and M^-1, pass 1) by node
+        if (CM == COEF_PACKED) {
 #pragma unroll
-        for (int u = 0; u < NV; u++) {
-          const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
-          T av;
-          if (CM == COEF_PACKED) {
-            // Eq. (3) with the six edge coefficients of the code byte; a node
-            // whose edges all lie on one side (all but the nodes next to the
-            // surface) takes a single coefficient times the neighbour sum
-            const uint32_t b = (code_prev >> (8 * u)) & 0xffu, e6 = b & 63u;
-            T dg;
+          for (int u = 0; u < NV; u++) {
+            const uint32_t b = (code_prev >> (8 * u)) & 127u;
             if (UPD) {
-              const Pair<T> t = mtab[b & 127u];
-              dg = t.d;
+              const Pair<T> t = mtab[b];
               dgs.v[u] = t.d;
               mis.v[u] = t.i;
             } else {
-              dg = dtab[b & 127u];
+              dgs.v[u] = dtab[b];
             }
-            if (e6 == 0u || e6 == 63u) {
+          }
+          // Eq. (3) with the six edge coefficients of the code byte.  A node
+          // whose edges all lie on one side of the surface takes a single
+          // coefficient times the neighbour sum; so does a whole group of
+          // such nodes on the same side (all but the groups at the surface),
+          // with no test per node.
+          const uint32_t m6 = code_prev & 0x3F3F3F3Fu;
+          if (m6 == 0u || m6 == 0x3F3F3F3Fu) {
+            const T e = m6 ? ei : eo;
+#pragma unroll
+            for (int u = 0; u < NV; u++) {
+              const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
               const T s6 = ((pl + pr) + (ym.v[u] + yp.v[u])) + (pm.v[u] + pn.v[u]);
-              av = dg * pc.v[u] - (e6 ? ei : eo) * s6;
-            } else {
-              T s = ((b & 1u) ? ei : eo) * pl;
-              s += ((b & 2u) ? ei : eo) * pr;
-              s += ((b & 4u) ? ei : eo) * ym.v[u];
-              s += ((b & 8u) ? ei : eo) * yp.v[u];
-              s += ((b & 16u) ? ei : eo) * pm.v[u];
-              s += ((b & 32u) ? ei : eo) * pn.v[u];
-              av = dg * pc.v[u] - s;
+              a.v[u] = dgs.v[u] * pc.v[u] - e * s6;
             }
           } else {
+#pragma unroll
+            for (int u = 0; u < NV; u++) {
+              const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
+              const uint32_t b = (code_prev >> (8 * u)) & 0xffu, e6 = b & 63u;
+              if (e6 == 0u || e6 == 63u) {
+                const T s6 = ((pl + pr) + (ym.v[u] + yp.v[u])) + (pm.v[u] + pn.v[u]);
+                a.v[u] = dgs.v[u] * pc.v[u] - (e6 ? ei : eo) * s6;
+              } else {
+                T s = ((b & 1u) ? ei : eo) * pl;
+                s += ((b & 2u) ? ei : eo) * pr;
+                s += ((b & 4u) ? ei : eo) * ym.v[u];
+                s += ((b & 8u) ? ei : eo) * yp.v[u];
+                s += ((b & 16u) ? ei : eo) * pm.v[u];
+                s += ((b & 32u) ? ei : eo) * pn.v[u];
+                a.v[u] = dgs.v[u] * pc.v[u] - s;
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < NV; u++) {
+            const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
             NodeCoef<T> c = NodeCoef<T>{0, 0, 0, 0, 0, 0, 0};
             if ((G.vmask >> u) & 1u) c = node_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0 + u, z - 1);
             T s = c.exm * pl;
@@ -443,9 +461,8 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
             s += c.eyp * yp.v[u];
             s += c.ezm * pm.v[u];
             s += c.ezp * pn.v[u];
-            av = c.diag * pc.v[u] - s;
+            a.v[u] = c.diag * pc.v[u] - s;
           }
-          a.v[u] = av;
         }
         if (!full_group) {  // pad columns keep Ap = 0
 #pragma unroll
