@@ -901,8 +901,17 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
-  for (auto &x : s->setup_stream)
-    ok = ok && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+#ifndef PB_SETUP_PRIORITY
+#define PB_SETUP_PRIORITY 1
+#endif
+  {
+    // setups first: a snapshot waiting for its setup is a slot the batch lacks
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    const int prio = PB_SETUP_PRIORITY ? greatest : least;
+    for (auto &x : s->setup_stream)
+      ok = ok && cudaStreamCreateWithPriority(&x, cudaStreamNonBlocking, prio) == cudaSuccess;
+  }
   s->ev_idle.assign(MAX_SLOTS, nullptr);
   s->ev_ready.assign(MAX_SLOTS, nullptr);
   for (int j = 0; ok && j < MAX_SLOTS; j++)
