@@ -92,3 +92,19 @@ def test_grid_bytes_model(lib):
     b64 = pb.pb_grid_bytes(d, "f64")
     assert 40 * n < b32 < 60 * n
     assert b64 > b32
+
+
+def test_pinned_pool_size_classes():
+    """Page-locked phi buffers are pooled in size classes: a class holds the
+    request, wastes at most a quarter of itself, and is a multiple of 4 KB;
+    nearby grid sizes share a class (no GPU needed: only the arithmetic)."""
+    from paper_1704_02745_gb300.pb import PinnedPool
+    sizes = [8 * n ** 3 for n in range(9, 200, 2)] + [1, 7, 4096, 4097, 1 << 30]
+    for b in sizes:
+        c = PinnedPool.size_class(b)
+        assert c >= b and c % 4096 == 0
+        assert c <= max(4096, 1.25 * b) + 4096
+        assert PinnedPool.size_class(c) == c  # a class is its own class
+    assert PinnedPool.size_class(8 * 125 ** 3) == PinnedPool.size_class(8 * 127 ** 3)
+    classes = [PinnedPool.size_class(b) for b in sorted(sizes)]
+    assert classes == sorted(classes)
