@@ -31,8 +31,9 @@
 // and the centre tile of x, NSTAGE planes ahead of the plane being computed,
 // each stage completing on its own mbarrier.  The grid boundary needs no test:
 // TMA fills out-of-range elements with zeros, which is exactly the zero ghost
-// of the operator.  New directions p are built in a ring of four shared
-// planes with halo, from which the seven-point stencil reads.
+// of the operator.  New directions p are built in a ring of three shared
+// planes with halo, from which the stencil reads the in-plane neighbours;
+// each thread keeps its own group's p on the planes z-1, z, z+1 in registers.
 #include <cuda_bf16.h>
 
 #include <type_traits>
@@ -205,7 +206,8 @@ struct StageRing {
 
 // ---------------------------------------------------------------------------
 // INNER phase, one tile of either pass of a CG iteration (TMA pipeline, a
-// ring of p planes in shared memory, Ap from the ring):
+// ring of p planes in shared memory for the in-plane neighbours, the z
+// neighbours in registers):
 //
 //   PASS 0 (direction): p = z + beta p_old (one fused multiply-add per node,
 //     halo included, since the stored vector is z = M^-1 r), Ap, this
@@ -216,12 +218,12 @@ struct StageRing {
 //     then r = M z - alpha Ap, z = M^-1 r; stores z; r.z in v0, r.r in v1.
 //
 // Recomputing Ap costs the p read of pass 1 (4 B per node) and saves the Ap
-// write of pass 0 and read of pass 1 (8 B), but a tile pass runs at a fixed
-// time per plane and tile, whatever its bytes: it pays where many grids fill
-// every SM with tiles (a server batch), not on one grid, where the row-chunk
-// update pass streams at close to the copy rate.  dtab: the operator's diagonal,
-// mtab: {M, M^-1}, by code byte, in shared memory per item.  Sets `abort`
-// if a pipeline wait timed out.
+// write of pass 0 and read of pass 1 (8 B), but a tile pass runs at a nearly
+// fixed time per plane and tile, whatever its bytes: it pays where many
+// grids fill every SM with tiles (a server batch, and no Ap array resident),
+// not on one grid, where the row-chunk update pass streams faster.  dtab: the
+// operator's diagonal, mtab: {diag A, M^-1}, by code byte, in shared memory
+// per item.  Sets `abort` if a pipeline wait timed out.
 //
 // Periodic grids: the z planes before and after the grid are the last and
 // the first (the TMA loads wrap the plane index), and every ring cell that
