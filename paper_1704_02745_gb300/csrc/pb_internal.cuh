@@ -43,7 +43,10 @@ constexpr int HMAX = 24;       // tallest tile
 constexpr int TILE_NODES = PB_TILE_NODES;  // W*H at most (<= NV*NT)
 constexpr int NT_UPD = 256;    // threads per update CTA
 constexpr int CH = 2048;       // fewest elements per chunk of the update pass
-constexpr int RESID_TZ = 4;    // z planes per item of the residual pass
+#ifndef PB_RESID_TZ
+#define PB_RESID_TZ 4
+#endif
+constexpr int RESID_TZ = PB_RESID_TZ;  // z planes per item of the residual pass
 constexpr int NDTAB = 14;      // diagonal table entries: (#inside edges 0..6) x (lambda 0/1)
 constexpr int PITCH_ALIGN = 16;  // node-array pitch in elements (TMA: 16-byte strides for bytes)
 

@@ -982,7 +982,10 @@ __global__ void __launch_bounds__(NT) k_resid(Batch B) {
 template <typename T, int CM>
 __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
   constexpr int V = 16 / sizeof(T);
-  constexpr int U = 4;  // vectors loaded before any is stored (loads in flight per thread)
+#ifndef PB_UPD_UNROLL
+#define PB_UPD_UNROLL 4
+#endif
+  constexpr int U = PB_UPD_UNROLL;  // vectors loaded before any is stored (loads in flight per thread)
   typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type VT;
   __shared__ double red[2 * (NT_UPD / 32)];
   __shared__ Pair<T> mtab[128];
