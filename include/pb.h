@@ -187,6 +187,23 @@ pb_status pb_apply_operator(pb_grid *grid, const void *u, void *Au, int dtype);
 pb_status pb_pcg_solve(pb_grid *grid, const pb_solve_opts *opts, double *phi,
                        pb_solve_info *info);
 
+/* Autotuner of a grid's stencil tile plan (the paper has no counterpart: its
+ * SpMV is a library call).  Times the stencil pass of each candidate plan --
+ * the fewest x tiles or one more, three tile heights, two z chunkings, and
+ * the analytic default -- on this grid with the kernels of `precision`
+ * (PB_PREC_*), keeps the fastest, and reports it in *info (may be NULL).
+ * The grid's later solves use that plan; their results do not depend on it
+ * beyond the order of the partial sums.  The grid's internal work vectors
+ * are scratch to the timing runs; its setup and the caller's arrays are
+ * untouched.  Errors: PB_ERR_ARG (NULL grid, bad precision), PB_ERR_OOM,
+ * PB_ERR_CUDA. */
+typedef struct {
+    int W, H, tz, n_tiles;      /* the plan kept: tile width, height, z planes, tiles */
+    int candidates;             /* plans timed */
+    double us_default, us_best; /* stencil pass (microseconds): default plan, plan kept */
+} pb_tune_info;
+pb_status pb_grid_autotune(pb_grid *grid, int precision, pb_tune_info *info);
+
 /* Electrostatic energy 1/2 * 332.0637 * sum_nodes q_node phi_node (kcal/mol)
  * of a DEVICE potential phi (nx*ny*nz doubles, borrowed); the energies that
  * Sec. 3.1 compares.  Evaluated in FP64 as sum_atoms q_a * (trilinear

@@ -177,18 +177,18 @@ extern "C" pb_status pb_free_grid(pb_grid *g) {
 #ifndef PB_PLAN_PER_SM
 #define PB_PLAN_PER_SM 2
 #endif
-void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
+// A tile plan given its x tiles, tile height and z chunks (clamped to what the
+// tiles allow); the residual pieces and update chunks follow from it.
+void pb_apply_plan(pb_grid *g, const KernelGrid &kg, bool batch, int tiles_x, int h, int zc) {
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
-  g->tiles_x = (nx + WMAX - 1) / WMAX;
-  g->W = round_up((nx + g->tiles_x - 1) / g->tiles_x, NV);
-  const int hmax = std::min(HMAX, TILE_NODES / g->W);
-  g->tiles_y = (ny + hmax - 1) / hmax;
+  tiles_x = std::max(tiles_x, (nx + WMAX - 1) / WMAX);
+  g->tiles_x = tiles_x;
+  g->W = round_up((nx + tiles_x - 1) / tiles_x, NV);
+  h = std::max(1, std::min(h, std::min(HMAX, TILE_NODES / g->W)));
+  g->tiles_y = (ny + h - 1) / h;
   g->H = (ny + g->tiles_y - 1) / g->tiles_y;
   const int cols = g->tiles_x * g->tiles_y;
-  const int resident = batch ? std::max(kg.stencil_blocks, 2 * g->ctx->num_sms)
-                             : std::min(kg.stencil_blocks, PB_PLAN_PER_SM * g->ctx->num_sms);
-  int zc = std::max(1, resident / cols);
-  zc = std::min(zc, std::max(1, nz / (batch ? 32 : 4)));
+  zc = std::max(1, std::min(zc, nz));
   g->tz = (nz + zc - 1) / zc;
   g->tiles_z = (nz + g->tz - 1) / g->tz;
   g->n_st = cols * g->tiles_z;
@@ -202,6 +202,20 @@ void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
   const long by_count = (rows + kg.update_blocks - 1) / kg.update_blocks;
   g->rows_per_chunk = (int)std::max<long>(std::max(1, (batch ? 16 * CH : CH) / nx), by_count);
   g->n_ch = (int)((rows + g->rows_per_chunk - 1) / g->rows_per_chunk);
+}
+
+void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
+  const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
+  const int tiles_x = (nx + WMAX - 1) / WMAX;
+  const int W = round_up((nx + tiles_x - 1) / tiles_x, NV);
+  const int hmax = std::min(HMAX, TILE_NODES / W);
+  const int tiles_y = (ny + hmax - 1) / hmax;
+  const int cols = tiles_x * tiles_y;
+  const int resident = batch ? std::max(kg.stencil_blocks, 2 * g->ctx->num_sms)
+                             : std::min(kg.stencil_blocks, PB_PLAN_PER_SM * g->ctx->num_sms);
+  int zc = std::max(1, resident / cols);
+  zc = std::min(zc, std::max(1, nz / (batch ? 32 : 4)));
+  pb_apply_plan(g, kg, batch, tiles_x, (ny + tiles_y - 1) / tiles_y, zc);
 }
 
 // (Re)run the setup kernels of a grid for the given host atoms.
@@ -746,6 +760,127 @@ static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, p
     info->ms_resid = acc.ms_resid; info->n_resid = acc.n_resid;
   }
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// Tile-plan autotuner: time the stencil pass of candidate plans on the grid.
+
+static pb_status realloc_work_lists(pb_grid *g, int mode) {
+  void *lists[] = {g->st_items, g->ch_items, g->st_part, g->ch_part, g->rs_part};
+  for (void *p : lists)
+    if (p) cudaFree(p);
+  g->st_items = g->ch_items = nullptr;
+  g->st_part = g->ch_part = g->rs_part = nullptr;
+  if (g->graph) {  // captured over the old lists
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  return pb_ensure_workspace(g, mode);
+}
+
+extern "C" pb_status pb_grid_autotune(pb_grid *g, int precision, pb_tune_info *info) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!g) return pb_fail(PB_ERR_ARG, "pb_grid_autotune: NULL grid");
+  if (precision < PB_PREC_F64 || precision > PB_PREC_F32_REFINE)
+    return pb_fail(PB_ERR_ARG, "pb_grid_autotune: bad precision");
+  if (g->batch) return pb_fail(PB_ERR_ARG, "pb_grid_autotune: a server's grid");
+  CK(cudaSetDevice(g->ctx->device));
+  const int mode = precision == PB_PREC_F64 ? MODE_F64
+                   : precision == PB_PREC_F32 ? MODE_F32 : MODE_F32_REFINE;
+  const int coef = pb_inner_coef(g, mode);
+  pb_status st;
+  if ((st = pb_ensure_workspace(g, mode))) return st;
+  cudaStream_t s = g->ctx->stream;
+  const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz, sms = g->ctx->num_sms;
+  const KernelGrid kplan = kernel_grid(MODE_F32, COEF_PACKED, sms, true);  // as at creation
+  struct Plan { int tx, h, zc; };
+  std::vector<Plan> cand{{g->tiles_x, g->H, g->tiles_z}};  // the analytic default first
+  const int tx_min = (nx + WMAX - 1) / WMAX;
+  const int resident = std::min(kplan.stencil_blocks, 2 * sms);
+  for (int tx = tx_min; tx <= tx_min + 1; tx++) {
+    const int W = round_up((nx + tx - 1) / tx, NV);
+    if (tx > tx_min && W < 32) continue;  // narrower tiles lose to their halos
+    const int hmax = std::min(HMAX, TILE_NODES / W);
+    for (int hf : {hmax, (3 * hmax) / 4, hmax / 2}) {
+      if (hf < 4) continue;
+      const int ty = (ny + hf - 1) / hf, h = (ny + ty - 1) / ty;
+      const int z0 = std::min(std::max(1, resident / (tx * ty)), std::max(1, nz / 4));
+      for (int zc : {z0, 2 * z0}) {
+        if (zc > std::max(1, nz / 2)) continue;
+        bool dup = false;
+        for (const Plan &p : cand) dup |= p.tx == tx && p.h == h && p.zc == zc;
+        if (!dup) cand.push_back(Plan{tx, h, zc});
+      }
+    }
+  }
+  pb_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  o.precond = PB_PRECOND_JACOBI;
+  o.precision = precision;
+  o.rel_tol = 1e-6;
+  o.max_iter = 1;
+  o.inner_tol = 1e-3;
+  o.max_outer = 1;
+  // each timed launch starts from the same scalars: an INNER iteration, alpha
+  // = beta = 0 (x and p stay as they are; the values are scratch)
+  Scal S0 = pb_initial_scal(1.0);
+  S0.phase = PH_INNER;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_plan = [&](double &us) -> pb_status {
+    Inst I;
+    pb_status r;
+    if ((r = pb_make_inst(g, &o, mode, coef, I))) return r;
+    CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
+    KernelGrid kg = kernel_grid(mode, coef, sms, true);
+    kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
+    kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
+    const Batch B = pb_single_batch(g);
+    std::vector<float> t;
+    for (int rep = 0; rep < 4; rep++) {
+      CK(cudaMemcpyAsync(g->scal, &S0, sizeof(Scal), cudaMemcpyHostToDevice, s));
+      CK(cudaEventRecord(e0, s));
+      CK(launch_phase(B, mode, coef, kg, 1, s));
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) t.push_back(ms);  // the first run warms the plan's descriptors
+    }
+    g->ctx->stats->launches += 4;
+    std::sort(t.begin(), t.end());
+    us = 1e3 * t[t.size() / 2];
+    return PB_OK;
+  };
+  int best = 0;
+  double best_us = 0, default_us = 0;
+  for (size_t k = 0; k < cand.size() && !st; k++) {
+    pb_apply_plan(g, kplan, false, cand[k].tx, cand[k].h, cand[k].zc);
+    double us = 0;
+    if ((st = realloc_work_lists(g, mode)) || (st = time_plan(us))) break;
+    if (k == 0) default_us = us;
+    if (k == 0 || us < best_us) {
+      best_us = us;
+      best = (int)k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pb_apply_plan(g, kplan, false, cand[best].tx, cand[best].h, cand[best].zc);
+  const pb_status st2 = realloc_work_lists(g, mode);
+  if (st) return st;
+  if (st2) return st2;
+  if (info) {
+    info->W = g->W;
+    info->H = g->H;
+    info->tz = g->tz;
+    info->n_tiles = g->n_st;
+    info->candidates = (int)cand.size();
+    info->us_default = default_us;
+    info->us_best = best_us;
+  }
+  return PB_OK;
 }
 
 extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *phi,

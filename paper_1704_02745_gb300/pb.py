@@ -71,6 +71,15 @@ class SolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneInfo(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int), ("tz", ctypes.c_int),
+                ("n_tiles", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("us_default", ctypes.c_double), ("us_best", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Solvation(ctypes.Structure):
     _fields_ = [("dG", ctypes.c_double), ("e_solv", ctypes.c_double), ("e_ref", ctypes.c_double),
                 ("solv", SolveInfo), ("ref", SolveInfo)]
@@ -128,6 +137,8 @@ def load(path: str = LIB_PATH):
     lib.pb_grid_update_atoms.argtypes = [_P, ctypes.c_int, _P, _P, _P]
     lib.pb_apply_operator.argtypes = [_P, _P, _P, ctypes.c_int]
     lib.pb_pcg_solve.argtypes = [_P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(SolveInfo)]
+    lib.pb_grid_autotune.restype = ctypes.c_int
+    lib.pb_grid_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(TuneInfo)]
     lib.pb_energy.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_double)]
     lib.pb_solvation_energy.argtypes = [_P, ctypes.POINTER(GridDesc), ctypes.c_int, _P, _P, _P,
                                         ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(Solvation)]
@@ -257,6 +268,12 @@ def pb_pcg_solve(grid: int, opts: SolveOpts, phi, check: bool = True) -> SolveIn
     return info
 
 
+def pb_grid_autotune(grid: int, precision: str = "f32_refine") -> TuneInfo:
+    info = TuneInfo()
+    _check(load().pb_grid_autotune(_P(grid), PREC[precision], ctypes.byref(info)))
+    return info
+
+
 def pb_energy(grid: int, phi) -> float:
     e = ctypes.c_double(0.0)
     _check(load().pb_energy(_P(grid), _P(_dptr(phi)), ctypes.byref(e)))
@@ -360,6 +377,10 @@ class Grid:
 
     def solve(self, phi, check: bool = True, **kw) -> SolveInfo:
         return pb_pcg_solve(self.handle, solve_opts(**kw), phi, check=check)
+
+    def autotune(self, precision: str = "f32_refine") -> TuneInfo:
+        """pb_grid_autotune: time candidate stencil tile plans, keep the fastest."""
+        return pb_grid_autotune(self.handle, precision)
 
     def energy(self, phi) -> float:
         return pb_energy(self.handle, phi)

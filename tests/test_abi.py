@@ -51,11 +51,11 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "pb.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pb_grid_desc), sizeof(pb_solve_opts),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pb_grid_desc), sizeof(pb_solve_opts),
          sizeof(pb_solve_info), offsetof(pb_grid_desc, dh_precision),
          offsetof(pb_solve_opts, profile), offsetof(pb_solve_info, n_resid),
          sizeof(pb_request), sizeof(pb_result), sizeof(pb_kernel_profile), sizeof(pb_solvation),
-         offsetof(pb_solvation, ref));
+         offsetof(pb_solvation, ref), sizeof(pb_tune_info), offsetof(pb_tune_info, us_best));
   return 0;
 }
 """)
@@ -66,7 +66,8 @@ int main(void) {
     want = [ctypes.sizeof(pb.GridDesc), ctypes.sizeof(pb.SolveOpts), ctypes.sizeof(pb.SolveInfo),
             pb.GridDesc.dh_precision.offset, pb.SolveOpts.profile.offset,
             pb.SolveInfo.n_resid.offset, ctypes.sizeof(pb.Request), ctypes.sizeof(pb.Result),
-            ctypes.sizeof(pb.KernelProfile), ctypes.sizeof(pb.Solvation), pb.Solvation.ref.offset]
+            ctypes.sizeof(pb.KernelProfile), ctypes.sizeof(pb.Solvation), pb.Solvation.ref.offset,
+            ctypes.sizeof(pb.TuneInfo), pb.TuneInfo.us_best.offset]
     assert got == want
 
 
