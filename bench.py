@@ -397,6 +397,20 @@ def run_serving(args):
     s_make, s_lat = poisson_run(served_stream_lat, Stream(seed=5, req_seed=77 + rank).take(n_pois), rate)
     p_make, p_lat_stream = poisson_run(plain_stream, Stream(seed=5, req_seed=77 + rank).take(n_pois),
                                        rate)
+    sweep = None
+    if args.poisson_sweep:  # the same stream at other multiples of the plain-FP64 capacity
+        sweep = []
+        for f in (0.5, 1.0, 1.5):
+            sm, sl = poisson_run(served_stream_lat, Stream(seed=5, req_seed=177 + rank).take(n_pois),
+                                 f * plain_rate)
+            pm, pl = poisson_run(plain_stream, Stream(seed=5, req_seed=177 + rank).take(n_pois),
+                                 f * plain_rate)
+            sweep.append({"factor": f, "rate_per_s": f * plain_rate, "requests": n_pois,
+                          "served": {"solves_per_s": n_pois / sm, "p50_ms": pct([1e3 * x for x in sl], 50),
+                                     "p99_ms": pct([1e3 * x for x in sl], 99)},
+                          "fp64_plain": {"solves_per_s": n_pois / pm,
+                                         "p50_ms": pct([1e3 * x for x in pl], 50),
+                                         "p99_ms": pct([1e3 * x for x in pl], 99)}})
     plain.close()
     # per-kernel device time on the served workload: one step with every
     # phase kernel launched on its own between CUDA events
@@ -452,6 +466,7 @@ def run_serving(args):
                            "served": {"solves_per_s": n_pois / s_make,
                                       "p50_ms": pct([1e3 * x for x in s_lat], 50),
                                       "p99_ms": pct([1e3 * x for x in s_lat], 99)},
+                           "sweep": sweep,
                            "fp64_plain": {"solves_per_s": n_pois / p_make,
                                           "p50_ms": pct([1e3 * x for x in p_lat_stream], 50),
                                           "p99_ms": pct([1e3 * x for x in p_lat_stream], 99)}},
@@ -961,6 +976,8 @@ def main():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
+    ap.add_argument("--poisson-sweep", action="store_true",
+                    help="serving: also run the Poisson stream at 0.5x, 1.0x and 1.5x the plain-FP64 capacity")
     ap.add_argument("--autotune", action="store_true",
                     help="single grids: run the library's tile-plan autotuner before timing")
     ap.add_argument("--quick", action="store_true",
