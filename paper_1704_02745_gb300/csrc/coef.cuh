@@ -55,6 +55,43 @@ __device__ __forceinline__ NodeCoef<T> node_coef(const Inst &I, size_t e, int k)
   return c;
 }
 
+// Coefficients of a group of NV nodes e0 .. e0+NV-1 (e0 a multiple of NV, one
+// row) from explicit storage, by vector loads.  The x-edge after the last
+// node is read only when that node is in the grid (last_ok): otherwise it
+// may lie past the row, and past the array on its last row.
+template <typename T> struct GroupCoef { T ex[NV + 1], eym[NV], eyp[NV], ezm[NV], ezp[NV], diag[NV]; };
+template <typename C, typename T>
+__device__ __forceinline__ void load_group(const C *p, T *out) {
+  if constexpr (sizeof(C) == 2) {  // four bf16 in 8 bytes
+    const uint2 v = *(const uint2 *)p;
+    const __nv_bfloat162 a = *(const __nv_bfloat162 *)&v.x, b = *(const __nv_bfloat162 *)&v.y;
+    out[0] = (T)__low2float(a); out[1] = (T)__high2float(a);
+    out[2] = (T)__low2float(b); out[3] = (T)__high2float(b);
+  } else if constexpr (sizeof(C) == 4) {
+    const float4 v = *(const float4 *)p;
+    out[0] = (T)v.x; out[1] = (T)v.y; out[2] = (T)v.z; out[3] = (T)v.w;
+  } else {
+    const double2 v0 = ((const double2 *)p)[0], v1 = ((const double2 *)p)[1];
+    out[0] = (T)v0.x; out[1] = (T)v0.y; out[2] = (T)v1.x; out[3] = (T)v1.y;
+  }
+}
+template <typename T, int CM>
+__device__ __forceinline__ GroupCoef<T> group_coef(const Inst &I, size_t e0, int k, bool last_ok) {
+  typedef typename Store<CM>::type C;
+  static_assert(NV == 4, "group loads are four-wide");
+  const C *ex = (const C *)I.ex, *ey = (const C *)I.ey, *ez = (const C *)I.ez;
+  const size_t px = I.px, ey0 = e0 + (size_t)k * px, plane = px * I.ny;
+  GroupCoef<T> g;
+  load_group<C, T>(ex + e0, g.ex);
+  g.ex[NV] = last_ok ? (T)cvt(ex[e0 + NV]) : (T)0;
+  load_group<C, T>(ey + ey0, g.eym);
+  load_group<C, T>(ey + ey0 + px, g.eyp);
+  load_group<C, T>(ez + e0, g.ezm);
+  load_group<C, T>(ez + e0 + plane, g.ezp);
+  load_group<T, T>((const T *)I.diag + e0, g.diag);
+  return g;
+}
+
 // z = M^-1 r at node e (Jacobi), or z = r without preconditioner.
 template <typename T, int CM>
 __device__ __forceinline__ T zval(const Inst &I, size_t e, T r) {

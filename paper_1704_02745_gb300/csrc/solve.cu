@@ -452,18 +452,20 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
             }
           }
         } else {
+          // explicit storage: the group's coefficients by vector loads (pad
+          // lanes read the arrays' pads, and their Ap is zeroed below)
+          const GroupCoef<T> c = group_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0, z - 1,
+                                                   (G.vmask >> (NV - 1)) & 1u);
 #pragma unroll
           for (int u = 0; u < NV; u++) {
             const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
-            NodeCoef<T> c = NodeCoef<T>{0, 0, 0, 0, 0, 0, 0};
-            if ((G.vmask >> u) & 1u) c = node_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0 + u, z - 1);
-            T s = c.exm * pl;
-            s += c.exp * pr;
-            s += c.eym * ym.v[u];
-            s += c.eyp * yp.v[u];
-            s += c.ezm * pm.v[u];
-            s += c.ezp * pn.v[u];
-            a.v[u] = c.diag * pc.v[u] - s;
+            T s = c.ex[u] * pl;
+            s += c.ex[u + 1] * pr;
+            s += c.eym[u] * ym.v[u];
+            s += c.eyp[u] * yp.v[u];
+            s += c.ezm[u] * pm.v[u];
+            s += c.ezp[u] * pn.v[u];
+            a.v[u] = c.diag[u] * pc.v[u] - s;
           }
         }
         if (!full_group) {  // pad columns keep Ap = 0
