@@ -81,6 +81,18 @@ NCU_TRAFFIC_PER_NODE = {# k_stencil<float, packed, batch> over two timed serving
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
 
 
+def max_over_ranks(values, world):
+    """Element-wise maximum of per-rank timings over the process group (the
+    slowest rank sets the job's time); identity on one rank."""
+    if world <= 1:
+        return list(values)
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -341,10 +353,7 @@ def run_serving(args):
     clk = clocks.stop()
     torch.cuda.synchronize()
     st1 = ctx.stats()
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t[0])
+    total = max_over_ranks([total], world)[0]
     # end to end: the same steady state with phi copied back to the host per request
     e2e_steps = max(2, args.steps // 2)
     e2e_batches = [[(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
@@ -551,10 +560,7 @@ def run_ours(args):
         d2h = (st1[2] - st0[2]) / float(args.steps)
         total_dev_s = sum(dev_ms) / 1e3
         total_wall_s = sum(wall_ms) / 1e3
-        if world > 1:
-            t = torch.tensor([total_dev_s, total_wall_s], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_dev_s, total_wall_s = float(t[0]), float(t[1])
+        total_dev_s, total_wall_s = max_over_ranks([total_dev_s, total_wall_s], world)
         if args.quick:  # profiling runs: the timed loop only
             if rank == 0:
                 print(json.dumps({"quick": True, "ms_per_step": sum(dev_ms) / len(dev_ms),
@@ -824,10 +830,7 @@ def run_solvation(args):
     clk = clocks.stop()
     st1 = ctx.stats()
     total = sum(times)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t[0])
+    total = max_over_ranks([total], world)[0]
     if rank == 0:
         print(json.dumps({
             "metric": SOLVATION_METRIC, "value": world * args.steps / total, "unit": "energies/s",
@@ -890,10 +893,7 @@ def run_batch(args):
     bad = [r.status for r in res if r.status != 0]
     if bad:
         raise RuntimeError(f"batch requests failed: {bad[:5]}")
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t[0])
+    total = max_over_ranks([total], world)[0]
     prewarm_pinned(pb, [reqs])
     e0 = ctx.stats()
     e2e_wall, _, _ = serve_steps(srv, [reqs] * max(1, args.steps // 2), want_phi=True)
