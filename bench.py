@@ -76,8 +76,8 @@ def bytes_per_node(coef):
 NCU_TRAFFIC_PER_NODE = {# k_stencil<float, packed, batch> over two timed serving steps: 1652.0 GB of
                         # DRAM traffic / 74,204,745,229 grid-node stencil passes
                         "stencil_batch": 1651.992160512e9 / 74204745229,
-                        # k_stencil<float, packed, single grid> on 257^3: 405.1 MB / 16,974,593
-                        "stencil_grid": 405.113e6 / 16974593}
+                        # k_stencil<float, packed, single grid> on 257^3: 407.0 MB / 16,974,593
+                        "stencil_grid": 407.018e6 / 16974593}
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
 
 
