@@ -311,6 +311,14 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
   const bool halo_wrap = per && Hh.role && (hgx < 0 || hgx >= I.nx || hgy < 0 || hgy >= I.ny);
   const bool full_group = G.vmask == (1u << NV) - 1u;
   const T m_unit = (T)1;
+  // Pass 1 on a grid without wrap reads the in-plane neighbours of plane q-1
+  // straight from that plane's stage (the stored p with its halo, zero
+  // outside the grid: what the ring would hold), so it writes no ring.  The
+  // stage of plane q-1 is then in use until the barrier of iteration q+1:
+  // iteration q refills the stage of plane q-2, one plane later than the
+  // ring form refills that of plane q.
+  const bool box_nb = UPD && !per;
+  const T *sz_prev = nullptr;  // stage box of plane q-1 (box_nb)
 
   uint32_t code_prev = 0;
   T acc = 0, rz = 0, rr = 0;
@@ -353,7 +361,7 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
           if (G.x0 + G.tx + u >= I.nx || G.y0 + G.ty >= I.ny)
             pn.v[u] = wrapped_p(G.x0 + G.tx + u, G.y0 + G.ty, zwrap(z));
       }
-      stv(rg + cg, pn);
+      if (!box_nb) stv(rg + cg, pn);
       // deferred update of the previous iteration: x += alpha p_old (the
       // first inner iteration starts the FP32 increment d from zero)
       if (!UPD && G.vmask && q >= 1 && q < Q - 1) {
@@ -367,7 +375,7 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
       }
     }
     if (!UPD && q >= 1 && q < Q - 1) x += plane;
-    if (ok && Hh.role) {
+    if (ok && Hh.role && !box_nb) {
       if (halo_wrap)
         rg[hg] = wrapped_p(hgx < 0 ? hgx + I.nx : hgx, hgy, zwrap(z));
       else
@@ -378,7 +386,8 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
       // bounded time, before the CTA leaves.
       if (threadIdx.x == 0) {
         uint32_t s2 = SR.st, ph = SR.phase;
-        for (int u = q + 1; u < min(Q, q + NS); ++u) {
+        const int last = box_nb ? max(NS - 1, q + NS - 3) : q + NS - 1;  // last plane issued
+        for (int u = q + 1; u <= min(Q - 1, last); ++u) {
           mbar_wait(&full[s2], (ph >> s2) & 1u);
           ph ^= 1u << s2;
           s2 = s2 + 1 == NS ? 0 : s2 + 1;
@@ -390,9 +399,12 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
       v0 = v1 = 0.0;
       return;
     }
-    if (threadIdx.x == 0 && q + NS < Q) {
-      issue(q + NS, st_issue);
-      st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
+    if (threadIdx.x == 0) {
+      const int qi = box_nb ? q - 2 + NS : q + NS;  // refills the stage of plane q-2 or q
+      if ((!box_nb || q >= 2) && qi < Q) {
+        issue(qi, st_issue);
+        st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
+      }
     }
     if (q >= 2) {
       // groups with no node inside the grid store nothing: past the last
@@ -400,9 +412,10 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
       // any valid node ends within it: pitch and group starts are multiples
       // of NV)
       if (G.vmask) {
-        // plane q-1: in-plane neighbours from the ring, z neighbours and the
-        // centre from this thread's registers
-        const T *rm = ring + rq1 * ring_plane;
+        // plane q-1: in-plane neighbours from the ring (or its stage box:
+        // the same layout), z neighbours and the centre from this thread's
+        // registers
+        const T *rm = box_nb ? sz_prev : ring + rq1 * ring_plane;
         const Vec<T> ym = ldv(rm + cg - RGW), yp = ldv(rm + cg + RGW);
         const T xl = rm[cg - 1], xr = rm[cg + NV];
         Vec<T> a, dgs, mis;  // packed: diag A (and M^-1, pass 1) by node
@@ -517,6 +530,7 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
     }
     pm = pc;
     pc = pn;
+    sz_prev = sz;
     z_prev = zc;
     code_prev = codes;
     rq = rq + 1 == CG_RING_PLANES ? 0 : rq + 1;
@@ -773,7 +787,7 @@ template <typename T, int CM, int G> struct StencilCfg {
 };
 // The tile update pass (server batches): a smaller stage (one halo box).
 #ifndef PB_STAGES_UPD
-#define PB_STAGES_UPD 3
+#define PB_STAGES_UPD 4
 #endif
 #ifndef PB_MINB_UPD
 #define PB_MINB_UPD 3
