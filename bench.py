@@ -73,9 +73,9 @@ def bytes_per_node(coef):
     return {"stencil": 4 + 4 + 4 + 3 * c + 4 + 4 + 4 + 4, "update": 4 + 4 + 4 + 4}
 # DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
 # profiles/ (None until a capture of the current kernel exists).
-NCU_TRAFFIC_PER_NODE = {# k_stencil<float, packed, batch> over two timed serving steps: 1652.0 GB of
-                        # DRAM traffic / 74,204,745,229 grid-node stencil passes
-                        "stencil_batch": 1651.992160512e9 / 74204745229,
+NCU_TRAFFIC_PER_NODE = {# k_stencil<float, packed, batch> over two timed serving steps: 1652.3 GB of
+                        # DRAM traffic / 74,196,209,889 grid-node stencil passes
+                        "stencil_batch": 1652.325313536e9 / 74196209889,
                         # k_stencil<float, packed, single grid> on 257^3: 407.0 MB / 16,974,593
                         "stencil_grid": 407.018e6 / 16974593}
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
