@@ -83,6 +83,15 @@ def test_errors_are_reported_without_gpu(lib):
     assert lib.pb_setup_grid(None, None, 0, None, None, None, None) == pb.PB_ERR_ARG
     assert lib.pb_pcg_solve(None, None, None, None) == pb.PB_ERR_ARG
     assert lib.pb_grid_bytes(None, 0) == 0
+    assert lib.pb_grid_autotune(None, 0, None) == pb.PB_ERR_ARG
+    assert lib.pb_pinned_alloc(16, None) == pb.PB_ERR_ARG
+    assert lib.pb_pinned_free(None) == pb.PB_OK
+    p = pb._P()
+    st = lib.pb_pinned_alloc(4096, ctypes.byref(p))
+    if st == pb.PB_OK:  # some drivers pin host memory without a GPU
+        assert lib.pb_pinned_free(p) == pb.PB_OK
+    else:
+        assert st == pb.PB_ERR_OOM and not p.value
 
 
 def test_grid_bytes_model(lib):
