@@ -29,6 +29,7 @@ import subprocess
 import sys
 import threading
 import time
+from types import SimpleNamespace
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -71,14 +72,36 @@ def bytes_per_node(coef):
         return dict(BYTES_PER_NODE_GRID)
     c = 2 if coef == "bf16" else 4
     return {"stencil": 4 + 4 + 4 + 3 * c + 4 + 4 + 4 + 4, "update": 4 + 4 + 4 + 4}
-# DRAM bytes per node per stencil-pass launch from the ncu capture summarised in
-# profiles/ (None until a capture of the current kernel exists).
-NCU_TRAFFIC_PER_NODE = {# k_stencil<float, packed, batch> over two timed serving steps: 1652.3 GB of
-                        # DRAM traffic / 74,196,209,889 grid-node stencil passes
-                        "stencil_batch": 1652.325313536e9 / 74196209889,
-                        # k_stencil<float, packed, single grid> on 257^3: 407.0 MB / 16,974,593
-                        "stencil_grid": 407.018e6 / 16974593}
+# DRAM bytes (read + write) per grid node of one stencil-pass launch, from
+# bounded ncu captures (one kernel, at most three launches, a few GB on the
+# device) summarised in profiles/: (bytes per node, the summary it comes from).
+# None where no such capture of the current kernel exists.
+NCU_TRAFFIC_PER_NODE = {
+    "stencil_batch": None,
+    # k_stencil<float, packed, single grid> on 257^3, one launch: 407.0 MB / 16,974,593 nodes
+    "stencil_grid": (407.018e6 / 16974593, "profiles/k_stencil_globule257.md"),
+}
+# FP64 operations per grid node of the residual pass: x + d (1), the operator
+# diag x - sum of six eps x_nb (1 multiply, 6 multiply-adds), b - A x (1).
+RESID_FP64_OPS_PER_NODE = 9
 SNAPSHOT_SIGMA = 0.2  # A, per-coordinate perturbation between snapshots
+
+
+def resid_roofline(kp, alu):
+    """The FP64 residual pass against the device's measured FP64 rate: it is
+    bound by FP64 arithmetic, not by its 37 B per node."""
+    nodes = kp.bytes_resid / 37.0
+    sec = kp.ms_resid / 1e3
+    out = {"bound": "alu", "launch_ms": kp.ms_resid / max(kp.launches_resid, 1),
+           "launches": kp.launches_resid, "bytes_per_node": 37,
+           "achieved_gbs": kp.bytes_resid / max(sec, 1e-15) / 1e9,
+           "fp64_ops_per_node": RESID_FP64_OPS_PER_NODE}
+    if alu is not None and sec > 0:
+        ach = RESID_FP64_OPS_PER_NODE * nodes / sec
+        out.update({"achieved": ach / 1e12, "peak": alu["fp64_fma_per_s"] / 1e12, "unit": "T FP64 op/s",
+                    "frac": ach / alu["fp64_fma_per_s"],
+                    "peak_kind": "measured (pb_measure_alu: FP64 FMA loop, this run)"})
+    return out
 
 
 def max_over_ranks(values, world):
@@ -322,6 +345,7 @@ def run_serving(args):
     stream = Stream(seed=5, req_seed=99 + 1000 * rank)
     per_step = args.batch
     ctx = pb.Context(local)
+    alu = ctx.measure_alu().as_dict()  # the FP64 roofline of the residual pass
     budget = int(args.budget_gb * (1 << 30))
     srv = pb.Server(ctx, budget, precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol,
                     warm_start=True)
@@ -362,34 +386,53 @@ def run_serving(args):
     e2e0 = ctx.stats()
     e2e_wall, _, _ = serve_steps(srv, e2e_batches, want_phi=True)
     e2e1 = ctx.stats()
-    # plain FP64, one at a time, on the same kind of requests (fresh trajectories)
+    # plain FP64, one at a time: its capacity, measured on the first requests
+    # of the Poisson stream's request list (after one untimed solve of each
+    # trajectory's grid, so that grid creation is not timed)
+    pois_reqs = Stream(seed=5, req_seed=77 + rank).take(args.stream_requests)
     plain = PlainFP64(pb, ctx, torch)
-    pstream = Stream(seed=5, req_seed=98 + 1000 * rank)
+    seen = set()
+    for k, g, a in pois_reqs:
+        if k not in seen:
+            seen.add(k)
+            plain.solve(k, g, a, args.tol)
     p_lat = []
-    plain.solve(*pstream.next(), args.tol)  # warm-up
+    n_plain = min(len(pois_reqs), max(8, per_step))
     t0 = time.perf_counter()
-    n_plain = max(8, per_step // 2)
-    for _ in range(n_plain):
+    for k, g, a in pois_reqs[:n_plain]:
         t1 = time.perf_counter()
-        plain.solve(*pstream.next(), args.tol)
+        plain.solve(k, g, a, args.tol)
         p_lat.append(time.perf_counter() - t1)
     plain_rate = n_plain / (time.perf_counter() - t0)
-    # Poisson stream at 0.8x the plain-FP64 capacity, both arms
-    rate = 0.8 * plain_rate
+    # Open-loop Poisson streams (configs: 4,000 requests).  One sequence of
+    # unit-mean exponential gaps (seeded) and one list of requests serve every
+    # run: run at rate R, request i arrives at gap_sum[i] / R.  The served arm
+    # runs at 0.5x, 0.8x and 1.0x its own closed-loop capacity; both arms run the
+    # whole stream at 1.5x the plain-FP64 capacity (the shared comparison: the
+    # plain arm saturates there) and its first --stream-requests-low requests at
+    # 0.8x the plain capacity (a load the plain arm sustains).
     n_pois = args.stream_requests
+    n_low = min(args.stream_requests_low, n_pois)
+    served_cap = args.steps * per_step / total  # this rank's closed-loop rate
+    gaps = np.random.default_rng([17, rank]).exponential(1.0, n_pois)
+    gap_sum = np.cumsum(gaps) - gaps[0]
 
     def served_stream_lat(reqs, arrivals):
+        """Latency = result ready - scheduled arrival (a late submit counts)."""
         t_start = time.perf_counter()
         tickets = []
         for (k, g, a), ta in zip(reqs, arrivals):
             d = t_start + ta - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            tickets.append(srv.submit(k, g.replace(dh="f32"), a))
+            lag = time.perf_counter() - t_start - ta
+            tickets.append((srv.submit(k, g.replace(dh="f32"), a), lag))
         lat = []
-        for t in tickets:
+        for t, lag in tickets:
             r, _ = srv.poll(t, 600000)
-            lat.append(r.seconds)
+            if r.status != 0:
+                raise RuntimeError(f"served stream request failed: {r.status}")
+            lat.append(r.seconds + lag)
         return time.perf_counter() - t_start, lat
 
     def plain_stream(reqs, arrivals):
@@ -403,23 +446,25 @@ def run_serving(args):
             lat.append(time.perf_counter() - t_start - ta)  # queueing + service
         return time.perf_counter() - t_start, lat
 
-    s_make, s_lat = poisson_run(served_stream_lat, Stream(seed=5, req_seed=77 + rank).take(n_pois), rate)
-    p_make, p_lat_stream = poisson_run(plain_stream, Stream(seed=5, req_seed=77 + rank).take(n_pois),
-                                       rate)
-    sweep = None
-    if args.poisson_sweep:  # the same stream at other multiples of the plain-FP64 capacity
-        sweep = []
-        for f in (0.5, 1.0, 1.5):
-            sm, sl = poisson_run(served_stream_lat, Stream(seed=5, req_seed=177 + rank).take(n_pois),
-                                 f * plain_rate)
-            pm, pl = poisson_run(plain_stream, Stream(seed=5, req_seed=177 + rank).take(n_pois),
-                                 f * plain_rate)
-            sweep.append({"factor": f, "rate_per_s": f * plain_rate, "requests": n_pois,
-                          "served": {"solves_per_s": n_pois / sm, "p50_ms": pct([1e3 * x for x in sl], 50),
-                                     "p99_ms": pct([1e3 * x for x in sl], 99)},
-                          "fp64_plain": {"solves_per_s": n_pois / pm,
-                                         "p50_ms": pct([1e3 * x for x in pl], 50),
-                                         "p99_ms": pct([1e3 * x for x in pl], 99)}})
+    def stream_stats(n, make, lat):
+        ms = [1e3 * x for x in lat]
+        return {"solves_per_s": n / make, "p50_ms": pct(ms, 50), "p99_ms": pct(ms, 99),
+                "max_ms": max(ms)}
+
+    runs = []
+    for label, rate, n, both in (("0.5x served capacity", 0.5 * served_cap, n_pois, False),
+                                 ("0.8x served capacity", 0.8 * served_cap, n_pois, False),
+                                 ("1.0x served capacity", 1.0 * served_cap, n_pois, False),
+                                 ("1.5x plain capacity", 1.5 * plain_rate, n_pois, True),
+                                 ("0.8x plain capacity", 0.8 * plain_rate, n_low, True)):
+        arr = gap_sum[:n] / rate
+        sm, sl = served_stream_lat(pois_reqs[:n], arr)
+        run = {"load": label, "rate_per_s": rate, "requests": n,
+               "served": stream_stats(n, sm, sl), "fp64_plain": None}
+        if both:
+            pm, pl = plain_stream(pois_reqs[:n], arr)
+            run["fp64_plain"] = stream_stats(n, pm, pl)
+        runs.append(run)
     plain.close()
     # per-kernel device time on the served workload: one step with every
     # phase kernel launched on its own between CUDA events
@@ -470,21 +515,22 @@ def run_serving(args):
         "fp64_plain": {"value": plain_rate, "unit": "solves/s",
                        "latency_ms": {"p50": pct([1e3 * x for x in p_lat], 50),
                                       "p99": pct([1e3 * x for x in p_lat], 99)},
-                       "requests": n_plain, "note": "one at a time, phi0 = 0"},
-        "poisson_stream": {"rate_per_s": rate, "requests": n_pois,
-                           "served": {"solves_per_s": n_pois / s_make,
-                                      "p50_ms": pct([1e3 * x for x in s_lat], 50),
-                                      "p99_ms": pct([1e3 * x for x in s_lat], 99)},
-                           "sweep": sweep,
-                           "fp64_plain": {"solves_per_s": n_pois / p_make,
-                                          "p50_ms": pct([1e3 * x for x in p_lat_stream], 50),
-                                          "p99_ms": pct([1e3 * x for x in p_lat_stream], 99)}},
+                       "requests": n_plain,
+                       "note": "one at a time, phi0 = 0, the first requests of the Poisson stream's list"},
+        "poisson_stream": {"requests": n_pois, "capacity_per_s": {"served": served_cap,
+                                                                   "fp64_plain": plain_rate},
+                           "arrivals": ("one seeded sequence of unit-mean exponential gaps and one "
+                                        "request list, scaled to each rate; latency = result ready - "
+                                        "scheduled arrival"),
+                           "sweep": runs},
         "roofline": {"bound": "hbm",
                      "kernel": "k_stencil<float,packed>: batched stencil pass over the active grids",
                      "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
                      "peak_kind": peak_kind,
-                     "traffic": None if trf is None else trf * kp.bytes_stencil / BYTES_PER_NODE["stencil"] /
+                     "traffic": None if trf is None else trf[0] * kp.bytes_stencil / BYTES_PER_NODE["stencil"] /
                      max(kp.launches_stencil, 1),
+                     "traffic_source": None if trf is None else (
+                         f"DRAM bytes per node from {trf[1]}, scaled by the nodes of this run's launches"),
                      "bytes_per_launch": kp.bytes_stencil / max(kp.launches_stencil, 1),
                      "bytes_per_node": BYTES_PER_NODE["stencil"], "launch_ms": t_st * 1e3,
                      "launches": kp.launches_stencil,
@@ -492,21 +538,19 @@ def run_serving(args):
                      "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
                                      "bytes_per_node": BYTES_PER_NODE["update"],
                                      "launch_ms": t_up * 1e3, "launches": kp.launches_update},
-                     "resid_pass": {"achieved": kp.bytes_resid / max(kp.ms_resid, 1e-12) / 1e6,
-                                    "bytes_per_node": 37, "note": "FP64 arithmetic",
-                                    "launch_ms": kp.ms_resid / max(kp.launches_resid, 1),
-                                    "launches": kp.launches_resid}},
+                     "resid_pass": resid_roofline(kp, alu)},
         "e2e": {"value": world * e2e_steps * per_step / e2e_wall, "unit": "solves/s",
                 "h2d_bytes_per_step": int((e2e1[1] - e2e0[1]) / e2e_steps),
                 "d2h_bytes_per_step": int((e2e1[2] - e2e0[2]) / e2e_steps),
                 "note": "same steps with phi copied to host memory per request"},
         "gpu_launches": int(st1[0] - st0[0]),
         "clocks": clk,
+        "alu_rates": alu,
     }
     if not args.no_cpu_baseline:
-        k, g, a = Stream(seed=5, req_seed=99).next()
-        out["cpu_baseline"] = cpu_baseline(inputs.Problem("serving-request", g, a), a,
-                                           float(np.mean(iters)), args)
+        sample = [(g, a) for k, g, a in batches[0][:args.cpu_sample]]
+        out["cpu_baseline"] = cpu_baseline(sample, "the first requests of the timed serving steps",
+                                           args)
     print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
@@ -538,6 +582,7 @@ def run_ours(args):
         solve_kw = dict(precision="f64", precond="gmg", tol=args.tol)
     with torch.cuda.stream(stream):
         ctx = pb.Context(local, stream=stream.cuda_stream)
+        alu = ctx.measure_alu().as_dict()
         g = pb.Grid(ctx, spec, snaps[0])
         # the library's tile-plan autotuner (opt-in: the default plan is the one
         # the committed ncu traffic figure was taken on)
@@ -625,12 +670,16 @@ def run_ours(args):
                      "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
                      "peak_kind": peak_kind,
                      "traffic": (None if trf is None or spec.coef != "packed" or spec.periodic or tune
-                                 else trf * n_nodes),
+                                 or spec.nx != 257 else trf[0] * n_nodes),
+                     "traffic_source": (None if trf is None or spec.coef != "packed" or spec.periodic or tune
+                                        or spec.nx != 257 else trf[1]),
                      "bytes_per_node": bpn["stencil"], "launch_ms": t_st * 1e3,
                      "update_pass": {"achieved": ach_up, "frac": ach_up / hbm,
                                      "bytes_per_node": bpn["update"],
                                      "launch_ms": t_up * 1e3},
-                     "resid_pass_ms": prof.ms_resid / max(prof.n_resid, 1)},
+                     "resid_pass": resid_roofline(SimpleNamespace(
+                         ms_resid=prof.ms_resid, launches_resid=prof.n_resid,
+                         bytes_resid=37.0 * n_nodes * prof.n_resid), alu)},
         "e2e": {"value": world * args.steps / total_wall_s, "unit": "solves/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "latency_ms": {"p50": pct(wall_ms, 50), "p99": pct(wall_ms, 99)}},
@@ -638,69 +687,53 @@ def run_ours(args):
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(inputs.Problem(problem.name, spec, problem.atoms), snaps[0],
-                                         float(np.mean(iters)), args)
+        out["cpu_baseline"] = cpu_baseline([(problem.grid, snaps[0])], f"one {problem.name} snapshot",
+                                           args)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def oracle_solve_sample(problem, atoms, tol, max_sample_iters, dh_sample=2048):
-    """Time the oracle on one snapshot: dielectric map and charges in full, the
-    Debye-Hueckel boundary on `dh_sample` ghost nodes (scaled to all), and a
-    bounded number of PCG iterations.  Returns (fixed seconds, seconds per
-    iteration, solve result)."""
-    import oracle
-    grid = problem.grid
-    t0 = time.perf_counter()
-    oracle.dielectric(grid, atoms)
-    oracle.spread_charge(grid, atoms)
-    t1 = time.perf_counter()
-    pos = oracle.ghost_positions(grid)
-    n_gh = pos.shape[0]
-    t_dh, ghost = 0.0, None  # a periodic grid has no boundary sum
-    if not getattr(grid, "periodic", False):
-        sel = pos[np.linspace(0, n_gh - 1, min(dh_sample, n_gh)).astype(int)]
-        t2 = time.perf_counter()
-        oracle.dh_points(grid, atoms, sel)
-        t_dh = (time.perf_counter() - t2) * n_gh / sel.shape[0]
-        ghost = oracle.dh_ghost(grid, atoms) if n_gh <= dh_sample else np.zeros(n_gh)
-    s = oracle.setup(grid, atoms, ghost=ghost)  # b from the sampled run is not used for timing
-    t3 = time.perf_counter()
-    r = oracle.pcg(s, tol=tol, max_iter=max_sample_iters)
-    t4 = time.perf_counter()
-    oracle.energy(s, r.phi)
-    t5 = time.perf_counter()
-    return (t1 - t0) + t_dh + (t5 - t4), (t4 - t3) / max(r.iters, 1), r
+def oracle_pool_run(jobs, tol, procs, warmup_jobs=()):
+    """Complete FP64 oracle solves (setup with the full Debye-Hueckel sum,
+    Jacobi-PCG from phi0 = 0 to `tol`, energy) of independent (grid, atoms)
+    jobs, run side by side in `procs` spawned worker processes (the oracle's
+    arithmetic stays single-threaded).  The warm-up jobs run first, untimed.
+    Returns (wall seconds of the timed jobs, their per-job results)."""
+    from oracle import pool as opool
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as p:
+        p.map(_noop, range(procs))  # workers started and imported before any timing
+        if warmup_jobs:
+            p.map(opool._solve_one, [(g, a, tol, False, None) for g, a in warmup_jobs], chunksize=1)
+        t0 = time.perf_counter()
+        res = p.map(opool._solve_one, [(g, a, tol, False, None) for g, a in jobs], chunksize=1)
+        wall = time.perf_counter() - t0
+    bad = [r["status"] for r in res if r["status"] != 0]
+    if bad:
+        raise RuntimeError(f"oracle solves failed: {bad[:5]}")
+    return wall, res
 
 
-def iteration_scale(tol):
-    """Full oracle Jacobi-PCG iterations per grid edge node, calibrated on the
-    smallest serving trajectory (Jacobi-PCG iterations grow about linearly
-    with the edge length on these grids)."""
-    import oracle
-    st = Stream(seed=5, req_seed=99)
-    k = int(np.argmin([t.grid.nx for t in st.trajs]))
-    g = st.trajs[k].grid
-    s = oracle.setup(g, st.trajs[k].base)
-    r = oracle.pcg(s, tol=tol)
-    return r.iters / g.nx
+def _noop(i):
+    import oracle  # noqa: F401  (the worker's import, outside the timed region)
+    return i
 
 
-def cpu_baseline(problem, atoms, gpu_iters, args):
-    """The FP64 oracle (single thread) on the host: setup (boundary sampled)
-    and a bounded number of PCG iterations, scaled to a full solve."""
+def cpu_baseline(jobs, label, args):
+    """The FP64 oracle on the host cores: complete solves of a bounded sample
+    of the workload's requests, one per worker process; value = solves / wall."""
+    from oracle import pool as opool
     import oracle
     oracle.build()
-    n_iter = max(20, int(args.cpu_sample_iters))
-    t_fixed, t_iter, r = oracle_solve_sample(problem, atoms, args.tol, n_iter)
-    full_iters = r.iters if r.status == 0 else iteration_scale(args.tol) * problem.grid.nx
-    t_solve = t_fixed + t_iter * full_iters
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one {problem.name} ({problem.grid.nx}^3, {atoms.n} atoms): oracle "
-                       f"dielectric + charges, Debye-Hueckel on 2048 ghost nodes scaled to all, "
-                       f"{min(r.iters, n_iter)} FP64 Jacobi-PCG iterations scaled to "
-                       f"{full_iters:.0f}"),
+    procs = max(1, min(opool.host_cores(), len(jobs)))
+    wall, res = oracle_pool_run(jobs, args.tol, procs)
+    return {"value": len(jobs) / wall, "unit": "solves/s", "cores": procs, "kind": "oracle",
+            "sample": (f"{len(jobs)} complete FP64 oracle solves ({label}; full setup with the "
+                       f"Debye-Hueckel sum, Jacobi-PCG from phi0 = 0 to {args.tol:g}, energy), one "
+                       f"per worker process on {procs} host cores, {wall:.1f} s wall"),
+            "solve_seconds": [round(r["seconds"], 3) for r in res],
+            "iterations": [r["iters"] for r in res],
             "cpu": platform_cpu()}
 
 
@@ -715,73 +748,65 @@ def platform_cpu():
     return platform.machine()
 
 
+def reference_jobs(args, n):
+    """The first n steps of the workload as lists of (grid, atoms) oracle jobs
+    (the oracle's Debye-Hueckel sum is FP64 whatever the GPU arm's setting)."""
+    if args.workload == SERVING:  # the serving stream's first requests, in order
+        return "serving stream: 16 trajectories, 300-8000 atoms, grids 33^3-193^3", \
+            [[(g, a)] for _, g, a in Stream(seed=5, req_seed=99).take(n)]
+    if args.workload == BATCH:
+        return ("batch of 256 snapshots: 1,000-atom cluster, sigma 0.3 A, grids 49^3-97^3, "
+                "one snapshot per step"), [[(p.grid, p.atoms)] for p in inputs.snapshot_batch()[:n]]
+    problem = WORKLOADS[args.workload]()
+    import oracle
+    if args.workload == SOLVATION:  # the solvated and the reference system of a snapshot
+        ref_grid = oracle.reference_grid(problem.grid)
+        return "solvation energy of 129^3 globule snapshots (2,500 atoms)", \
+            [[(problem.grid, a), (ref_grid, a)] for a in snapshots(problem, n, seed=100)]
+    return problem.name, [[(problem.grid, a)] for a in snapshots(problem, n, seed=100)]
+
+
 def run_reference(args):
-    """The FP64 CPU oracle as the reference arm (rank 0 only): per step one
-    request of the workload, timed as in oracle_solve_sample and scaled to a
-    full solve."""
+    """The FP64 CPU oracle as the reference arm (rank 0 only): each step is one
+    request of the workload (two solves for a solvation energy), solved
+    completely; the steps run side by side in spawned worker processes on the
+    host cores.  value = timed steps / wall time of the timed steps."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
     import oracle
+    from oracle import pool as opool
     oracle.build()
-    if args.workload == SERVING:
-        reqs = Stream(seed=5, req_seed=99).take(args.warmup + args.steps)
-        probs = [inputs.Problem("serving-request", g, a) for _, g, a in reqs]
-        scale = iteration_scale(args.tol)
-        iters_of = lambda pr: scale * pr.grid.nx
-        name = "serving stream: 16 trajectories, 300-8000 atoms, grids 33^3-193^3"
-    elif args.workload == BATCH:
-        probs = inputs.snapshot_batch()[:args.warmup + args.steps]
-        scale = iteration_scale(args.tol)
-        iters_of = lambda pr: scale * pr.grid.nx
-        name = ("batch of 256 snapshots: 1,000-atom cluster, sigma 0.3 A, grids 49^3-97^3, "
-                "one server batch")
-    elif args.workload == SOLVATION:
-        # each step: the solvated and the reference system of one snapshot
-        problem = WORKLOADS[args.workload]()
-        ref_grid = oracle.reference_grid(problem.grid)
-        atoms = snapshots(problem, args.warmup + args.steps, seed=100)
-        full = {g.eps_out: oracle.pcg(oracle.setup(g, atoms[0]), tol=args.tol).iters
-                for g in (problem.grid, ref_grid)}
-        probs = []
-        for a in atoms:
-            probs.append([inputs.Problem("solvated", problem.grid, a),
-                          inputs.Problem("reference", ref_grid, a)])
-        iters_of = lambda pr: full[pr.grid.eps_out]
-        name = "solvation energy of 129^3 globule snapshots (2,500 atoms)"
-    else:
-        problem = WORKLOADS[args.workload]()
-        probs = [inputs.Problem(problem.name, problem.grid, a)
-                 for a in snapshots(problem, args.warmup + args.steps, seed=100)]
-        full = oracle.pcg(oracle.setup(problem.grid, probs[0].atoms), tol=args.tol)
-        iters_of = lambda pr: full.iters
-        name = problem.name
-    times = []
-    for i, step in enumerate(probs):
-        t = 0.0
-        for pr in (step if isinstance(step, list) else [step]):
-            t_fixed, t_iter, _ = oracle_solve_sample(pr, pr.atoms, args.tol, args.cpu_sample_iters)
-            t += t_fixed + t_iter * iters_of(pr)
-        if i >= args.warmup:
-            times.append(t)
-    total = sum(times)
-    val = args.steps / total
+    name, steps = reference_jobs(args, args.warmup + args.steps)
+    warm = [j for st in steps[:args.warmup] for j in st]
+    timed = steps[args.warmup:]
+    jobs = [j for st in timed for j in st]
+    procs = max(1, min(opool.host_cores(), len(jobs)))
+    wall, res = oracle_pool_run(jobs, args.tol, procs, warmup_jobs=warm)
+    per_step, k = [], 0
+    for st in timed:
+        per_step.append(sum(r["seconds"] for r in res[k:k + len(st)]))
+        k += len(st)
+    val = args.steps / wall
     unit = "energies/s" if args.workload == SOLVATION else "solves/s"
     print(json.dumps({
         "impl": "reference",
         "metric": {BATCH: BATCH_METRIC, SOLVATION: SOLVATION_METRIC}.get(args.workload, METRIC),
         "value": val, "unit": unit, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": name, "tol": args.tol, "solver": "oracle FP64 Jacobi-PCG"},
-        "latency_ms": {"p50": pct([t * 1e3 for t in times], 50),
-                       "p99": pct([t * 1e3 for t in times], 99)},
-        "cpu_baseline": {"value": val, "unit": unit, "cores": 1, "kind": "oracle",
-                         "sample": (f"per step one request: oracle dielectric + charges, "
-                                    f"Debye-Hueckel on 2048 ghost nodes scaled to all, "
-                                    f"{args.cpu_sample_iters} FP64 Jacobi-PCG iterations scaled "
-                                    f"to a full solve"),
+        "config": {"workload": name, "tol": args.tol,
+                   "solver": "oracle FP64 Jacobi-PCG from phi0 = 0 (complete solves)"},
+        "latency_ms": {"p50": pct([t * 1e3 for t in per_step], 50),
+                       "p99": pct([t * 1e3 for t in per_step], 99),
+                       "note": "one request's solve time in its worker"},
+        "iterations_mean": float(np.mean([r["iters"] for r in res])),
+        "cpu_baseline": {"value": val, "unit": unit, "cores": procs, "kind": "oracle",
+                         "sample": (f"{args.steps} steps of the workload, each solved completely by "
+                                    f"the oracle (full setup with the Debye-Hueckel sum, Jacobi-PCG to "
+                                    f"{args.tol:g}, energy), side by side in {procs} worker processes "
+                                    f"(after {args.warmup} untimed steps); {wall:.1f} s wall"),
                          "cpu": platform_cpu()},
         "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -956,14 +981,17 @@ def main():
     ap.add_argument("--workload", default=SERVING, choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=64, help="serving: requests per step")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device-memory budget")
-    ap.add_argument("--stream-requests", type=int, default=200,
-                    help="serving: requests of the Poisson stream (each arm)")
+    ap.add_argument("--stream-requests", type=int, default=4000,
+                    help="serving: requests of the open-loop Poisson stream")
+    ap.add_argument("--stream-requests-low", type=int, default=1000,
+                    help="serving: requests of the stream at 0.8x the plain-FP64 capacity (both arms)")
     ap.add_argument("--coef", default="packed", choices=["packed", "f32", "bf16"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="inner FP32 tolerance of the refinement (default: 1e-4 for the warm-started "
                          "serving stream and the batch, 1e-3 for cold single grids)")
-    ap.add_argument("--cpu-sample-iters", type=int, default=20)
+    ap.add_argument("--cpu-sample", type=int, default=8,
+                    help="serving: requests the oracle solves completely for cpu_baseline")
     ap.add_argument("--dh", default="f32", choices=["f32", "f64"],
                     help="precision of the Debye-Hueckel boundary sum in the grid setup")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -976,8 +1004,6 @@ def main():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
-    ap.add_argument("--poisson-sweep", action="store_true",
-                    help="serving: also run the Poisson stream at 0.5x, 1.0x and 1.5x the plain-FP64 capacity")
     ap.add_argument("--autotune", action="store_true",
                     help="single grids: run the library's tile-plan autotuner before timing")
     ap.add_argument("--quick", action="store_true",

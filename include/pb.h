@@ -46,9 +46,12 @@ enum {
     PB_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in pb_last_error) */
     PB_ERR_NOT_CONVERGED = 5, /* iteration cap reached before the tolerance */
     PB_ERR_BREAKDOWN = 6,     /* p.Ap <= 0 or a non-finite CG scalar */
-    PB_ERR_TIMEOUT = 7,       /* pb_batch_poll: result not ready within the timeout */
+    PB_ERR_TIMEOUT = 7,       /* pb_batch_poll: result not ready within the timeout; a solve:
+                                 a bounded device wait (a TMA tile load, ~50 ms of clock) gave
+                                 up, so the solve could not finish */
     PB_ERR_BUSY = 8,          /* pb_batch_submit: over the memory budget and queue full */
-    PB_ERR_NOT_FOUND = 9      /* unknown ticket */
+    PB_ERR_NOT_FOUND = 9,     /* unknown ticket */
+    PB_ERR_CANCELLED = 10     /* pb_batch_poll: the request was cancelled (pb_batch_cancel) */
 };
 
 /* Storage of the dielectric coefficients used by the FP32 operator. */
@@ -152,6 +155,21 @@ pb_status pb_destroy(pb_ctx *ctx);
  * and bytes it copied host->device and device->host.  Any pointer may be NULL. */
 pb_status pb_ctx_stats(pb_ctx *ctx, uint64_t *kernel_launches, uint64_t *h2d_bytes,
                        uint64_t *d2h_bytes);
+
+/* Measured arithmetic rates of ctx's device (the paper has no counterpart: its
+ * solver ran in FP32 on a GPU of its day).  A pure FMA loop -- eight
+ * independent chains per thread, one store per thread, a full wave of CTAs --
+ * timed with CUDA events, best of three launches after one untimed; FMAs per
+ * second in FP64 and FP32.  It is the roofline of the kernels whose FP64
+ * arithmetic sets their time (the FP64 true residual of the refinement, plain
+ * FP64 solves).  Allocates and frees a small device buffer; synchronises the
+ * context's stream.  Errors: PB_ERR_ARG (NULL), PB_ERR_OOM, PB_ERR_CUDA. */
+typedef struct {
+    double fp64_fma_per_s, fp32_fma_per_s;
+    int sms;                 /* streaming multiprocessors of the device */
+    double sm_max_mhz;       /* the device's maximum SM clock */
+} pb_alu_rates;
+pb_status pb_measure_alu(pb_ctx *ctx, pb_alu_rates *out);
 
 /* Grid setup on the device (Eq. 3 coefficients; Sec. 2.7 conditions):
  *  - eps on every edge: eps_in when the edge midpoint lies strictly inside an
@@ -261,7 +279,11 @@ size_t pb_grid_bytes(const pb_grid_desc *desc, int precision);
  * memory (room for n_atoms <= 1,048,576; larger returns PB_ERR_ARG).  The
  * first call on a device looks up that array's device address (make it
  * before any stream capture); every later call on that device reuses it.
- * All calls share the array, so calls that overlap on the GPU race. */
+ * That cached address assumes one CUDA context per device for the life of
+ * the process (the runtime's primary context): after cudaDeviceReset, or if
+ * the caller switches the device to another context, the cached address is
+ * stale and must not be used -- such callers should not use this entry
+ * point.  All calls share the array, so calls that overlap on the GPU race. */
 pb_status pb_energy_noalloc(int n_atoms, const double *xyzq, int nx, int ny, int nz, double h,
                             const double *origin, const double *phi, double *energy,
                             void *cuda_stream);
@@ -310,7 +332,12 @@ typedef struct {
  * options applied to every request (precision, preconditioner, tolerances;
  * warm_start = 1: later snapshots of a trajectory start from its last
  * solution).  NULL opts: FP32 + FP64 refinement, Jacobi, rel_tol 1e-6.  The
- * server runs a worker thread; pb_server_destroy stops it and frees all. */
+ * server runs a worker thread; pb_server_destroy stops it and frees all.
+ * Failures reach the requests they concern, and the server goes on serving:
+ * a grid the device has no memory for (after idle grids are released and the
+ * allocation retried once) fails its request with PB_ERR_OOM; a timed-out
+ * device wait in a batch fails every solve then on the device with
+ * PB_ERR_TIMEOUT (their grids are released). */
 pb_status pb_server_create(pb_ctx *ctx, size_t hbm_budget_bytes, const pb_solve_opts *opts,
                            pb_server **out);
 pb_status pb_server_destroy(pb_server *server);
@@ -318,10 +345,21 @@ pb_status pb_server_destroy(pb_server *server);
  * PB_ERR_ARG for a bad request (checked on the host before queueing). */
 pb_status pb_batch_submit(pb_server *server, const pb_request *req, uint64_t *ticket);
 /* Wait up to timeout_ms (0: do not wait; < 0: wait until ready) for a
- * ticket.  PB_ERR_TIMEOUT if not ready (the ticket stays valid);
+ * ticket.  PB_OK when the result is handed out (the ticket is then spent);
+ * the request's own outcome is result->status (PB_OK, or e.g. PB_ERR_ARG,
+ * PB_ERR_OOM, PB_ERR_TIMEOUT for a timed-out device wait, PB_ERR_CANCELLED).
+ * PB_ERR_TIMEOUT if not ready within timeout_ms (the ticket stays valid);
  * PB_ERR_NOT_FOUND for an unknown or already returned ticket.  Never blocks
  * forever when timeout_ms >= 0. */
 pb_status pb_batch_poll(pb_server *server, uint64_t ticket, int timeout_ms, pb_result *result);
+/* Cancel a request (the paper has no counterpart).  A request still queued
+ * leaves the queue; one on the device is stopped at the worker's next round
+ * (between graph launches), and its grid stays resident for the trajectory's
+ * next snapshot (which then starts cold).  *cancelled (may be NULL) = 1: the
+ * request's pb_batch_poll returns PB_ERR_CANCELLED, with no energy and phi_out
+ * unwritten; 0: its result was complete already and stands.  PB_ERR_NOT_FOUND
+ * for an unknown or already returned ticket.  Never blocks on the device. */
+pb_status pb_batch_cancel(pb_server *server, uint64_t ticket, int *cancelled);
 /* Counters: requests queued, active on the device, grids resident, bytes
  * resident, solves completed.  Any pointer may be NULL. */
 pb_status pb_server_stats(pb_server *server, int *queued, int *active, int *resident,
@@ -330,10 +368,14 @@ pb_status pb_server_stats(pb_server *server, int *queued, int *active, int *resi
 /* Kernel measurement of a running server.  Between begin and end the worker
  * launches each phase kernel on its own between CUDA events (slower, for
  * measurement) and sums, per kind of launch, the device time and the
- * algorithmic HBM bytes of the grids active in it: per grid node, 25 B for a
- * CG stencil pass, 13 B for an update pass, 37 B for an FP64 residual pass
- * (FP32 inner solves with one-byte coefficients; FP64 solves: 49, 25, 37).
- * Launches with no grid in the phase they serve are not counted. */
+ * algorithmic HBM bytes of the grids active in it.  Per grid node, FP32 inner
+ * solves with one-byte coefficients: 21 B for a CG stencil pass (read z,
+ * p_old, the x increment d and the code byte; write p and d -- a server's
+ * stencil pass stores no Ap), 13 B for an update pass (read p, z and the code
+ * byte; write z -- Ap is formed again from p), 37 B for an FP64 residual pass
+ * (read x, d, p, the code byte and b; write x and the new z).  FP64 solves:
+ * 41 B and 25 B for the two CG passes.  Launches with no grid in the phase
+ * they serve are not counted. */
 typedef struct {
     double ms_stencil, bytes_stencil;  /* CG stencil-pass launches */
     double ms_update, bytes_update;    /* update-pass launches */

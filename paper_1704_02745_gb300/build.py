@@ -67,5 +67,39 @@ def build(force: bool = False, extra=(), verbose: bool = False) -> str:
     return LIB
 
 
+FAULT_BUILD = os.path.join(PKG, "_build_fault")
+FAULT_LIB = os.path.join(FAULT_BUILD, "libpb_faulttest.so")
+
+
+def build_fault_test(force: bool = False) -> str:
+    """A separate copy of the library for the failure-path tests, compiled with
+    -DPB_FAULT_TEST: it adds two test hooks (pb_test_abandon_waits: the next
+    first-plane stage waits give up at once; pb_test_fail_allocs: the next
+    device allocations fail) and is never loaded by the product path."""
+    deps = _deps()
+    if not force and os.path.exists(FAULT_LIB) and all(
+            os.path.getmtime(p) <= os.path.getmtime(FAULT_LIB) for p in deps):
+        return FAULT_LIB
+    os.makedirs(FAULT_BUILD, exist_ok=True)
+    srcs = _sources()
+
+    def comp(src):
+        obj = os.path.join(FAULT_BUILD, os.path.basename(src)[:-3] + ".o")
+        cmd = [NVCC] + ARCH + FLAGS + ["-DPB_FAULT_TEST", "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        objs = list(ex.map(comp, srcs))
+    tmp = FAULT_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, FAULT_LIB)
+    return FAULT_LIB
+
+
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True)

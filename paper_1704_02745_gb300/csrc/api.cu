@@ -1,5 +1,6 @@
 // api.cu -- C ABI of libpb (declared in include/pb.h): contexts, grid setup,
 // operator application, the Jacobi-PCG solve driver and the energy.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -28,8 +29,22 @@ pb_status pb_fail(pb_status s, const std::string &msg) {
 
 extern "C" const char *pb_last_error(void) { return g_err.c_str(); }
 
+#ifdef PB_FAULT_TEST
+// Test builds only (-DPB_FAULT_TEST, never the product library): the next
+// `count` device allocations of the library fail as an exhausted device would.
+static std::atomic<int> g_fault_fail_allocs{0};
+extern "C" int pb_test_fail_allocs(int count) {
+  g_fault_fail_allocs.store(count);
+  return 0;
+}
+#endif
+
 pb_status pb_dalloc(void **p, size_t bytes) {
   *p = nullptr;
+#ifdef PB_FAULT_TEST
+  if (g_fault_fail_allocs.load() > 0 && g_fault_fail_allocs.fetch_sub(1) > 0)
+    return pb_fail(PB_ERR_OOM, "cudaMalloc(" + std::to_string(bytes) + "): injected failure");
+#endif
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -931,13 +946,16 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   if (o->profile) {
     if ((st = profiled_loop(g, mode, coef, max_ticks, info))) return st;
   } else {
+    int *herr_poll = (int *)(hs + 1);  // pinned slot after the scalars
     for (;;) {
       if ((st = pb_run_ticks(g, mode, coef, ticks))) return st;
       done_ticks += ticks;
       CK(cudaMemcpyAsync(hs, g->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
-      g->ctx->stats->d2h += sizeof(Scal);
+      CK(cudaMemcpyAsync(herr_poll, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      g->ctx->stats->d2h += sizeof(Scal) + sizeof(int);
       CK(cudaStreamSynchronize(s));
       if (hs->phase == PH_DONE) break;
+      if (*herr_poll & 2) break;  // a pipeline wait gave up: the solve cannot finish
       if (done_ticks > max_ticks) {
         hs->status = PB_ERR_TIMEOUT;
         break;

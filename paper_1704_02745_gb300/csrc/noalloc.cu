@@ -26,7 +26,10 @@ static __device__ __align__(256) double g_energy_partials[NOALLOC_PARTIALS];
 
 // Device address of g_energy_partials on each device, taken once per device
 // with that device current (the host-side name of the array is only a
-// stand-in, not a device address).
+// stand-in, not a device address).  The cache is keyed by device index and
+// kept for the life of the process, so it assumes one CUDA context per device
+// (the runtime's primary context): after cudaDeviceReset, or under another
+// context made current on the device, the cached address would be stale.
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 double *g_scratch[MAX_DEVICES] = {};

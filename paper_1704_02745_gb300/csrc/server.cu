@@ -133,6 +133,7 @@ struct Slot {
   size_t bytes = 0;
   bool busy = false;
   bool pending = false;       // busy, its setup queued and not yet seen complete
+  bool stopping = false;      // cancelled while on the device: its scalars were set to DONE
   bool has_solution = false;  // x64[xbuf] holds a solution of this trajectory
   uint64_t last_used = 0;
   uint64_t solved_at = 0;     // clock of that solution
@@ -187,6 +188,7 @@ struct pb_server {
   std::deque<Request> queue;
   std::unordered_map<uint64_t, pb_result> done;
   std::unordered_set<uint64_t> outstanding;  // submitted, result not yet returned by a poll
+  std::unordered_set<uint64_t> cancelled;    // cancelled after admission: stop, report PB_ERR_CANCELLED
   uint64_t next_ticket = 1, completed = 0, clock = 0;
   int n_active = 0, n_resident = 0;
   size_t bytes_resident = 0;
@@ -195,6 +197,7 @@ struct pb_server {
   std::vector<Slot> slots;  // index = device slot
   std::vector<int> free_slots;
   Scal *d_scal = nullptr, *h_scal = nullptr;
+  int *h_stop = nullptr;  // pinned {PH_DONE, PB_ERR_CANCELLED}: written into a stopped grid's scalars
   Inst *d_inst = nullptr;
   int *d_counts = nullptr, *d_list = nullptr, *d_err = nullptr;
   int *d_rlist = nullptr;  // instances waiting for a residual pass
@@ -257,6 +260,7 @@ void fail_request(pb_server *s, const Request &rq, int status) {
   r.info.status = status;
   r.seconds = since(rq.t_submit);
   std::lock_guard<std::mutex> lk(s->mu);
+  if (s->cancelled.erase(rq.ticket)) r.status = r.info.status = PB_ERR_CANCELLED;
   s->done[rq.ticket] = r;
   s->completed++;
   s->cv_done.notify_all();
@@ -279,6 +283,23 @@ std::vector<int> admit(pb_server *s) {
   std::vector<Request> cand;
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->cancelled.empty()) {  // cancelled before admission: leave the queue now
+      std::deque<Request> keep;
+      for (auto &r : s->queue) {
+        if (!s->cancelled.erase(r.ticket)) {
+          keep.push_back(std::move(r));
+          continue;
+        }
+        pb_result res;
+        memset(&res, 0, sizeof(res));
+        res.status = res.info.status = PB_ERR_CANCELLED;
+        res.seconds = since(r.t_submit);
+        s->done[r.ticket] = res;
+        s->completed++;
+      }
+      s->queue.swap(keep);
+      s->cv_done.notify_all();
+    }
     const size_t look = std::min<size_t>(s->queue.size(), 4096);
     for (size_t i = 0; i < look; i++) cand.push_back(s->queue[i]);
   }
@@ -315,15 +336,32 @@ std::vector<int> admit(pb_server *s) {
     int j;
     if (adm[i] >= 0) {
       j = idx[adm[i]];
+      if (!s->slots[j].g) continue;  // evicted after an allocation failure: replan later
     } else {
       if (s->free_slots.empty()) continue;  // all slots in use: stays queued
       j = s->free_slots.back();
       pb_grid *g = nullptr;
-      if (pb_grid_create(s->ctx, &rq.desc, true, &g) || pb_ensure_workspace(g, s->mode)) {
-        if (g) pb_grid_release(g);
-        continue;  // device memory short of the model: retry later
+      auto create = [&]() -> bool {
+        if (pb_grid_create(s->ctx, &rq.desc, true, &g) || pb_ensure_workspace(g, s->mode)) {
+          if (g) pb_grid_release(g);
+          g = nullptr;
+          return false;
+        }
+        return true;
+      };
+      if (!create()) {
+        // The device refused memory the budget model allows: free every idle
+        // grid and try once more; if that fails too, the request fails with
+        // PB_ERR_OOM (never retried forever) and the server goes on.
+        for (int k = 0; k < (int)s->slots.size(); k++)
+          if (k != j && s->slots[k].g && !s->slots[k].busy) evict_slot(s, k);
+        if (!create()) {
+          fail_request(s, rq, PB_ERR_OOM);
+          taken.push_back(rq.ticket);
+          continue;
+        }
       }
-      s->free_slots.pop_back();
+      s->free_slots.erase(std::find(s->free_slots.begin(), s->free_slots.end(), j));
       g->scal = s->d_scal + j;
       g->own_scal = false;
       cudaEventRecord(s->ev_idle[j], s->stream);  // its workspace clears
@@ -562,11 +600,12 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
     f.energy = sg.energy + k;
     *f.energy = 0.0;
     const size_t n = (size_t)g->d.nx * g->d.ny * g->d.nz;
-    if (S.status != PB_ERR_ARG && S.outer == -1 && sl.req.phi_out) {  // phi = 0, energy 0
+    const bool no_result = S.status == PB_ERR_ARG || S.status == PB_ERR_CANCELLED;
+    if (!no_result && S.outer == -1 && sl.req.phi_out) {  // phi = 0, energy 0
       f.zero_phi = true;
       f.n = n;
     }
-    if (S.status != PB_ERR_ARG && S.outer != -1) {
+    if (!no_result && S.outer != -1) {
       const double *x = S.xbuf ? g->x64b : g->x64;
       const double *phi = x;  // the padded solution itself, unless phi is wanted dense
       int pitch = g->g.px;
@@ -598,6 +637,7 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
     f.req = std::move(sl.req);
     out.push_back(std::move(f));
     sl.busy = false;
+    sl.stopping = false;
     sl.has_solution = S.status == PB_OK && S.outer != -1;
     sl.xbuf = S.xbuf;
     sl.last_used = ++s->clock;
@@ -625,6 +665,13 @@ void publish(pb_server *s, std::vector<Finishing> &fin) {
     pb_result r;
     memset(&r, 0, sizeof(r));
     r.status = S.status;
+    if (s->cancelled.erase(f.req.ticket)) {  // cancelled before its result was handed out
+      r.status = r.info.status = PB_ERR_CANCELLED;
+      r.seconds = since(f.req.t_submit);
+      s->done[f.req.ticket] = r;
+      s->completed++;
+      continue;
+    }
     r.energy = S.status == PB_ERR_ARG ? 0.0 : *f.energy;
     r.info.status = S.status;
     r.info.iterations = S.total_iter;
@@ -748,6 +795,41 @@ void worker_main(pb_server *s) {
       pending.erase(pending.begin() + k);
     }
     if (!s->worker_error.empty()) break;
+    // Cancellations: a snapshot whose setup just completed does not start;
+    // a running solve is stopped before this round's graph (its scalars say
+    // DONE, so the phase kernels skip it and it leaves the batch as a finished
+    // solve would, with no energy).
+    {
+      std::unordered_set<uint64_t> cx;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        cx = s->cancelled;
+      }
+      if (!cx.empty()) {
+        for (size_t k = 0; k < started.size();) {
+          Slot &sl = s->slots[started[k]];
+          if (cx.count(sl.req.ticket)) {
+            fail_request(s, sl.req, PB_ERR_CANCELLED);
+            sl.busy = false;
+            sl.req = Request();
+            started.erase(started.begin() + k);
+          } else {
+            k++;
+          }
+        }
+        for (int j = 0; j < (int)s->slots.size(); j++) {
+          Slot &sl = s->slots[j];
+          if (sl.g && sl.busy && !sl.pending && !sl.stopping && cx.count(sl.req.ticket)) {
+            cudaMemcpyAsync(&s->d_scal[j].phase, &s->h_stop[0], sizeof(int), cudaMemcpyHostToDevice,
+                            s->stream);
+            cudaMemcpyAsync(&s->d_scal[j].status, &s->h_stop[1], sizeof(int), cudaMemcpyHostToDevice,
+                            s->stream);
+            s->ctx->stats->h2d += 2 * sizeof(int);
+            sl.stopping = true;
+          }
+        }
+      }
+    }
     if (!started.empty()) active_changed = true;
     if (active_changed) {
       // descriptors first: the start kernel reads each grid's error word and
@@ -785,7 +867,8 @@ void worker_main(pb_server *s) {
       }
       const int hi = *std::max_element(active.begin(), active.end()) + 1;
       cudaMemcpyAsync(sg.scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
-      s->ctx->stats->d2h += hi * sizeof(Scal);
+      cudaMemcpyAsync(sg.counts + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+      s->ctx->stats->d2h += hi * sizeof(Scal) + sizeof(int);
       if (!cuda_ok(cudaEventRecord(sg.ev_graph, s->stream), s, "event")) break;
       ran = true;
     }
@@ -797,6 +880,26 @@ void worker_main(pb_server *s) {
     }
     if (prev_graph) {
       if (!cuda_ok(cudaEventSynchronize(sp.ev_graph), s, "round")) break;
+      if (sp.counts[2] & 2) {
+        // A pipeline wait gave up in that graph (bounded device wait): the
+        // grid whose tile was abandoned can no longer finish, and the error
+        // word does not say which.  Fail every solve on the device with
+        // PB_ERR_TIMEOUT, release their grids, clear the word, go on.
+        if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "round")) break;
+        for (int j = 0; j < (int)s->slots.size(); j++) {
+          Slot &sl = s->slots[j];
+          if (sl.g && sl.busy && !sl.pending) {
+            fail_request(s, sl.req, PB_ERR_TIMEOUT);
+            evict_slot(s, j);
+          }
+        }
+        if (!cuda_ok(cudaMemsetAsync(s->d_err, 0, 4 * sizeof(int), s->stream), s, "clear error")) break;
+        active_changed = true;
+        prev_graph = false;
+        prev_active.clear();
+        s->round++;
+        continue;
+      }
       std::vector<int> fin;
       for (int j : prev_active) {
         const Slot &sl = s->slots[j];
@@ -897,6 +1000,11 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && !pb_dalloc((void **)&s->d_rlist, MAX_SLOTS * sizeof(int));
   ok = ok && !pb_dalloc((void **)&s->d_err, 4 * sizeof(int));
   ok = ok && cudaMallocHost((void **)&s->h_scal, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void **)&s->h_stop, 2 * sizeof(int)) == cudaSuccess;
+  if (ok) {
+    s->h_stop[0] = PH_DONE;
+    s->h_stop[1] = PB_ERR_CANCELLED;
+  }
   ok = ok && cudaMemset(s->d_scal, 0, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
   ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
@@ -977,6 +1085,7 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->h_scal) cudaFreeHost(s->h_scal);
+  if (s->h_stop) cudaFreeHost(s->h_stop);
   for (Stage &sg : s->stage) {
     void *hp[] = {sg.inst, sg.items, sg.counts, sg.start, sg.scal, sg.energy, sg.phi};
     for (void *p : hp)
@@ -1059,7 +1168,19 @@ extern "C" pb_status pb_batch_poll(pb_server *s, uint64_t ticket, int timeout_ms
   *res = s->done[ticket];
   s->done.erase(ticket);
   s->outstanding.erase(ticket);
-  return res->status == PB_OK ? PB_OK : res->status;
+  return PB_OK;  // a result was handed out: its own outcome is res->status
+}
+
+extern "C" pb_status pb_batch_cancel(pb_server *s, uint64_t ticket, int *cancelled) {
+  if (!s) return pb_fail(PB_ERR_ARG, "pb_batch_cancel: NULL server");
+  if (cancelled) *cancelled = 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->outstanding.count(ticket)) return pb_fail(PB_ERR_NOT_FOUND, "unknown or returned ticket");
+  if (s->done.count(ticket)) return PB_OK;  // finished already: its result stands
+  s->cancelled.insert(ticket);  // the worker drops it from the queue, or stops it on the device
+  if (cancelled) *cancelled = 1;
+  s->cv_work.notify_all();
+  return PB_OK;
 }
 
 extern "C" pb_status pb_server_stats(pb_server *s, int *queued, int *active, int *resident,

@@ -80,8 +80,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 #endif
   return ok != 0;
 }
-// Wait for phase `parity` of a barrier, giving up after ~1 s of clock.
-constexpr long long WAIT_CYCLES = 2000000000LL;
+// Wait for phase `parity` of a barrier, giving up after 1e8 SM cycles (~50 ms
+// at 2 GHz; a TMA tile load lands in microseconds).  A wait that gives up sets
+// the launch's error word, and the host reports PB_ERR_TIMEOUT.
+#ifndef PB_WAIT_CYCLES
+#define PB_WAIT_CYCLES 100000000LL
+#endif
+constexpr long long WAIT_CYCLES = PB_WAIT_CYCLES;
 constexpr int CG_RING_PLANES = 3;  // p planes with halo held by a CG stencil pass
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -90,6 +95,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if (clock64() - t0 > WAIT_CYCLES) return false;
   return true;
 }
+
+#ifdef PB_FAULT_TEST
+// Test builds only (compiled with -DPB_FAULT_TEST, never into the product
+// library): while this count is positive, the first stage wait of a tile, in
+// the thread that issues the tile's copies, gives up at once, as a wait that
+// ran out of time would.  The copies themselves are issued and land as usual;
+// the exit path must wait for every one of them.
+__device__ int g_fault_abandon_waits;
+__device__ __forceinline__ bool fault_abandon_wait() {
+  return *(volatile int *)&g_fault_abandon_waits > 0 && atomicAdd(&g_fault_abandon_waits, -1) > 0;
+}
+#endif
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
                                             int y, int z) {
   asm volatile(
@@ -331,7 +348,12 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
   for (int u = 0; u < min(NS, Q); ++u) st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
   for (int q = 0; q < Q; ++q) {
     const uint32_t st = SR.st;
+#ifdef PB_FAULT_TEST
+    const bool ok = (q == 0 && threadIdx.x == 0 && fault_abandon_wait())
+                        ? false : mbar_wait(&full[st], (SR.phase >> st) & 1u);
+#else
     const bool ok = mbar_wait(&full[st], (SR.phase >> st) & 1u);
+#endif
     SR.phase ^= 1u << st;
     SR.st = st + 1 == NS ? 0 : st + 1;
     const uint8_t *sb = stages + st * stage_bytes;
@@ -382,12 +404,13 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
         rg[hg] = UPD || first ? sz[hr] : sz[hr] + beta * sp[hr];
     }
     if (__syncthreads_or(!ok)) {
-      // A wait gave up: let the copies already issued land, each for a
-      // bounded time, before the CTA leaves.
+      // A wait gave up: let the copies already issued land -- those of this
+      // plane q, whose wait gave up, and of every later plane issued -- each
+      // for a bounded time, before the CTA leaves.
       if (threadIdx.x == 0) {
-        uint32_t s2 = SR.st, ph = SR.phase;
+        uint32_t s2 = st, ph = SR.phase ^ (1u << st);  // plane q's stage and parity
         const int last = box_nb ? max(NS - 1, q + NS - 3) : q + NS - 1;  // last plane issued
-        for (int u = q + 1; u <= min(Q - 1, last); ++u) {
+        for (int u = q; u <= min(Q - 1, last); ++u) {
           mbar_wait(&full[s2], (ph >> s2) & 1u);
           ph ^= 1u << s2;
           s2 = s2 + 1 == NS ? 0 : s2 + 1;
@@ -965,6 +988,13 @@ __global__ void __launch_bounds__(NT) k_resid(Batch B) {
     Scal *Sp = I.s;
     const TileScal S = tile_scal(Sp);
     __syncthreads();  // everyone has read s_item
+    if (S.phase != PH_RESID) {
+      // an instance stopped by the host between launches (a cancelled
+      // request) while it waited for this pass: nothing to do
+      if (threadIdx.x == 0) s_item = take_item(&B.work[4]);
+      __syncthreads();
+      continue;
+    }
     double v0 = 0, v1 = 0;
     resid_tile<T, CM>(I, S, tile, ring, v0, v1);
     if (threadIdx.x == 0) s_item = take_item(&B.work[4]);
@@ -1256,3 +1286,11 @@ KernelGrid kernel_grid(int mode, int coef, int num_sms, bool single) {
 }
 
 }  // namespace pb
+
+#ifdef PB_FAULT_TEST
+// Test builds only: make the next `count` first-plane stage waits give up at
+// once (see g_fault_abandon_waits).  Returns 0, or PB_ERR_CUDA.
+extern "C" int pb_test_abandon_waits(int count) {
+  return cudaMemcpyToSymbol(pb::g_fault_abandon_waits, &count, sizeof(int)) == cudaSuccess ? 0 : 3;
+}
+#endif

@@ -18,17 +18,21 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpb.so")
+# PB_LIBRARY names another build of the same ABI (the failure-path tests load
+# the separately built test copy this way, in a process of their own).
+LIB_PATH = os.environ.get("PB_LIBRARY") or os.path.join(_HERE, "libpb.so")
 
 PB_OK, PB_ERR_ARG, PB_ERR_OOM, PB_ERR_CUDA = 0, 1, 2, 3
 PB_ERR_NOT_CONVERGED, PB_ERR_BREAKDOWN, PB_ERR_TIMEOUT, PB_ERR_BUSY, PB_ERR_NOT_FOUND = 5, 6, 7, 8, 9
+PB_ERR_CANCELLED = 10
 COEF = {"packed": 0, "f32": 1, "bf16": 2, "f64": 3}
 PB_F64, PB_F32 = 0, 1
 PREC = {"f64": 0, "f32": 1, "f32_refine": 2}
 PRECOND = {"none": 0, "jacobi": 1, "gmg": 2}
 EXPORT = {"eps_x": 0, "eps_y": 1, "eps_z": 2, "lambda": 3, "b": 4, "ghost": 5}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 5: "ERR_NOT_CONVERGED",
-                6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_BUSY", 9: "ERR_NOT_FOUND"}
+                6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_BUSY", 9: "ERR_NOT_FOUND",
+                10: "ERR_CANCELLED"}
 
 #: Every symbol include/pb.h declares (checked by the CPU tests).
 EXPORTED = ["pb_last_error", "pb_create", "pb_destroy", "pb_ctx_stats", "pb_setup_grid", "pb_free_grid",
@@ -107,6 +111,14 @@ class KernelProfile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AluRates(ctypes.Structure):
+    _fields_ = [("fp64_fma_per_s", ctypes.c_double), ("fp32_fma_per_s", ctypes.c_double),
+                ("sms", ctypes.c_int), ("sm_max_mhz", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SlotState(ctypes.Structure):
     _fields_ = [("trajectory_id", ctypes.c_int64), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("bytes", ctypes.c_size_t), ("busy", ctypes.c_int),
@@ -131,6 +143,8 @@ def load(path: str = LIB_PATH):
     lib.pb_destroy.argtypes = [_P]
     lib.pb_ctx_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(ctypes.c_uint64)]
+    lib.pb_measure_alu.restype = ctypes.c_int
+    lib.pb_measure_alu.argtypes = [_P, ctypes.POINTER(AluRates)]
     lib.pb_setup_grid.argtypes = [_P, ctypes.POINTER(GridDesc), ctypes.c_int, _P, _P, _P,
                                   ctypes.POINTER(_P)]
     lib.pb_free_grid.argtypes = [_P]
@@ -149,6 +163,8 @@ def load(path: str = LIB_PATH):
     lib.pb_server_destroy.argtypes = [_P]
     lib.pb_batch_submit.argtypes = [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     lib.pb_batch_poll.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result)]
+    lib.pb_batch_cancel.restype = ctypes.c_int
+    lib.pb_batch_cancel.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
     lib.pb_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t),
                                     ctypes.POINTER(ctypes.c_uint64)]
@@ -325,6 +341,12 @@ class Context:
     def stats(self):
         return pb_ctx_stats(self.handle)
 
+    def measure_alu(self) -> AluRates:
+        """pb_measure_alu: the device's measured FP64 and FP32 FMA rates."""
+        out = AluRates()
+        _check(load().pb_measure_alu(_P(self.handle), ctypes.byref(out)))
+        return out
+
     def solvation(self, spec, atoms, phi, check: bool = True, **opts) -> Solvation:
         return pb_solvation_energy(self.handle, spec, atoms, phi, check=check, **opts)
 
@@ -423,6 +445,14 @@ def pb_batch_poll(server: int, ticket: int, timeout_ms: int = -1, check: bool = 
     if check:
         _check(st)
     return st, res
+
+
+def pb_batch_cancel(server: int, ticket: int) -> bool:
+    """True: the request was cancelled (its poll reports PB_ERR_CANCELLED);
+    False: its result was complete already."""
+    c = ctypes.c_int(0)
+    _check(load().pb_batch_cancel(_P(server), ticket, ctypes.byref(c)))
+    return bool(c.value)
 
 
 def pb_server_stats(server: int):
@@ -550,6 +580,10 @@ class Server:
 
     def stats(self):
         return pb_server_stats(self.handle)
+
+    def cancel(self, ticket: int) -> bool:
+        """pb_batch_cancel: True if the request was cancelled."""
+        return pb_batch_cancel(self.handle, ticket)
 
     def profile_begin(self):
         _check(load().pb_server_profile_begin(_P(self.handle)))
