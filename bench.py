@@ -349,9 +349,20 @@ def run_serving(args):
     budget = int(args.budget_gb * (1 << 30))
     srv = pb.Server(ctx, budget, precision="f32_refine", tol=args.tol, inner_tol=args.inner_tol,
                     warm_start=True)
-    # warm-up steps, then the timed steps
-    for _ in range(args.warmup):
-        serve_batch(srv, [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)])
+    if args.plan:
+        srv.set_plan(*[int(v) for v in args.plan.split(",")])
+        args.no_autotune = True
+    # warm-up steps (the batch's tile plan is tuned on the first), then the timed steps
+    tune = None
+    for w in range(args.warmup):
+        reqs = [(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
+        if w == 0 and not args.no_autotune:
+            tickets = [srv.submit(k, g, a) for k, g, a in reqs]
+            tune = srv.autotune(600000).as_dict()
+            for t in tickets:
+                srv.poll(t, 600000)
+        else:
+            serve_batch(srv, reqs)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -378,6 +389,14 @@ def run_serving(args):
     torch.cuda.synchronize()
     st1 = ctx.stats()
     total = max_over_ranks([total], world)[0]
+    if args.quick:  # sweeps: the closed-loop rate only
+        if rank == 0:
+            print(json.dumps({"quick": True, "workload": "serving", "plan": args.plan, "tune": tune,
+                              "solves_per_s": world * args.steps * per_step / total,
+                              "iterations_mean": float(np.mean(iters)), "clocks": clk}), flush=True)
+        srv.close()
+        ctx.close()
+        return
     # end to end: the same steady state with phi copied back to the host per request
     e2e_steps = max(2, args.steps // 2)
     e2e_batches = [[(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
@@ -506,7 +525,8 @@ def run_serving(args):
                    "inner_tol": args.inner_tol, "budget_gb": args.budget_gb,
                    "debye_hueckel_sum": "f32", "snapshot_sigma_A": 0.2,
                    "l2": "inputs larger than L2 (2.1 M nodes mean per request, 64 per step)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "batch_plan": tune if tune is not None else (args.plan or "default {min_planes 32, height 100%, 3 CTAs/SM}")},
         "latency_ms": {"p50": pct([1e3 * x for x in lats], 50), "p99": pct([1e3 * x for x in lats], 99),
                        "note": "steady state: 64 requests per step, the next step queued while "
                                "this one completes; submit -> result"},
@@ -899,8 +919,21 @@ def run_batch(args):
     ctx = pb.Context(local)
     srv = pb.Server(ctx, int(args.budget_gb * (1 << 30)), precision="f32_refine", tol=args.tol,
                     inner_tol=args.inner_tol, warm_start=False)
+    if args.plan:
+        srv.set_plan(*[int(v) for v in args.plan.split(",")])
     for _ in range(args.warmup):
         serve_batch(srv, reqs)
+    tune, default_rate = None, None
+    if args.autotune:  # the default plan timed, then the batch tuned on a live step
+        if world > 1:
+            torch.distributed.barrier()
+        t_def, _, _ = serve_steps(srv, [reqs] * args.steps)
+        default_rate = len(reqs) * args.steps / max_over_ranks([t_def], world)[0]
+        tickets = [srv.submit(k, g, a) for k, g, a in reqs]
+        tune = srv.autotune(600000).as_dict()
+        for t in tickets:
+            srv.poll(t, 600000)
+        serve_batch(srv, reqs)  # one more warm-up step under the kept plan
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -946,7 +979,9 @@ def run_batch(args):
                                "grids 49^3-97^3, one server batch",
                    "nodes_per_step": nodes, "tol": args.tol, "inner_tol": args.inner_tol,
                    "debye_hueckel_sum": "f32", "l2": f"inputs larger than L2 ({nodes / 1e6:.0f} M nodes)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "batch_plan": tune if tune is not None else (args.plan or "default {min_planes 32, height 100%, 3 CTAs/SM}")},
+        "default_plan_solves_per_s": None if default_rate is None else world * default_rate,
         "iterations_mean": float(np.mean(iters)),
         "grid_point_iters_per_s": world * args.steps * sum(
             p.grid.n * r.info.iterations for p, r in zip(snaps * args.steps, res)) / args.steps / total,
@@ -1005,7 +1040,13 @@ def main():
                     help="bracket the timed steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
     ap.add_argument("--autotune", action="store_true",
-                    help="single grids: run the library's tile-plan autotuner before timing")
+                    help="single grids: run the library's tile-plan autotuner before timing; batch256: "
+                         "time the default plan, tune the batch, then time the tuned plan")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="serving: keep the default batch plan (no tuning during the warm-up)")
+    ap.add_argument("--plan", default=None,
+                    help="serving/batch256: fixed batch plan 'min_planes,height_pct,occupancy' "
+                         "(skips the tuning)")
     ap.add_argument("--quick", action="store_true",
                     help="timed loop only (no FP64 comparator, profiled solve or CPU baseline)")
     args = ap.parse_args()

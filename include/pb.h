@@ -365,6 +365,42 @@ pb_status pb_batch_cancel(pb_server *server, uint64_t ticket, int *cancelled);
 pb_status pb_server_stats(pb_server *server, int *queued, int *active, int *resident,
                           size_t *bytes_resident, uint64_t *completed);
 
+/* Tile plan of a server's batch (the paper has no counterpart: its SpMV was a
+ * library call).  Every grid of the batch is cut into W x H column tiles --
+ * the fewest tiles of width <= 64 across x, then height_pct percent of the
+ * tallest height a tile of that width allows (W*H <= 1024) -- and the columns
+ * into z chunks of at least min_planes planes (as many chunks as fill the
+ * device's resident stencil CTAs, no more).  occupancy: resident CTAs per SM
+ * of the stencil pass, 3 (the batch build) or 2 (the build whose shared
+ * memory admits two).  Results do not depend on the plan beyond the order of
+ * the partial sums of each reduction.  Default: {32, 100, 3}. */
+typedef struct {
+    int min_planes;   /* >= 1 */
+    int height_pct;   /* 1 .. 100 */
+    int occupancy;    /* 2 or 3 */
+} pb_batch_plan;
+/* Use `plan` for the batch from the worker's next round on (every resident
+ * grid is re-planned between graph launches; solves in flight continue).
+ * PB_ERR_ARG for an out-of-range field. */
+pb_status pb_server_set_plan(pb_server *server, const pb_batch_plan *plan);
+
+/* Autotuner of the batch's tile plan, on the live batch.  At the worker's
+ * next round with solves on the device, every candidate plan -- min_planes
+ * 16, 32, 64, 128 or whole grids; height_pct 100 or 67; occupancy 3 or 2 --
+ * is applied to all active grids in turn and the stencil and update passes
+ * of two CG ticks are timed with CUDA events (the solves advance meanwhile);
+ * the four fastest by HBM bytes per second are timed again, and the fastest
+ * plan is kept for the batch and for grids admitted later.  Waits up to
+ * timeout_ms (< 0: without limit) for the tuning to finish; PB_ERR_TIMEOUT if
+ * it has not (it still runs once a batch is active).  *out (may be NULL):
+ * the plan kept, and bytes per second of the default and of the kept plan. */
+typedef struct {
+    pb_batch_plan plan;                /* the plan kept */
+    int candidates;                    /* plans timed */
+    double gbs_default, gbs_best;      /* stencil + update passes: algorithmic GB/s */
+} pb_server_tune_info;
+pb_status pb_server_autotune(pb_server *server, int timeout_ms, pb_server_tune_info *out);
+
 /* Kernel measurement of a running server.  Between begin and end the worker
  * launches each phase kernel on its own between CUDA events (slower, for
  * measurement) and sums, per kind of launch, the device time and the

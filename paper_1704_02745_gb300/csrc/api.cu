@@ -219,7 +219,25 @@ void pb_apply_plan(pb_grid *g, const KernelGrid &kg, bool batch, int tiles_x, in
   g->n_ch = (int)((rows + g->rows_per_chunk - 1) / g->rows_per_chunk);
 }
 
+void pb_batch_plan_grid(pb_grid *g, const KernelGrid &kg, int min_planes, int height_pct) {
+  const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
+  const int tiles_x = (nx + WMAX - 1) / WMAX;
+  const int W = round_up((nx + tiles_x - 1) / tiles_x, NV);
+  const int hmax = std::min(HMAX, TILE_NODES / W);
+  const int h = std::max(1, (hmax * std::max(1, std::min(height_pct, 100)) + 50) / 100);
+  const int tiles_y = (ny + h - 1) / h;
+  const int cols = tiles_x * tiles_y;
+  const int resident = std::max(kg.stencil_blocks, 2 * g->ctx->num_sms);
+  int zc = std::max(1, resident / cols);
+  zc = std::min(zc, std::max(1, nz / std::max(1, min_planes)));
+  pb_apply_plan(g, kg, true, tiles_x, (ny + tiles_y - 1) / tiles_y, zc);
+}
+
 void pb_tile_plan(pb_grid *g, const KernelGrid &kg, bool batch) {
+  if (batch) {
+    pb_batch_plan_grid(g, kg, 32, 100);
+    return;
+  }
   const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
   const int tiles_x = (nx + WMAX - 1) / WMAX;
   const int W = round_up((nx + tiles_x - 1) / tiles_x, NV);
@@ -701,6 +719,7 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
     KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms, true);
     kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
     kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
+    kg.fast = !g->d.periodic;
     Batch B = pb_single_batch(g);
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -731,6 +750,7 @@ static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, p
   KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms, true);
   kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
   kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
+  kg.fast = !g->d.periodic;
   Batch B = pb_single_batch(g);
   Scal *hs = g->ctx->host_scal;
   cudaEvent_t e0, e1;
@@ -851,6 +871,7 @@ extern "C" pb_status pb_grid_autotune(pb_grid *g, int precision, pb_tune_info *i
     KernelGrid kg = kernel_grid(mode, coef, sms, true);
     kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
     kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
+    kg.fast = !g->d.periodic;
     const Batch B = pb_single_batch(g);
     std::vector<float> t;
     for (int rep = 0; rep < 4; rep++) {

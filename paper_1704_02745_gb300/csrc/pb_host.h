@@ -7,6 +7,7 @@
 #include "pb.h"
 #include "pb_internal.cuh"
 #include "setup.cuh"
+#include "solve.cuh"
 
 struct pb_ctx {
   int device = 0;
@@ -80,6 +81,10 @@ pb_status pb_check_atoms(int n_atoms, const double *xyz, const double *q, const 
 pb_status pb_gmg_solve(pb_grid *g, const pb_solve_opts *o, double *phi, pb_solve_info *info);
 void pb_mg_release(struct pb_mg *m);
 pb_status pb_grid_create(pb_ctx *ctx, const pb_grid_desc *desc, bool batch, pb_grid **out);
+// Tile plan of a server grid: fewest x tiles, height_pct percent of the
+// tallest tile height, z chunks of at least min_planes planes filling the
+// resident stencil CTAs of kg.
+void pb_batch_plan_grid(pb_grid *g, const pb::KernelGrid &kg, int min_planes, int height_pct);
 // st: the stream of the setup work (NULL: the grid's context stream)
 pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double *q,
                        const double *radius, bool sync, cudaStream_t st = nullptr);

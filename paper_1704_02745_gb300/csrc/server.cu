@@ -224,6 +224,13 @@ struct pb_server {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   KernelGrid kg{};
   std::string worker_error;
+  // tile plan of the batch (pb_server_set_plan, pb_server_autotune)
+  pb_batch_plan plan{32, 100, 3};
+  pb_batch_plan plan_next{32, 100, 3};  // requested, applied by the worker (under mu)
+  bool plan_requested = false;
+  int tune_state = 0;                   // 0 idle, 1 requested, 2 done (under mu)
+  pb_server_tune_info tune_out{};
+  std::condition_variable cv_tune;
 };
 
 namespace {
@@ -347,6 +354,7 @@ std::vector<int> admit(pb_server *s) {
           g = nullptr;
           return false;
         }
+        pb_batch_plan_grid(g, s->kg, s->plan.min_planes, s->plan.height_pct);
         return true;
       };
       if (!create()) {
@@ -429,6 +437,21 @@ std::vector<int> admit(pb_server *s) {
   return started;
 }
 
+// Kernel grid of the batch for a plan's stencil occupancy (the two builds of
+// the FP32 packed stencil pass: three or two CTAs per SM).
+KernelGrid batch_kernel_grid(const pb_server *s, const pb_batch_plan &P) {
+  KernelGrid kg = kernel_grid(s->mode, s->coef, s->ctx->num_sms, P.occupancy == 2);
+  kg.tile_update = 1;
+  return kg;
+}
+
+// Re-plan every resident grid (between graph launches: the tile plan holds no
+// state across launches).
+void replan_all(pb_server *s) {
+  for (auto &sl : s->slots)
+    if (sl.g) pb_batch_plan_grid(sl.g, s->kg, s->plan.min_planes, s->plan.height_pct);
+}
+
 // Upload the descriptors, work lists and partial offsets of the active grids.
 // Host staging capacity for n items (pinned; the set is idle when called).
 bool stage_items(Stage &st, size_t n) {
@@ -463,6 +486,13 @@ bool rebuild_batch(pb_server *s, Stage &sg, bool *graph_stale) {
     for (int t = 0; t < g->n_st; t++) st.push_back(Item{j, t});
     st_off += g->n_st;
     hi = j + 1;
+  }
+  // the fast builds of the tile passes serve a batch with no grid that wraps
+  bool fast = s->mode != MODE_F64 && s->coef == COEF_PACKED;
+  for (int j : active) fast = fast && !s->slots[j].g->d.periodic;
+  if (s->kg.fast != (fast ? 1 : 0)) {
+    s->kg.fast = fast ? 1 : 0;
+    *graph_stale = true;
   }
   // descriptors of slots [0, hi): the idle ones among them are never read
   if (hi > 0) {
@@ -709,7 +739,8 @@ double launch_bytes(pb_server *s, const std::vector<int> &active, int which) {
 
 // Measurement ticks: each kernel on its own between events, phases read
 // before each launch.
-bool run_profiled(pb_server *s, const std::vector<int> &active) {
+bool run_profiled(pb_server *s, const std::vector<int> &active, pb_kernel_profile &prof,
+                  int ticks) {
   Batch B;
   B.inst = s->d_inst;
   B.st_items = s->d_st;
@@ -723,7 +754,7 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
   B.ch_part = nullptr;
   B.error = s->d_err;
   const int hi = *std::max_element(active.begin(), active.end()) + 1;
-  for (int t = 0; t < 3 * s->ticks; t++) {
+  for (int t = 0; t < 3 * ticks; t++) {
     const int which = t % 3 == 0 ? 4 : t % 3 == 1 ? 1 : 2;
     cudaMemcpyAsync(s->h_scal, s->d_scal, hi * sizeof(Scal), cudaMemcpyDeviceToHost, s->stream);
     if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "profile")) return false;
@@ -738,19 +769,85 @@ bool run_profiled(pb_server *s, const std::vector<int> &active) {
     s->ctx->stats->launches += 1;
     if (bytes <= 0) continue;  // nothing of this kind was active
     if (which == 4) {
-      s->prof.ms_resid += ms;
-      s->prof.bytes_resid += bytes;
-      s->prof.launches_resid++;
+      prof.ms_resid += ms;
+      prof.bytes_resid += bytes;
+      prof.launches_resid++;
     } else if (which == 1) {
-      s->prof.ms_stencil += ms;
-      s->prof.bytes_stencil += bytes;
-      s->prof.launches_stencil++;
+      prof.ms_stencil += ms;
+      prof.bytes_stencil += bytes;
+      prof.launches_stencil++;
     } else {
-      s->prof.ms_update += ms;
-      s->prof.bytes_update += bytes;
-      s->prof.launches_update++;
+      prof.ms_update += ms;
+      prof.bytes_update += bytes;
+      prof.launches_update++;
     }
   }
+  return true;
+}
+
+// The batch autotuner: time the stencil and update passes of candidate plans
+// on the live batch (each applied to all active grids, two ticks each; the
+// four fastest again with three ticks), keep the fastest.  Runs between
+// graph launches in the worker; the solves advance during the timed ticks.
+bool tune_batch(pb_server *s, Stage &sg, const std::vector<int> &active, bool *graph_stale) {
+  std::vector<pb_batch_plan> cand{s->plan};
+  for (int occ : {3, 2})
+    for (int hp : {100, 67})
+      for (int mp : {16, 32, 64, 128, 1 << 20}) {
+        const pb_batch_plan c{mp, hp, occ};
+        bool dup = false;
+        for (const auto &x : cand)
+          dup |= x.min_planes == c.min_planes && x.height_pct == c.height_pct && x.occupancy == c.occupancy;
+        if (!dup) cand.push_back(c);
+      }
+  auto measure = [&](const pb_batch_plan &c, int ticks, double *gbs) -> bool {
+    if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "tune")) return false;
+    s->plan = c;
+    s->kg = batch_kernel_grid(s, c);
+    replan_all(s);
+    if (!rebuild_batch(s, sg, graph_stale)) return false;
+    pb_kernel_profile p{};
+    if (!run_profiled(s, active, p, ticks)) return false;
+    const double ms = p.ms_stencil + p.ms_update, b = p.bytes_stencil + p.bytes_update;
+    *gbs = ms > 0 ? b / ms / 1e6 : 0.0;
+    return true;
+  };
+  std::vector<double> score(cand.size(), 0.0);
+  for (size_t k = 0; k < cand.size(); k++)
+    if (!measure(cand[k], 2, &score[k])) return false;
+  const double first_default = score[0];
+  std::vector<size_t> order(cand.size());
+  for (size_t k = 0; k < order.size(); k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return score[a] > score[b]; });
+  // the four fastest, and the default, timed again: the kept plan is the
+  // fastest of these second timings
+  std::vector<size_t> again(order.begin(), order.begin() + std::min<size_t>(4, order.size()));
+  if (std::find(again.begin(), again.end(), (size_t)0) == again.end()) again.push_back(0);
+  size_t best = 0;
+  double best_gbs = -1, default_gbs = first_default;
+  for (size_t k : again) {
+    double g = 0;
+    if (!measure(cand[k], 3, &g)) return false;
+    if (k == 0) default_gbs = g;
+    if (g > best_gbs) {
+      best_gbs = g;
+      best = k;
+    }
+  }
+  if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "tune")) return false;
+  s->plan = cand[best];
+  s->kg = batch_kernel_grid(s, s->plan);
+  replan_all(s);
+  *graph_stale = true;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->tune_out.plan = s->plan;
+  s->tune_out.candidates = (int)cand.size();
+  s->tune_out.gbs_default = default_gbs;
+  s->tune_out.gbs_best = best_gbs;
+  s->plan_next = s->plan;
+  s->plan_requested = false;
+  s->tune_state = 2;
+  s->cv_tune.notify_all();
   return true;
 }
 
@@ -857,10 +954,32 @@ void worker_main(pb_server *s) {
       for (auto &x : s->slots)
         if (x.g) { s->n_resident++; s->bytes_resident += x.bytes; }
     }
+    // a plan set by pb_server_set_plan, or the autotuner on this batch
+    bool want_plan = false, want_tune = false;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      want_plan = s->plan_requested;
+      want_tune = s->tune_state == 1 && !active.empty();
+      if (want_plan) {
+        s->plan = s->plan_next;
+        s->plan_requested = false;
+      }
+    }
+    if (want_plan) {
+      if (!cuda_ok(cudaStreamSynchronize(s->stream), s, "plan")) break;
+      s->kg = batch_kernel_grid(s, s->plan);
+      replan_all(s);
+      graph_stale = true;
+      if (!active.empty() && !rebuild_batch(s, sg, &graph_stale)) break;
+    }
+    if (want_tune) {
+      if (!tune_batch(s, sg, active, &graph_stale)) break;
+      if (!rebuild_batch(s, sg, &graph_stale)) break;
+    }
     bool ran = false;
     if (!active.empty()) {
       if (s->profiling.load()) {
-        if (!run_profiled(s, active)) break;
+        if (!run_profiled(s, active, s->prof, s->ticks)) break;
       } else {
         if (!run_graph(s, graph_stale)) break;
         graph_stale = false;
@@ -939,6 +1058,7 @@ void worker_main(pb_server *s) {
     }
   s->stop = true;
   s->cv_done.notify_all();
+  s->cv_tune.notify_all();
 }
 
 }  // namespace
@@ -1192,6 +1312,37 @@ extern "C" pb_status pb_server_stats(pb_server *s, int *queued, int *active, int
   if (resident) *resident = s->n_resident;
   if (bytes) *bytes = s->bytes_resident;
   if (completed) *completed = s->completed;
+  return PB_OK;
+}
+
+extern "C" pb_status pb_server_set_plan(pb_server *s, const pb_batch_plan *plan) {
+  if (!s || !plan) return pb_fail(PB_ERR_ARG, "pb_server_set_plan: NULL argument");
+  if (plan->min_planes < 1 || plan->height_pct < 1 || plan->height_pct > 100 ||
+      (plan->occupancy != 2 && plan->occupancy != 3))
+    return pb_fail(PB_ERR_ARG, "pb_server_set_plan: min_planes >= 1, height_pct 1..100, occupancy 2 or 3");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->plan_next = *plan;
+  s->plan_requested = true;
+  s->cv_work.notify_all();
+  return PB_OK;
+}
+
+extern "C" pb_status pb_server_autotune(pb_server *s, int timeout_ms, pb_server_tune_info *out) {
+  if (!s) return pb_fail(PB_ERR_ARG, "pb_server_autotune: NULL server");
+  if (out) memset(out, 0, sizeof(*out));
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->stop) return pb_fail(PB_ERR_CUDA, "server stopped: " + s->worker_error);
+  s->tune_state = 1;
+  s->cv_work.notify_all();
+  auto done = [&] { return s->tune_state == 2 || s->stop; };
+  if (timeout_ms < 0) s->cv_tune.wait(lk, done);
+  else s->cv_tune.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
+  if (s->tune_state != 2) {
+    if (s->stop) return pb_fail(PB_ERR_CUDA, "server stopped: " + s->worker_error);
+    return pb_fail(PB_ERR_TIMEOUT, "no batch has been tuned yet (the tuning runs once solves are active)");
+  }
+  if (out) *out = s->tune_out;
+  s->tune_state = 0;
   return PB_OK;
 }
 

@@ -91,8 +91,12 @@ constexpr int CG_RING_PLANES = 3;  // p planes with halo held by a CG stencil pa
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
+  while (!mbar_try_wait(bar, parity)) {
+#ifdef PB_WAIT_SLEEP_NS
+    __nanosleep(PB_WAIT_SLEEP_NS);
+#endif
     if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
   return true;
 }
 
@@ -562,6 +566,12 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
   v1 = UPD ? (double)rr : 0.0;
 }
 
+}  // namespace pb
+
+#include "fastpath.cuh"
+
+namespace pb {
+
 // RESID phase (FP64, plain loads): fold the deferred update, true residual,
 // new inner right-hand side.  Same groups of NV nodes per thread, z pieces of
 // I.rtz planes.  GB300 runs FP64 arithmetic at a small fraction of its FP32
@@ -780,6 +790,12 @@ constexpr int RING_CELLS = max_ring_cells();
 __host__ __device__ constexpr size_t ring_bytes(size_t es, int planes = 3) {
   return ((size_t)planes * RING_CELLS * es + 127) / 128 * 128;
 }
+// The fast tile passes (fastpath.cuh) for FP32 packed grids without wrap, in
+// kernels of their own (FAST = true) that the host launches when no grid of
+// the launch needs wrap; 0 keeps every launch on the general cg_tile.
+#ifndef PB_FASTPATH
+#define PB_FASTPATH 1
+#endif
 // Stencil pass configurations: TMA pipeline depth in z planes, and resident
 // CTAs per SM the register budget targets.  The FP32 packed-code pass (the one
 // of served and refined solves) runs three CTAs of 256 threads per SM over a
@@ -820,6 +836,12 @@ template <typename T, int CM> struct UpdCfg {
   static constexpr int stages = lean ? PB_STAGES_UPD : StencilCfg<T, CM, 0>::stages;
   static constexpr int minb = lean ? PB_MINB_UPD : StencilCfg<T, CM, 0>::minb;
 };
+// The fast update pass holds no ring: six stages (four planes ahead of the
+// one it forms) in the shared memory of three CTAs per SM; four measured 3%
+// slower.
+#ifndef PB_STAGES_UPD_FAST
+#define PB_STAGES_UPD_FAST 6
+#endif
 
 // Diagonal of the operator of precision T by code byte (shared memory).
 template <typename T>
@@ -856,9 +878,10 @@ __device__ __forceinline__ void leave_items(unsigned *next, unsigned *done) {
 // then beta and the stop test).  Work counters 0/1 (pass 0) or 2/3 (pass 1);
 // the tile partials of both passes share st_part (pass 1 starts after pass 0
 // has finished with them).
-template <typename T, int CM, int PASS, int G>
+template <typename T, int CM, int PASS, int G, bool FAST>
 __device__ __forceinline__ void cg_pass(const Batch &B) {
-  constexpr int NS = PASS == 1 ? UpdCfg<T, CM>::stages : StencilCfg<T, CM, G>::stages;
+  constexpr int NS = PASS == 1 ? (FAST ? PB_STAGES_UPD_FAST : UpdCfg<T, CM>::stages)
+                               : StencilCfg<T, CM, G>::stages;
   constexpr bool UPD = PASS == 1;
   extern __shared__ __align__(128) uint8_t dyn[];
   __shared__ __align__(8) uint64_t full[NS];
@@ -871,7 +894,7 @@ __device__ __forceinline__ void cg_pass(const Batch &B) {
   // the ring of p planes, then the stages.
   uint8_t *base = (uint8_t *)(((uintptr_t)dyn + 127) & ~(uintptr_t)127);
   T *ring = (T *)base;
-  uint8_t *stages = base + ring_bytes(sizeof(T), CG_RING_PLANES);
+  uint8_t *stages = FAST && UPD ? base : base + ring_bytes(sizeof(T), CG_RING_PLANES);
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; s++) mbar_init(&full[s], 1);
     mbar_fence_init();
@@ -902,8 +925,20 @@ __device__ __forceinline__ void cg_pass(const Batch &B) {
     const int ph = s_phase;
     if (ph == PH_INNER || (!UPD && ph == PH_START)) {
       const TileScal S = tile_scal(Sp);
-      double v0, v1;
-      cg_tile<T, CM, NS, PASS>(I, S, item.tile, stages, ring, dtab, mtab, full, SR, abort, v0, v1);
+      double v0 = 0.0, v1 = 0.0;
+      if constexpr (FAST) {  // FP32, packed codes, no wrap (checked by the host)
+        if constexpr (UPD) {
+          fast_update<NS>(I, S, item.tile, stages, (const Pair<float> *)mtab, full, SR, abort, v0, v1);
+        } else if (S.phase == PH_START) {
+          fast_stencil<NS, true>(I, S, item.tile, stages, (float *)ring, (const float *)dtab, full, SR,
+                                 abort, v0);
+        } else {
+          fast_stencil<NS, false>(I, S, item.tile, stages, (float *)ring, (const float *)dtab, full,
+                                  SR, abort, v0);
+        }
+      } else {
+        cg_tile<T, CM, NS, PASS>(I, S, item.tile, stages, ring, dtab, mtab, full, SR, abort, v0, v1);
+      }
       if (abort) {
         if (threadIdx.x == 0) atomicOr(B.error, 2);  // a pipeline wait timed out
         break;
@@ -936,13 +971,13 @@ __device__ __forceinline__ void cg_pass(const Batch &B) {
   if (threadIdx.x == 0) leave_items(next, done);
 }
 
-template <typename T, int CM, int G>
+template <typename T, int CM, int G, bool FAST = false>
 __global__ void __launch_bounds__(NT, StencilCfg<T, CM, G>::minb) k_stencil(Batch B) {
-  cg_pass<T, CM, 0, G>(B);
+  cg_pass<T, CM, 0, G, FAST>(B);
 }
-template <typename T, int CM>
+template <typename T, int CM, bool FAST = false>
 __global__ void __launch_bounds__(NT, UpdCfg<T, CM>::minb) k_update_tile(Batch B) {
-  cg_pass<T, CM, 1, 0>(B);
+  cg_pass<T, CM, 1, 0, FAST>(B);
 }
 
 // RESID pass of the instances that asked for one (FP64, plain loads).  Its
@@ -1187,6 +1222,9 @@ static size_t update_smem() {  // ring + compact stages of the tile update pass
   return 128 + ring_bytes(sizeof(T), CG_RING_PLANES) +
          (size_t)UpdCfg<T, CM>::stages * max_stage_bytes_upd(sizeof(T));
 }
+static size_t update_smem_fast() {  // the fast update pass: stages only
+  return 128 + (size_t)PB_STAGES_UPD_FAST * max_stage_bytes_upd(sizeof(float));
+}
 static size_t resid_smem() { return 128 + ring_bytes(sizeof(double)); }
 
 
@@ -1213,20 +1251,31 @@ template <typename T, int CM>
 static cudaError_t phase_impl(const Batch &B, const KernelGrid &kg, int which, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (which & 4) e = launch_pdl(k_resid<T, CM>, kg.resid_blocks, NT, resid_smem(), st, B);
+  constexpr bool can_fast = PB_FASTPATH && StencilCfg<T, CM, 0>::lean;
+  const bool fast = can_fast && kg.fast;
   if (e == cudaSuccess && (which & 1)) {
-    if constexpr (StencilCfg<T, CM, 0>::lean) {
+    if constexpr (can_fast) {
       if (kg.single)
-        e = launch_pdl(k_stencil<T, CM, 1>, kg.stencil_blocks, NT, stencil_smem<T, CM, 1>(), st, B);
+        e = fast ? launch_pdl(k_stencil<T, CM, 1, true>, kg.stencil_blocks, NT, stencil_smem<T, CM, 1>(), st, B)
+                 : launch_pdl(k_stencil<T, CM, 1>, kg.stencil_blocks, NT, stencil_smem<T, CM, 1>(), st, B);
       else
-        e = launch_pdl(k_stencil<T, CM, 0>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B);
+        e = fast ? launch_pdl(k_stencil<T, CM, 0, true>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B)
+                 : launch_pdl(k_stencil<T, CM, 0>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B);
     } else {
       e = launch_pdl(k_stencil<T, CM, 0>, kg.stencil_blocks, NT, stencil_smem<T, CM, 0>(), st, B);
     }
   }
-  if (e == cudaSuccess && (which & 2))
-    e = kg.tile_update
-            ? launch_pdl(k_update_tile<T, CM>, kg.update_tile_blocks, NT, update_smem<T, CM>(), st, B)
-            : launch_pdl(k_update<T, CM>, kg.update_blocks, NT_UPD, 0, st, B);
+  if (e == cudaSuccess && (which & 2)) {
+    if (!kg.tile_update) {
+      e = launch_pdl(k_update<T, CM>, kg.update_blocks, NT_UPD, 0, st, B);
+    } else {
+      if constexpr (can_fast)
+        e = fast ? launch_pdl(k_update_tile<T, CM, true>, kg.update_fast_blocks, NT, update_smem_fast(), st, B)
+                 : launch_pdl(k_update_tile<T, CM>, kg.update_tile_blocks, NT, update_smem<T, CM>(), st, B);
+      else
+        e = launch_pdl(k_update_tile<T, CM>, kg.update_tile_blocks, NT, update_smem<T, CM>(), st, B);
+    }
+  }
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1246,7 +1295,7 @@ cudaError_t launch_tick(const Batch &B, int mode, int coef, const KernelGrid &kg
 }
 
 template <typename T, int CM>
-static void occ(int &s, int &u, int &r, int &ut, bool single) {
+static void occ(int &s, int &u, int &r, int &ut, int &uf, bool single) {
   const size_t sm = stencil_smem<T, CM, 0>(), rm = resid_smem();
   cudaFuncSetAttribute(k_stencil<T, CM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_update_tile<T, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1256,6 +1305,13 @@ static void occ(int &s, int &u, int &r, int &ut, bool single) {
   if constexpr (StencilCfg<T, CM, 0>::lean) {
     const size_t sm1 = stencil_smem<T, CM, 1>();
     cudaFuncSetAttribute(k_stencil<T, CM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if constexpr (PB_FASTPATH) {  // the fast builds: the same launch bounds and shared memory
+      cudaFuncSetAttribute(k_stencil<T, CM, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_stencil<T, CM, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+      cudaFuncSetAttribute(k_update_tile<T, CM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)update_smem_fast());
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&uf, k_update_tile<T, CM, true>, NT, update_smem_fast());
+    }
     if (single) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM, 1>, NT, sm1);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s, k_stencil<T, CM, 0>, NT, sm);
   } else {
@@ -1266,13 +1322,13 @@ static void occ(int &s, int &u, int &r, int &ut, bool single) {
 }
 
 KernelGrid kernel_grid(int mode, int coef, int num_sms, bool single) {
-  int s = 1, u = 1, r = 1, ut = 1;
+  int s = 1, u = 1, r = 1, ut = 1, uf = 1;
   if (mode == MODE_F64) {
-    if (coef == COEF_F64) occ<double, COEF_F64>(s, u, r, ut, single);
-    else occ<double, COEF_PACKED>(s, u, r, ut, single);
-  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u, r, ut, single);
-  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u, r, ut, single);
-  else occ<float, COEF_PACKED>(s, u, r, ut, single);
+    if (coef == COEF_F64) occ<double, COEF_F64>(s, u, r, ut, uf, single);
+    else occ<double, COEF_PACKED>(s, u, r, ut, uf, single);
+  } else if (coef == COEF_F32) occ<float, COEF_F32>(s, u, r, ut, uf, single);
+  else if (coef == COEF_BF16) occ<float, COEF_BF16>(s, u, r, ut, uf, single);
+  else occ<float, COEF_PACKED>(s, u, r, ut, uf, single);
   KernelGrid kg;
   kg.stencil_per_sm = s > 0 ? s : 1;
   kg.update_per_sm = u > 0 ? u : 1;
@@ -1280,8 +1336,10 @@ KernelGrid kernel_grid(int mode, int coef, int num_sms, bool single) {
   kg.update_blocks = num_sms * kg.update_per_sm;
   kg.resid_blocks = num_sms * (r > 0 ? r : 1);
   kg.update_tile_blocks = num_sms * (ut > 0 ? ut : 1);
+  kg.update_fast_blocks = num_sms * (uf > 0 ? uf : 1);
   kg.tile_update = 0;
   kg.single = single ? 1 : 0;
+  kg.fast = 0;
   return kg;
 }
 

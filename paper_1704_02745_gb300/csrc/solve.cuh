@@ -7,10 +7,13 @@ namespace pb {
 
 struct KernelGrid {  // persistent grid sizes of the phase kernels
   int stencil_blocks, update_blocks, resid_blocks, update_tile_blocks;
+  int update_fast_blocks;  // the fast build of the tile update pass
   int stencil_per_sm, update_per_sm;  // resident CTAs per SM
   int tile_update;  // 1: the update pass runs over the stencil tiles and forms Ap
                     // again (k_update_tile; the stencil pass stores no Ap, Inst.ap
                     // is NULL); 0: over row chunks, reading the stored Ap (k_update)
+  int fast;         // 1: every grid of the launch is FP32 with packed codes and no wrap:
+                    // the stencil and tile update passes run their fast builds
   int single;       // 1: launches over one grid (the lean stencil pass then runs its
                     // single-grid configuration)
 };

@@ -111,6 +111,22 @@ class KernelProfile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("min_planes", ctypes.c_int), ("height_pct", ctypes.c_int), ("occupancy", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerTuneInfo(ctypes.Structure):
+    _fields_ = [("plan", BatchPlan), ("candidates", ctypes.c_int), ("gbs_default", ctypes.c_double),
+                ("gbs_best", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"plan": self.plan.as_dict(), "candidates": self.candidates,
+                "gbs_default": self.gbs_default, "gbs_best": self.gbs_best}
+
+
 class AluRates(ctypes.Structure):
     _fields_ = [("fp64_fma_per_s", ctypes.c_double), ("fp32_fma_per_s", ctypes.c_double),
                 ("sms", ctypes.c_int), ("sm_max_mhz", ctypes.c_double)]
@@ -163,6 +179,10 @@ def load(path: str = LIB_PATH):
     lib.pb_server_destroy.argtypes = [_P]
     lib.pb_batch_submit.argtypes = [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     lib.pb_batch_poll.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result)]
+    lib.pb_server_set_plan.restype = ctypes.c_int
+    lib.pb_server_set_plan.argtypes = [_P, ctypes.POINTER(BatchPlan)]
+    lib.pb_server_autotune.restype = ctypes.c_int
+    lib.pb_server_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ServerTuneInfo)]
     lib.pb_batch_cancel.restype = ctypes.c_int
     lib.pb_batch_cancel.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
     lib.pb_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -580,6 +600,18 @@ class Server:
 
     def stats(self):
         return pb_server_stats(self.handle)
+
+    def set_plan(self, min_planes: int = 32, height_pct: int = 100, occupancy: int = 3):
+        """pb_server_set_plan: the batch's tile plan from the next round on."""
+        p = BatchPlan(min_planes, height_pct, occupancy)
+        _check(load().pb_server_set_plan(_P(self.handle), ctypes.byref(p)))
+
+    def autotune(self, timeout_ms: int = -1) -> ServerTuneInfo:
+        """pb_server_autotune: tune the batch's tile plan on the live batch
+        (waits until solves are active and the tuning has run)."""
+        out = ServerTuneInfo()
+        _check(load().pb_server_autotune(_P(self.handle), timeout_ms, ctypes.byref(out)))
+        return out
 
     def cancel(self, ticket: int) -> bool:
         """pb_batch_cancel: True if the request was cancelled."""
