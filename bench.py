@@ -77,9 +77,11 @@ def bytes_per_node(coef):
 # device) summarised in profiles/: (bytes per node, the summary it comes from).
 # None where no such capture of the current kernel exists.
 NCU_TRAFFIC_PER_NODE = {
-    "stencil_batch": None,
-    # k_stencil<float, packed, single grid> on 257^3, one launch: 407.0 MB / 16,974,593 nodes
-    "stencil_grid": (407.018e6 / 16974593, "profiles/k_stencil_globule257.md"),
+    # k_stencil<float, packed, batch, fast>, launches 40-41 of the batch256 kernel-profile window:
+    # (3.2555 + 1.7578 + 3.2563 + 1.7551) GB / (2 x 214,261,784 nodes)
+    "stencil_batch": (10.024756736e9 / 428523568, "profiles/k_stencil_batch256.md"),
+    # the single-grid build has no capture of its current (fast) kernel
+    "stencil_grid": None,
 }
 # FP64 operations per grid node of the residual pass: x + d (1), the operator
 # diag x - sum of six eps x_nb (1 multiply, 6 multiply-adds), b - A x (1).
@@ -408,7 +410,7 @@ def run_serving(args):
     # plain FP64, one at a time: its capacity, measured on the first requests
     # of the Poisson stream's request list (after one untimed solve of each
     # trajectory's grid, so that grid creation is not timed)
-    pois_reqs = Stream(seed=5, req_seed=77 + rank).take(args.stream_requests)
+    pois_reqs = Stream(seed=5, req_seed=77 + rank).take(max(args.stream_requests, per_step))
     plain = PlainFP64(pb, ctx, torch)
     seen = set()
     for k, g, a in pois_reqs:
@@ -433,7 +435,7 @@ def run_serving(args):
     n_pois = args.stream_requests
     n_low = min(args.stream_requests_low, n_pois)
     served_cap = args.steps * per_step / total  # this rank's closed-loop rate
-    gaps = np.random.default_rng([17, rank]).exponential(1.0, n_pois)
+    gaps = np.random.default_rng([17, rank]).exponential(1.0, max(n_pois, 1))
     gap_sum = np.cumsum(gaps) - gaps[0]
 
     def served_stream_lat(reqs, arrivals):
@@ -471,7 +473,7 @@ def run_serving(args):
                 "max_ms": max(ms)}
 
     runs = []
-    for label, rate, n, both in (("0.5x served capacity", 0.5 * served_cap, n_pois, False),
+    for label, rate, n, both in () if n_pois == 0 else (("0.5x served capacity", 0.5 * served_cap, n_pois, False),
                                  ("0.8x served capacity", 0.8 * served_cap, n_pois, False),
                                  ("1.0x served capacity", 1.0 * served_cap, n_pois, False),
                                  ("1.5x plain capacity", 1.5 * plain_rate, n_pois, True),
@@ -550,7 +552,8 @@ def run_serving(args):
                      "traffic": None if trf is None else trf[0] * kp.bytes_stencil / BYTES_PER_NODE["stencil"] /
                      max(kp.launches_stencil, 1),
                      "traffic_source": None if trf is None else (
-                         f"DRAM bytes per node from {trf[1]}, scaled by the nodes of this run's launches"),
+                         f"scaled from {trf[1]}: DRAM bytes per node of two bounded captures on the "
+                         f"256-snapshot batch, times the nodes of this run's launches"),
                      "bytes_per_launch": kp.bytes_stencil / max(kp.launches_stencil, 1),
                      "bytes_per_node": BYTES_PER_NODE["stencil"], "launch_ms": t_st * 1e3,
                      "launches": kp.launches_stencil,
@@ -957,9 +960,15 @@ def run_batch(args):
     e2e_wall, _, _ = serve_steps(srv, [reqs] * max(1, args.steps // 2), want_phi=True)
     e1 = ctx.stats()
     e2e_steps = max(1, args.steps // 2)
+    torch.cuda.synchronize()
+    if args.ncu_window:  # the server is idle: the first stencil launches inside are profiled ones
+        torch.cuda.profiler.start()
     srv.profile_begin()
     serve_steps(srv, [reqs] * 3)  # steady state, as in the timed loop
     kp = srv.profile_end()
+    if args.ncu_window:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     srv.close()
     if rank != 0:
         ctx.close()
@@ -987,7 +996,13 @@ def run_batch(args):
             p.grid.n * r.info.iterations for p, r in zip(snaps * args.steps, res)) / args.steps / total,
         "roofline": {"bound": "hbm", "kernel": "k_stencil<float,packed>: batched stencil pass",
                      "achieved": ach_st, "peak": hbm, "unit": "GB/s", "frac": ach_st / hbm,
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "traffic": (None if NCU_TRAFFIC_PER_NODE["stencil_batch"] is None else
+                                 NCU_TRAFFIC_PER_NODE["stencil_batch"][0] * kp.bytes_stencil /
+                                 BYTES_PER_NODE["stencil"] / max(kp.launches_stencil, 1)),
+                     "traffic_source": (None if NCU_TRAFFIC_PER_NODE["stencil_batch"] is None else
+                                        f"scaled from {NCU_TRAFFIC_PER_NODE['stencil_batch'][1]} "
+                                        f"(bounded captures of this workload's kernel)"),
                      "bytes_per_node": BYTES_PER_NODE["stencil"],
                      "launch_ms": kp.ms_stencil / max(kp.launches_stencil, 1),
                      "launches": kp.launches_stencil,
@@ -995,7 +1010,12 @@ def run_batch(args):
                                      "launch_ms": kp.ms_update / max(kp.launches_update, 1),
                                      "launches": kp.launches_update},
                      "resid_pass": {"launch_ms": kp.ms_resid / max(kp.launches_resid, 1),
-                                    "launches": kp.launches_resid}},
+                                    "launches": kp.launches_resid},
+                     "capture_window": {
+                         "first_bytes_stencil": list(kp.first_bytes_stencil)[:kp.first_stencil],
+                         "first_bytes_update": list(kp.first_bytes_update)[:kp.first_update],
+                         "note": ("algorithmic bytes of the first stencil / update launches of the "
+                                  "profiled steps (--ncu-window brackets them for a counter capture)")}},
         "e2e": {"value": world * len(reqs) * e2e_steps / e2e_wall, "unit": "solves/s",
                 "h2d_bytes_per_step": int((e1[1] - e0[1]) / e2e_steps),
                 "d2h_bytes_per_step": int((e1[2] - e0[2]) / e2e_steps),
@@ -1036,6 +1056,9 @@ def main():
                     help="single-grid workloads: boundary dielectric (harmonic: weighted harmonic average)")
     ap.add_argument("--periodic", action="store_true",
                     help="single-grid workloads: periodic boundary instead of Debye-Hueckel")
+    ap.add_argument("--ncu-window", action="store_true",
+                    help="batch256: bracket the kernel-profile steps with cudaProfilerStart/Stop "
+                         "(for a bounded counter capture of their first launches)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")

@@ -418,6 +418,12 @@ typedef struct {
     int launches_stencil, launches_update;
     double ms_resid, bytes_resid;      /* residual-pass launches */
     int launches_resid;
+    /* the algorithmic bytes of the first 64 stencil-pass and update-pass
+     * launches between begin and end, in launch order, counting launches
+     * with no grid in their phase too (0 bytes), so that a counter capture
+     * of those same launches can be divided by the grid nodes they covered */
+    double first_bytes_stencil[64], first_bytes_update[64];
+    int first_stencil, first_update;   /* entries filled (at most 64) */
 } pb_kernel_profile;
 pb_status pb_server_profile_begin(pb_server *server);
 pb_status pb_server_profile_end(pb_server *server, pb_kernel_profile *out);

@@ -192,6 +192,11 @@ extern "C" pb_status pb_free_grid(pb_grid *g) {
 #ifndef PB_PLAN_PER_SM
 #define PB_PLAN_PER_SM 2
 #endif
+// Row chunks of the update pass per resident update CTA (taken dynamically;
+// 2 and 4 measured slower than one wave of one chunk each).
+#ifndef PB_UPD_CHUNKS_PER_CTA
+#define PB_UPD_CHUNKS_PER_CTA 1
+#endif
 // A tile plan given its x tiles, tile height and z chunks (clamped to what the
 // tiles allow); the residual pieces and update chunks follow from it.
 void pb_apply_plan(pb_grid *g, const KernelGrid &kg, bool batch, int tiles_x, int h, int zc) {
@@ -214,7 +219,8 @@ void pb_apply_plan(pb_grid *g, const KernelGrid &kg, bool batch, int tiles_x, in
   // update chunks: one wave of resident update CTAs on large grids, never
   // fewer than CH elements per chunk
   const long rows = (long)ny * nz;
-  const long by_count = (rows + kg.update_blocks - 1) / kg.update_blocks;
+  const long by_count = (rows + (long)PB_UPD_CHUNKS_PER_CTA * kg.update_blocks - 1) /
+                        ((long)PB_UPD_CHUNKS_PER_CTA * kg.update_blocks);
   g->rows_per_chunk = (int)std::max<long>(std::max(1, (batch ? 16 * CH : CH) / nx), by_count);
   g->n_ch = (int)((rows + g->rows_per_chunk - 1) / g->rows_per_chunk);
 }
@@ -700,6 +706,31 @@ Batch pb_single_batch(pb_grid *g) {
   return B;
 }
 
+// A single grid's update pass runs over row chunks, reading the Ap its
+// stencil pass stored.  The tile update pass (Ap formed again from p, 34 B
+// per node and iteration instead of 38; 1 here) is the faster form for a
+// server batch, but not on one grid: on 257^3 it measured 0.43-0.47 of
+// measured HBM against 0.64 for the row chunks, and the whole iteration
+// 156 us against 146 us.
+#ifndef PB_GRID_TILE_UPDATE
+#define PB_GRID_TILE_UPDATE 0
+#endif
+static bool grid_tile_update(const pb_grid *g, int mode, int coef) {
+  return PB_GRID_TILE_UPDATE && !g->d.periodic && mode != MODE_F64 && coef == COEF_PACKED;
+}
+static KernelGrid single_kernel_grid(const pb_grid *g, int mode, int coef) {
+  KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms, true);
+  kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
+  kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
+  kg.fast = !g->d.periodic;
+  if (grid_tile_update(g, mode, coef)) {
+    kg.tile_update = 1;
+    kg.update_tile_blocks = std::min(kg.update_tile_blocks, g->n_st);
+    kg.update_fast_blocks = std::min(kg.update_fast_blocks, g->n_st);
+  }
+  return kg;
+}
+
 static int auto_ticks(const pb_grid *g) {
   // enough work per host check that the poll is cheap, few enough that a
   // converged solve does not idle long
@@ -716,10 +747,7 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
       cudaGraphExecDestroy(g->graph);
       g->graph = nullptr;
     }
-    KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms, true);
-    kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
-    kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
-    kg.fast = !g->d.periodic;
+    const KernelGrid kg = single_kernel_grid(g, mode, coef);
     Batch B = pb_single_batch(g);
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -747,10 +775,7 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks) {
 // with a synchronisation after each so that its work kind is known.
 static pb_status profiled_loop(pb_grid *g, int mode, int coef, long max_ticks, pb_solve_info *info) {
   cudaStream_t s = g->ctx->stream;
-  KernelGrid kg = kernel_grid(mode, coef, g->ctx->num_sms, true);
-  kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
-  kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
-  kg.fast = !g->d.periodic;
+  const KernelGrid kg = single_kernel_grid(g, mode, coef);
   Batch B = pb_single_batch(g);
   Scal *hs = g->ctx->host_scal;
   cudaEvent_t e0, e1;
@@ -867,11 +892,9 @@ extern "C" pb_status pb_grid_autotune(pb_grid *g, int precision, pb_tune_info *i
     Inst I;
     pb_status r;
     if ((r = pb_make_inst(g, &o, mode, coef, I))) return r;
+    if (grid_tile_update(g, mode, coef)) I.ap = nullptr;  // as in the solves
     CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
-    KernelGrid kg = kernel_grid(mode, coef, sms, true);
-    kg.stencil_blocks = std::min(kg.stencil_blocks, g->n_st);
-    kg.update_blocks = std::min(kg.update_blocks, g->n_ch);
-    kg.fast = !g->d.periodic;
+    const KernelGrid kg = single_kernel_grid(g, mode, coef);
     const Batch B = pb_single_batch(g);
     std::vector<float> t;
     for (int rep = 0; rep < 4; rep++) {
@@ -946,6 +969,7 @@ extern "C" pb_status pb_pcg_solve(pb_grid *g, const pb_solve_opts *o, double *ph
   if (mode != MODE_F32_REFINE) oo.max_outer = 1;
   Inst I;
   if ((st = pb_make_inst(g, &oo, mode, coef, I))) return st;
+  if (grid_tile_update(g, mode, coef)) I.ap = nullptr;  // the update pass forms Ap again
   Scal S0 = pb_initial_scal(g->bnorm);
   CK(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, s));
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));

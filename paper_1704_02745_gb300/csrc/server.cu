@@ -767,6 +767,8 @@ bool run_profiled(pb_server *s, const std::vector<int> &active, pb_kernel_profil
     float ms = 0;
     cudaEventElapsedTime(&ms, s->ev0, s->ev1);
     s->ctx->stats->launches += 1;
+    if (which == 1 && prof.first_stencil < 64) prof.first_bytes_stencil[prof.first_stencil++] = bytes;
+    if (which == 2 && prof.first_update < 64) prof.first_bytes_update[prof.first_update++] = bytes;
     if (bytes <= 0) continue;  // nothing of this kind was active
     if (which == 4) {
       prof.ms_resid += ms;

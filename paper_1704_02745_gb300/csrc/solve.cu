@@ -803,10 +803,10 @@ __host__ __device__ constexpr size_t ring_bytes(size_t es, int planes = 3) {
 // loaded).  On a single grid (G = 1: about two tiles per SM) it runs two CTAs
 // per SM at most (its shared memory is padded so that a third does not fit):
 // with room for three, the CTA scheduler may stack three tiles on one SM
-// while another holds one, and the stacked SM sets the pace.  (Measured on a
-// 257^3 grid: 20 solves/s against 16 with three; four stages were slower
-// than three.)  The passes that also read coefficient arrays need more
-// registers; the FP64 pass is held to one CTA per SM by its shared memory.
+// while another holds one, and the stacked SM sets the pace.  Four stages
+// were slower than three.  The passes that also read coefficient arrays need
+// more registers; the FP64 pass is held to one CTA per SM by its shared
+// memory.
 #ifndef PB_STAGES_F32
 #define PB_STAGES_F32 3
 #endif
@@ -1207,6 +1207,11 @@ cudaError_t launch_start(const Inst *inst, const int *list, int n, int *resid_pe
 // ---------------------------------------------------------------------------
 // Host side
 
+// Shared memory of the single-grid stencil build at least this (80 KB: two
+// CTAs per SM at most).  On one 257^3 grid with the row-chunk update (the
+// stencil pass also stores Ap) two CTAs per SM ran the pass in 95 us, three
+// in 105 us; without the Ap store three would win (87 us), but the tile
+// update pass that this needs loses more on one grid than that.
 #ifndef PB_GRID_SMEM_MIN
 #define PB_GRID_SMEM_MIN (80 * 1024)
 #endif

@@ -105,10 +105,16 @@ class KernelProfile(ctypes.Structure):
                 ("ms_update", ctypes.c_double), ("bytes_update", ctypes.c_double),
                 ("launches_stencil", ctypes.c_int), ("launches_update", ctypes.c_int),
                 ("ms_resid", ctypes.c_double), ("bytes_resid", ctypes.c_double),
-                ("launches_resid", ctypes.c_int)]
+                ("launches_resid", ctypes.c_int),
+                ("first_bytes_stencil", ctypes.c_double * 64), ("first_bytes_update", ctypes.c_double * 64),
+                ("first_stencil", ctypes.c_int), ("first_update", ctypes.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if isinstance(v, ctypes.Array) else v
+        return d
 
 
 class BatchPlan(ctypes.Structure):
