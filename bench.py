@@ -80,8 +80,8 @@ NCU_TRAFFIC_PER_NODE = {
     # k_stencil<float, packed, batch, fast>, launches 40-41 of the batch256 kernel-profile window:
     # (3.2555 + 1.7578 + 3.2563 + 1.7551) GB / (2 x 214,261,784 nodes)
     "stencil_batch": (10.024756736e9 / 428523568, "profiles/k_stencil_batch256.md"),
-    # the single-grid build has no capture of its current (fast) kernel
-    "stencil_grid": None,
+    # k_stencil<float, packed, single grid, fast> on 257^3, one launch: 405.05 MB / 16,974,593 nodes
+    "stencil_grid": (405.05472e6 / 16974593, "profiles/k_stencil_globule257.md"),
 }
 # FP64 operations per grid node of the residual pass: x + d (1), the operator
 # diag x - sum of six eps x_nb (1 multiply, 6 multiply-adds), b - A x (1).
@@ -399,8 +399,10 @@ def run_serving(args):
         srv.close()
         ctx.close()
         return
-    # end to end: the same steady state with phi copied back to the host per request
-    e2e_steps = max(2, args.steps // 2)
+    # end to end: the same steady state with phi copied back to the host per request,
+    # as many steps as the timed phase (the requests differ; fewer steps sample grid
+    # sizes too unevenly to compare)
+    e2e_steps = max(2, args.steps)
     e2e_batches = [[(k, g.replace(dh="f32"), a) for k, g, a in stream.take(per_step)]
                    for _ in range(e2e_steps)]
     prewarm_pinned(pb, e2e_batches)
