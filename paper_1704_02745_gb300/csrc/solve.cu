@@ -42,7 +42,17 @@
 #include "pb_internal.cuh"
 #include "solve.cuh"
 
+// Explicit coefficient storage: a group's coefficients are requested before
+// the stage wait and CTA barrier of the iteration that uses them (FP32
+// arrays: the 257^3 stencil pass 153 -> 134 us), or just before use (BF16
+// arrays, where requesting them early measured slower: 141 -> 150 us; and
+// FP64).  PB_COEF_EARLY = 0 keeps every storage on the late form.
+#ifndef PB_COEF_EARLY
+#define PB_COEF_EARLY 1
+#endif
 namespace pb {
+template <int CM> struct CoefEarly { static constexpr bool value = PB_COEF_EARLY && CM == COEF_F32; };
+
 
 // ---------------------------------------------------------------------------
 // TMA / mbarrier primitives (inline PTX).
@@ -351,6 +361,15 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
   uint32_t st_issue = SR.st;
   for (int u = 0; u < min(NS, Q); ++u) st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
   for (int q = 0; q < Q; ++q) {
+    const int z = G.z0 - 1 + q;
+    // explicit storage: the coefficients of plane z-1 (computed in this
+    // iteration) are requested before the stage wait and the CTA barrier, so
+    // their latency overlaps both
+    GroupCoef<T> cpre;
+    if constexpr (CoefEarly<CM>::value) {
+      if (q >= 2 && G.vmask)
+        cpre = group_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0, z - 1, (G.vmask >> (NV - 1)) & 1u);
+    }
     const uint32_t st = SR.st;
 #ifdef PB_FAULT_TEST
     const bool ok = (q == 0 && threadIdx.x == 0 && fault_abandon_wait())
@@ -367,7 +386,6 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
     const T *sx = (const T *)(sb + off_x);
     T *rg = ring + rq * ring_plane;
     const int rq1 = rq == 0 ? CG_RING_PLANES - 1 : rq - 1;
-    const int z = G.z0 - 1 + q;
     Vec<T> pn = {}, zc = {};
     uint32_t codes = 0;
     // z and p_old are zero outside the grid (TMA fill, zero pads), and so is
@@ -492,10 +510,12 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
             }
           }
         } else {
-          // explicit storage: the group's coefficients by vector loads (pad
-          // lanes read the arrays' pads, and their Ap is zeroed below)
-          const GroupCoef<T> c = group_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0, z - 1,
-                                                   (G.vmask >> (NV - 1)) & 1u);
+          // explicit storage: the group's coefficients, requested at the top
+          // of the iteration by vector loads (pad lanes read the arrays' pads,
+          // and their Ap is zeroed below)
+          if constexpr (!CoefEarly<CM>::value)
+            cpre = group_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0, z - 1, (G.vmask >> (NV - 1)) & 1u);
+          const GroupCoef<T> &c = cpre;
 #pragma unroll
           for (int u = 0; u < NV; u++) {
             const T pl = u == 0 ? xl : pc.v[u - 1], pr = u == NV - 1 ? xr : pc.v[u + 1];
@@ -1133,7 +1153,11 @@ __global__ void __launch_bounds__(NT_UPD) k_update(Batch B) {
               m = I.precond ? ((const T *)I.diag)[(size_t)row0 * px + e[k] + u] : (T)1;
             }
             const T r = m * zk[u] - alpha * apv[u];
-            zk[u] = CM == COEF_PACKED ? r * mi : r / m;
+            // explicit FP32 storage: times the correctly rounded reciprocal
+            // (within an ulp of r / m, without a division per node)
+            if constexpr (CM == COEF_PACKED) zk[u] = r * mi;
+            else if constexpr (sizeof(T) == 4) zk[u] = r * __frcp_rn(m);
+            else zk[u] = r / m;
             rz += r * zk[u];
             rr += r * r;
           }
