@@ -14,6 +14,9 @@
 // the phase kernels built with FAST = true run these for every item.
 #pragma once
 
+#define PB_PRAGMA(x) _Pragma(#x)
+#define PB_UNROLL(n) PB_PRAGMA(unroll n)
+
 namespace pb {
 
 __device__ __forceinline__ float4 lds4(uint32_t a) {
@@ -179,6 +182,9 @@ __device__ __forceinline__ void fast_stencil(const Inst &I, const TileScal &S, i
   uint32_t cprev = 0, ccur = 0;
   float acc = 0.f;
   uint32_t rq = 0;  // ring slot of plane q
+#ifdef PB_FAST_UNROLL
+  PB_UNROLL(PB_FAST_UNROLL)
+#endif
   for (int q = 0; q < Q; ++q) {
     const uint32_t st = SR.st;
 #ifdef PB_FAULT_TEST
@@ -314,6 +320,9 @@ __device__ __forceinline__ void fast_update(const Inst &I, const TileScal &S, in
   float4 pm = f4(0, 0, 0, 0), pc = pm, pn = pm;
   uint32_t sbp = sbase;
   float rz = 0.f, rr = 0.f;
+#ifdef PB_FAST_UNROLL
+  PB_UNROLL(PB_FAST_UNROLL)
+#endif
   for (int q = 0; q < Q; ++q) {
     const uint32_t st = SR.st;
 #ifdef PB_FAULT_TEST
