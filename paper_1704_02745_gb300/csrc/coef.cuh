@@ -92,6 +92,46 @@ __device__ __forceinline__ GroupCoef<T> group_coef(const Inst &I, size_t e0, int
   return g;
 }
 
+// The same group's coefficients as the words loaded (BF16 storage): the
+// loads are issued here and their results first used by group_expand, so a
+// request made early does not wait for its data where it is made.
+struct GroupRaw16 {
+  uint2 ex, eym, eyp, ezm, ezp;
+  unsigned short exl;
+  float4 diag;
+};
+__device__ __forceinline__ GroupRaw16 group_raw16(const Inst &I, size_t e0, int k, bool last_ok) {
+  const __nv_bfloat16 *ex = (const __nv_bfloat16 *)I.ex, *ey = (const __nv_bfloat16 *)I.ey;
+  const __nv_bfloat16 *ez = (const __nv_bfloat16 *)I.ez;
+  const size_t px = I.px, ey0 = e0 + (size_t)k * px, plane = px * I.ny;
+  GroupRaw16 r;
+  r.ex = *(const uint2 *)(ex + e0);
+  r.exl = last_ok ? *(const unsigned short *)(ex + e0 + NV) : (unsigned short)0;  // bf16 +0
+  r.eym = *(const uint2 *)(ey + ey0);
+  r.eyp = *(const uint2 *)(ey + ey0 + px);
+  r.ezm = *(const uint2 *)(ez + e0);
+  r.ezp = *(const uint2 *)(ez + e0 + plane);
+  r.diag = *(const float4 *)((const float *)I.diag + e0);
+  return r;
+}
+__device__ __forceinline__ void bf16x4(uint2 v, float *out) {
+  const __nv_bfloat162 a = *(const __nv_bfloat162 *)&v.x, b = *(const __nv_bfloat162 *)&v.y;
+  out[0] = __low2float(a); out[1] = __high2float(a);
+  out[2] = __low2float(b); out[3] = __high2float(b);
+}
+__device__ __forceinline__ GroupCoef<float> group_expand(const GroupRaw16 &r) {
+  static_assert(NV == 4, "group loads are four-wide");
+  GroupCoef<float> g;
+  bf16x4(r.ex, g.ex);
+  g.ex[NV] = __uint_as_float((uint32_t)r.exl << 16);  // bf16 -> fp32 is exact: the high half
+  bf16x4(r.eym, g.eym);
+  bf16x4(r.eyp, g.eyp);
+  bf16x4(r.ezm, g.ezm);
+  bf16x4(r.ezp, g.ezp);
+  g.diag[0] = r.diag.x; g.diag[1] = r.diag.y; g.diag[2] = r.diag.z; g.diag[3] = r.diag.w;
+  return g;
+}
+
 // z = M^-1 r at node e (Jacobi), or z = r without preconditioner.
 template <typename T, int CM>
 __device__ __forceinline__ T zval(const Inst &I, size_t e, T r) {

@@ -44,14 +44,22 @@
 
 // Explicit coefficient storage: a group's coefficients are requested before
 // the stage wait and CTA barrier of the iteration that uses them (FP32
-// arrays: the 257^3 stencil pass 153 -> 134 us), or just before use (BF16
-// arrays, where requesting them early measured slower: 141 -> 150 us; and
-// FP64).  PB_COEF_EARLY = 0 keeps every storage on the late form.
+// arrays: the 257^3 stencil pass 153 -> 134 us), or just before use (FP64).
+// BF16 arrays are requested early as raw words and widened after the wait
+// (PB_BF16_EARLY; widening them where they are requested makes the thread
+// wait for the loads there, and measured slower: 141 -> 150 us).
+// PB_COEF_EARLY = 0 keeps every storage on the late form.
 #ifndef PB_COEF_EARLY
 #define PB_COEF_EARLY 1
 #endif
+#ifndef PB_BF16_EARLY
+#define PB_BF16_EARLY 1
+#endif
 namespace pb {
 template <int CM> struct CoefEarly { static constexpr bool value = PB_COEF_EARLY && CM == COEF_F32; };
+template <int CM> struct RawEarly {
+  static constexpr bool value = PB_COEF_EARLY && PB_BF16_EARLY && CM == COEF_BF16;
+};
 
 
 // ---------------------------------------------------------------------------
@@ -366,9 +374,13 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
     // iteration) are requested before the stage wait and the CTA barrier, so
     // their latency overlaps both
     GroupCoef<T> cpre;
+    GroupRaw16 craw;
     if constexpr (CoefEarly<CM>::value) {
       if (q >= 2 && G.vmask)
         cpre = group_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0, z - 1, (G.vmask >> (NV - 1)) & 1u);
+    } else if constexpr (RawEarly<CM>::value) {
+      if (q >= 2 && G.vmask)
+        craw = group_raw16(I, (size_t)(z - 1) * plane + ec0, z - 1, (G.vmask >> (NV - 1)) & 1u);
     }
     const uint32_t st = SR.st;
 #ifdef PB_FAULT_TEST
@@ -513,7 +525,9 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
           // explicit storage: the group's coefficients, requested at the top
           // of the iteration by vector loads (pad lanes read the arrays' pads,
           // and their Ap is zeroed below)
-          if constexpr (!CoefEarly<CM>::value)
+          if constexpr (RawEarly<CM>::value)
+            cpre = group_expand(craw);
+          else if constexpr (!CoefEarly<CM>::value)
             cpre = group_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0, z - 1, (G.vmask >> (NV - 1)) & 1u);
           const GroupCoef<T> &c = cpre;
 #pragma unroll
@@ -544,8 +558,7 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
               m = I.precond ? dgs.v[u] : m_unit;
               mi = mis.v[u];
             } else {
-              m = I.precond && ((G.vmask >> u) & 1u)
-                      ? ((const T *)I.diag)[(size_t)(z - 1) * plane + ec0 + u] : m_unit;
+              m = I.precond && ((G.vmask >> u) & 1u) ? cpre.diag[u] : m_unit;  // loaded with the group
             }
             const T r = m * z_prev.v[u] - alpha * a.v[u];
             zn.v[u] = CM == COEF_PACKED ? r * mi : r / m;
