@@ -166,8 +166,6 @@ struct Stage {
   double *phi = nullptr;
   size_t cap_phi = 0;
   double *d_energy = nullptr;      // device: the energies of the round's finished solves
-  double *d_dense = nullptr;       // device: their phi, unpacked (requested ones)
-  size_t cap_dense = 0;
   cudaEvent_t ev_graph = nullptr;  // after the graph and the scalar copy
   cudaEvent_t ev_done = nullptr;   // after the energy (and phi) copies
 };
@@ -210,7 +208,10 @@ struct pb_server {
   cudaStream_t setup_stream[SETUP_STREAMS] = {};
   // per slot: after the last compute-stream work on its grid (creation, or the
   // unpack and energy of its last solve); after its setup (setup stream)
-  std::vector<cudaEvent_t> ev_idle, ev_ready;
+  // per slot: ev_energy after the last solve's energy (its atoms may then be
+  // replaced), ev_idle after every read of the grid (phi read-out included),
+  // ev_ready after the next snapshot's setup
+  std::vector<cudaEvent_t> ev_idle, ev_ready, ev_energy;
   cudaGraphExec_t graph = nullptr;
 #ifndef PB_SERVER_TICKS
 #define PB_SERVER_TICKS 8
@@ -373,6 +374,7 @@ std::vector<int> admit(pb_server *s) {
       g->scal = s->d_scal + j;
       g->own_scal = false;
       cudaEventRecord(s->ev_idle[j], s->stream);  // its workspace clears
+      cudaEventRecord(s->ev_energy[j], s->stream);
       Slot &sl = s->slots[j];
       sl.g = g;
       sl.traj = rq.traj;
@@ -380,10 +382,11 @@ std::vector<int> admit(pb_server *s) {
       sl.has_solution = false;
     }
     Slot &sl = s->slots[j];
-    // this snapshot's setup stream waits for the last compute-stream work on
-    // its grid, which finished long before in the steady state
+    // this snapshot's setup stream waits for the energy of the grid's last
+    // solve (the setup replaces the atoms it reads); the read-out of that
+    // solve's phi may still run beside the setup kernels
     cudaStream_t sst = s->setup_stream[started.size() % pb_server::SETUP_STREAMS];
-    cudaStreamWaitEvent(sst, s->ev_idle[j], 0);
+    cudaStreamWaitEvent(sst, s->ev_energy[j], 0);
     // a new grid of a trajectory starts from the trajectory's latest solution
     // held by an idle grid of the same dims, if any (device-to-device copy)
     if (adm[i] == -1 && s->opts.warm_start && rq.traj >= 0) {
@@ -418,6 +421,7 @@ std::vector<int> admit(pb_server *s) {
       taken.push_back(rq.ticket);
       continue;
     }
+    cudaStreamWaitEvent(sst, s->ev_idle[j], 0);  // the last solve's phi is read out
     if (!sl.warm) {  // cold start: phi0 = 0 in both solution buffers
       cudaMemsetAsync(sl.g->x64, 0, sl.g->n_pad * sizeof(double), sst);
       cudaMemsetAsync(sl.g->x64b, 0, sl.g->n_pad * sizeof(double), sst);
@@ -586,21 +590,22 @@ bool run_graph(pb_server *s, bool stale) {
 // Queue the energy (and phi) of the solves that finished in the previous
 // round's graph, and free their slots.  The host has seen that graph finish,
 // and the running graph only skips these grids (their phase is DONE), so the
-// unpack and energy kernels and the device-to-host copies all run on the copy
-// stream, beside the running graph; a grid's next setup waits for its
-// kernels only (ev_idle).  Phi goes straight into page-locked caller memory,
-// else through the round's pinned staging.
+// energy kernels and the device-to-host copies run on the copy stream, beside
+// the running graph.  Phi is copied by the copy engine straight from the
+// padded solution (a pitched copy, rows of nx of px doubles), into page-locked
+// caller memory or else the round's pinned staging: no kernel, so the copy
+// does not wait for SMs that the graph's persistent kernels hold.  A grid's
+// next setup waits for its energy (ev_energy), its next solve for the copy of
+// its phi as well (ev_idle).
 // snap: the scalars the previous round's graph left; sg: this round's
 // staging set (idle: its last copies were waited for).
 bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector<int> &fin,
                     std::vector<Finishing> &out) {
-  size_t dense_total = 0, stage_total = 0;
+  size_t stage_total = 0;
   for (int j : fin) {
     const Slot &sl = s->slots[j];
-    if (!sl.req.phi_out) continue;
-    const size_t n = (size_t)sl.g->d.nx * sl.g->d.ny * sl.g->d.nz;
-    dense_total += n;
-    if (!sl.req.phi_pinned) stage_total += n;
+    if (sl.req.phi_out && !sl.req.phi_pinned)
+      stage_total += (size_t)sl.g->d.nx * sl.g->d.ny * sl.g->d.nz;
   }
   if (stage_total > sg.cap_phi) {
     if (sg.phi) cudaFreeHost(sg.phi);
@@ -613,13 +618,9 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
     }
     sg.cap_phi = stage_total;
   }
-  if (!grow(&sg.d_dense, &sg.cap_dense, std::max<size_t>(dense_total, 1))) {
-    s->worker_error = "out of device memory for phi";
-    return false;
-  }
-  struct Copy { double *dst; const double *src; size_t n; };
+  struct Copy { double *dst; const double *src; int slot; const pb_grid *g; };
   std::vector<Copy> copies;
-  size_t dense_off = 0, stage_off = 0;
+  size_t stage_off = 0;
   for (size_t k = 0; k < fin.size(); k++) {
     Slot &sl = s->slots[fin[k]];
     pb_grid *g = sl.g;
@@ -635,35 +636,30 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
       f.zero_phi = true;
       f.n = n;
     }
+    bool copied = false;
     if (!no_result && S.outer != -1) {
       const double *x = S.xbuf ? g->x64b : g->x64;
-      const double *phi = x;  // the padded solution itself, unless phi is wanted dense
-      int pitch = g->g.px;
+      launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, g->g.px, g->d.periodic, g->d.h,
+                    g->d.origin[0], g->d.origin[1], g->d.origin[2], x,
+                    g->scratch + SCR_ENERGY_PART, sg.d_energy + k, s->copy_stream);
+      s->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;
       if (sl.req.phi_out) {
-        double *dense = sg.d_dense + dense_off;
-        dense_off += n;
-        launch_unpack(x, dense, g->d.nx, g->d.ny, g->d.nz, g->g.px, s->copy_stream);
-        s->ctx->stats->launches += 1;
-        phi = dense;
-        pitch = g->d.nx;
         if (sl.req.phi_pinned) {
-          copies.push_back(Copy{sl.req.phi_out, dense, n});
+          copies.push_back(Copy{sl.req.phi_out, x, fin[k], g});
         } else {
           f.phi = sg.phi + stage_off;
           f.n = n;
           stage_off += n;
-          copies.push_back(Copy{f.phi, dense, n});
+          copies.push_back(Copy{f.phi, x, fin[k], g});
         }
         s->ctx->stats->d2h += n * sizeof(double);
+        copied = true;
       }
-      launch_energy(g->xyzq, g->n_atoms, g->d.nx, g->d.ny, g->d.nz, pitch, g->d.periodic, g->d.h,
-                    g->d.origin[0], g->d.origin[1], g->d.origin[2], phi,
-                    g->scratch + SCR_ENERGY_PART, sg.d_energy + k, s->copy_stream);
-      s->ctx->stats->launches += g->n_atoms > 0 ? 2 : 1;
     } else {
       cudaMemsetAsync(sg.d_energy + k, 0, sizeof(double), s->copy_stream);
     }
-    cudaEventRecord(s->ev_idle[fin[k]], s->copy_stream);  // after its unpack and energy
+    cudaEventRecord(s->ev_energy[fin[k]], s->copy_stream);
+    if (!copied) cudaEventRecord(s->ev_idle[fin[k]], s->copy_stream);
     f.req = std::move(sl.req);
     out.push_back(std::move(f));
     sl.busy = false;
@@ -677,8 +673,12 @@ bool queue_finished(pb_server *s, Stage &sg, const Scal *snap, const std::vector
   cudaMemcpyAsync(sg.energy, sg.d_energy, fin.size() * sizeof(double), cudaMemcpyDeviceToHost,
                   s->copy_stream);
   s->ctx->stats->d2h += fin.size() * sizeof(double);
-  for (const Copy &c : copies)
-    cudaMemcpyAsync(c.dst, c.src, c.n * sizeof(double), cudaMemcpyDeviceToHost, s->copy_stream);
+  for (const Copy &c : copies) {
+    const size_t row = (size_t)c.g->d.nx * sizeof(double);
+    cudaMemcpy2DAsync(c.dst, row, c.src, (size_t)c.g->g.px * sizeof(double), row,
+                      (size_t)c.g->d.ny * c.g->d.nz, cudaMemcpyDeviceToHost, s->copy_stream);
+    cudaEventRecord(s->ev_idle[c.slot], s->copy_stream);  // after the copy of its phi
+  }
   return cuda_ok(cudaEventRecord(sg.ev_done, s->copy_stream), s, "event");
 }
 
@@ -1130,23 +1130,32 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
   ok = ok && cudaMemset(s->d_scal, 0, MAX_SLOTS * sizeof(Scal)) == cudaSuccess;
   ok = ok && cudaMemset(s->d_err, 0, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
-  ok = ok && cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
 #ifndef PB_SETUP_PRIORITY
 #define PB_SETUP_PRIORITY 1
 #endif
+#ifndef PB_COPY_PRIORITY
+#define PB_COPY_PRIORITY 1
+#endif
   {
-    // setups first: a snapshot waiting for its setup is a slot the batch lacks
+    // setups first: a snapshot waiting for its setup is a slot the batch lacks;
+    // and a finished solve's unpack and energy, whose grid the trajectory's
+    // next snapshot waits for (the graph's persistent kernels would otherwise
+    // keep them off the SMs until the graph ends)
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
     const int prio = PB_SETUP_PRIORITY ? greatest : least;
     for (auto &x : s->setup_stream)
       ok = ok && cudaStreamCreateWithPriority(&x, cudaStreamNonBlocking, prio) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&s->copy_stream, cudaStreamNonBlocking,
+                                            PB_COPY_PRIORITY ? greatest : least) == cudaSuccess;
   }
   s->ev_idle.assign(MAX_SLOTS, nullptr);
   s->ev_ready.assign(MAX_SLOTS, nullptr);
+  s->ev_energy.assign(MAX_SLOTS, nullptr);
   for (int j = 0; ok && j < MAX_SLOTS; j++)
     ok = cudaEventCreateWithFlags(&s->ev_idle[j], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&s->ev_ready[j], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&s->ev_ready[j], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_energy[j], cudaEventDisableTiming) == cudaSuccess;
   for (Stage &sg : s->stage) {
     ok = ok && cudaMallocHost((void **)&sg.inst, MAX_SLOTS * sizeof(Inst)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&sg.counts, 4 * sizeof(int)) == cudaSuccess;
@@ -1213,7 +1222,6 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
     for (void *p : hp)
       if (p) cudaFreeHost(p);
     if (sg.d_energy) cudaFree(sg.d_energy);
-    if (sg.d_dense) cudaFree(sg.d_dense);
     if (sg.ev_graph) cudaEventDestroy(sg.ev_graph);
     if (sg.ev_done) cudaEventDestroy(sg.ev_done);
   }
@@ -1226,6 +1234,8 @@ extern "C" pb_status pb_server_destroy(pb_server *s) {
   for (auto e : s->ev_idle)
     if (e) cudaEventDestroy(e);
   for (auto e : s->ev_ready)
+    if (e) cudaEventDestroy(e);
+  for (auto e : s->ev_energy)
     if (e) cudaEventDestroy(e);
   if (s->ctx) {
     if (s->ctx->host_scal) cudaFreeHost(s->ctx->host_scal);
