@@ -267,6 +267,57 @@ __global__ void k_mg_update(size_t n, double alpha, const double *p, const doubl
 __global__ void k_mg_direction(size_t n, double beta, const double *z, double *p) {
   MG_LOOP(t, n) p[t] = fma(beta, p[t], z[t]);
 }
+// Scalars of the outer CG on the device, so that a graph of several
+// iterations runs without host round trips: rz = r.z, pap = p.Ap, rr = r.r,
+// rz_new = the next r.z; done stops the updates (convergence when rr <
+// stop2 = (tol ||b||)^2, the iteration cap, or breakdown), it counts the
+// iterations taken.
+struct MgScal {
+  double rz, pap, rr, rz_new, alpha, beta, stop2;
+  int it, done, status, max_iter;
+};
+__global__ void k_mg_alpha(MgScal *S) {  // alpha = r.z / p.Ap, or breakdown
+  if (S->done) return;
+  const double a = S->rz / S->pap;
+  if (!(S->pap > 0.0) || !isfinite(a)) {
+    S->status = PB_ERR_BREAKDOWN;
+    S->done = 1;
+    S->alpha = 0.0;
+  } else {
+    S->alpha = a;
+  }
+}
+__global__ void k_mg_check(MgScal *S) {  // after x, r are updated and r.r formed
+  if (S->done) return;
+  S->it++;
+  if (S->rr < S->stop2) {
+    S->status = PB_OK;
+    S->done = 1;
+  } else if (S->it >= S->max_iter) {
+    S->done = 1;
+  }
+}
+__global__ void k_mg_beta(MgScal *S) {  // beta = r.z (new) / r.z
+  if (S->done) return;
+  S->beta = S->rz_new / S->rz;
+  S->rz = S->rz_new;
+}
+// x += alpha p; r -= alpha Ap (alpha from the device scalars)
+__global__ void k_mg_update_dev(size_t n, const MgScal *S, const double *p, const double *ap, double *x,
+                                double *r) {
+  if (S->done) return;
+  const double alpha = S->alpha;
+  MG_LOOP(t, n) {
+    x[t] = fma(alpha, p[t], x[t]);
+    r[t] = fma(-alpha, ap[t], r[t]);
+  }
+}
+// p = z + beta p (beta from the device scalars)
+__global__ void k_mg_direction_dev(size_t n, const MgScal *S, const double *z, double *p) {
+  if (S->done) return;
+  const double beta = S->beta;
+  MG_LOOP(t, n) p[t] = fma(beta, p[t], z[t]);
+}
 // r = b - r (the Ap of x0 in r): b read from the padded layout
 __global__ void k_mg_initial_residual(MgDims d, int px, const double *b, double *r) {
   MG_LOOP(t, d.nodes()) {
@@ -293,7 +344,13 @@ struct pb_mg {
   };
   std::vector<Level> lv;
   double *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr, *z = nullptr, *part = nullptr,
-         *scal = nullptr;  // scal: pinned-free device doubles for dot results
+         *scal = nullptr;  // scal: device doubles for dot results
+  MgScal *S = nullptr;     // device scalars of the outer CG
+  MgScal *hS = nullptr;    // pinned host copy
+  // graph of MG_GRAPH_ITERS outer iterations (captured on the first solve)
+  cudaGraphExec_t graph = nullptr;
+  int graph_coef = -1;
+  unsigned long long graph_launches = 0;  // kernels per graph launch
   std::vector<void *> owned;
 };
 
@@ -305,6 +362,8 @@ static pb_status mg_alloc(pb_mg *m, void **p, size_t bytes) {
 
 void pb_mg_release(pb_mg *m) {
   if (!m) return;
+  if (m->graph) cudaGraphExecDestroy(m->graph);
+  if (m->hS) cudaFreeHost(m->hS);
   for (void *p : m->owned) cudaFree(p);
   delete m;
 }
@@ -339,8 +398,13 @@ static pb_status mg_build(pb_grid *g, pb_mg **out) {
   if ((st = mg_alloc(m, (void **)&m->x, n * 8)) || (st = mg_alloc(m, (void **)&m->r, n * 8)) ||
       (st = mg_alloc(m, (void **)&m->p, n * 8)) || (st = mg_alloc(m, (void **)&m->ap, n * 8)) ||
       (st = mg_alloc(m, (void **)&m->z, n * 8)) || (st = mg_alloc(m, (void **)&m->part, MG_DOT_CTAS * 8)) ||
-      (st = mg_alloc(m, (void **)&m->scal, 4 * 8)))
+      (st = mg_alloc(m, (void **)&m->scal, 4 * 8)) || (st = mg_alloc(m, (void **)&m->S, sizeof(MgScal))))
     return fail(st);
+  if (cudaMallocHost((void **)&m->hS, sizeof(MgScal)) != cudaSuccess) {
+    cudaGetLastError();
+    m->hS = nullptr;
+    return fail(pb_fail(PB_ERR_OOM, "multigrid: pinned scalars"));
+  }
   // level 0 from the grid, then coarsen
   const pb_mg::Level &L0 = m->lv[0];
   k_mg_level0<<<mg_blocks(L0.d.nex()), MG_NT, 0, s>>>(
@@ -394,8 +458,15 @@ static void vcycle(pb_mg *m, size_t l, cudaStream_t s, unsigned long long &launc
   launches += 3;
 }
 
-// The preconditioned CG of Sec. 2.2 with z = V(r), in FP64; scalars on the
-// host (few iterations).  Called by pb_pcg_solve for PB_PRECOND_GMG.
+// The preconditioned CG of Sec. 2.2 with z = V(r), in FP64.  Its scalars
+// stay on the device (MgScal): after the first direction, the host launches a
+// CUDA graph of MG_GRAPH_ITERS iterations (the operator, three dot products,
+// the updates and a V-cycle each: about 80 kernels) and reads the scalars
+// once per graph; iterations after convergence leave x and r as they are.
+// Called by pb_pcg_solve for PB_PRECOND_GMG.
+#ifndef MG_GRAPH_ITERS
+#define MG_GRAPH_ITERS 3
+#endif
 pb_status pb_gmg_solve(pb_grid *g, const pb_solve_opts *o, double *phi, pb_solve_info *info) {
   cudaStream_t s = g->ctx->stream;
   if (!g->mg) {
@@ -406,22 +477,25 @@ pb_status pb_gmg_solve(pb_grid *g, const pb_solve_opts *o, double *phi, pb_solve
   const pb_mg::Level &L0 = m->lv[0];
   const size_t n = L0.d.nodes();
   const int nb = mg_blocks(n);
-  unsigned long long launches = 0, n_dots = 0;
+  unsigned long long launches = 0, n_reads = 0;
   Inst I;
   pb_solve_opts oo = *o;
   pb_status st;
   if ((st = pb_ensure_workspace(g, MODE_F64))) return st;
-  if ((st = pb_make_inst(g, &oo, MODE_F64, pb_inner_coef(g, MODE_F64), I))) return st;
+  const int coef = pb_inner_coef(g, MODE_F64);
+  if ((st = pb_make_inst(g, &oo, MODE_F64, coef, I))) return st;
   CK(cudaMemcpyAsync(g->dinst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
-  double *hs = (double *)g->ctx->host_scal;  // pinned
-  auto dot = [&](const double *a, const double *b) -> double {
+  MgScal *S = m->S, *hS = m->hS;
+  auto dot = [&](const double *a, const double *b, double *out) {
     k_mg_dot_partial<<<MG_DOT_CTAS, MG_NT, 0, s>>>(n, a, b, m->part);
-    k_mg_dot_final<<<1, MG_NT, 0, s>>>(m->part, m->scal);
-    cudaMemcpyAsync(hs, m->scal, 8, cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+    k_mg_dot_final<<<1, MG_NT, 0, s>>>(m->part, out);
     launches += 2;
-    n_dots += 1;
-    return hs[0];
+  };
+  auto read_scal = [&]() -> pb_status {  // *hS = *S
+    CK(cudaMemcpyAsync(hS, S, sizeof(MgScal), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    n_reads++;
+    return PB_OK;
   };
   auto apply = [&](const double *u, double *au) -> cudaError_t {
     launches += 1;
@@ -433,6 +507,22 @@ pb_status pb_gmg_solve(pb_grid *g, const pb_solve_opts *o, double *phi, pb_solve
     k_mg_to_f64<<<nb, MG_NT, 0, s>>>(n, m->lv[0].z1, m->z);
     launches += 2;
   };
+  // One outer iteration, from p, r, z and rz: alpha, x and r, the stop test,
+  // z = V(r), beta, p.
+  auto iteration = [&]() -> cudaError_t {
+    cudaError_t e = apply(m->p, m->ap);
+    dot(m->p, m->ap, &S->pap);
+    k_mg_alpha<<<1, 1, 0, s>>>(S);
+    k_mg_update_dev<<<nb, MG_NT, 0, s>>>(n, S, m->p, m->ap, m->x, m->r);
+    dot(m->r, m->r, &S->rr);
+    k_mg_check<<<1, 1, 0, s>>>(S);
+    precondition();
+    dot(m->r, m->z, &S->rz_new);
+    k_mg_beta<<<1, 1, 0, s>>>(S);
+    k_mg_direction_dev<<<nb, MG_NT, 0, s>>>(n, S, m->z, m->p);
+    launches += 5;
+    return e != cudaSuccess ? e : cudaGetLastError();
+  };
   // x0 = phi (warm start) or 0; r = b - A x0
   if (o->warm_start) CK(cudaMemcpyAsync(m->x, phi, n * 8, cudaMemcpyDeviceToDevice, s));
   else CK(cudaMemsetAsync(m->x, 0, n * 8, s));
@@ -440,51 +530,72 @@ pb_status pb_gmg_solve(pb_grid *g, const pb_solve_opts *o, double *phi, pb_solve
   k_mg_initial_residual<<<nb, MG_NT, 0, s>>>(L0.d, g->g.px, g->b, m->r);
   launches += 1;
   const double bnorm = g->bnorm;
-  double rr = dot(m->r, m->r), rel = bnorm > 0 ? std::sqrt(rr) / bnorm : 0.0;
+  MgScal h0;
+  memset(&h0, 0, sizeof(h0));
+  h0.stop2 = (o->rel_tol * bnorm) * (o->rel_tol * bnorm);
+  h0.max_iter = o->max_iter;
+  h0.status = PB_ERR_NOT_CONVERGED;
+  *hS = h0;
+  CK(cudaMemcpyAsync(S, hS, sizeof(MgScal), cudaMemcpyHostToDevice, s));
+  dot(m->r, m->r, &S->rr);
+  if ((st = read_scal())) return st;
+  double rel = bnorm > 0 ? std::sqrt(hS->rr) / bnorm : 0.0;
   int it = 0, status = PB_OK;
   if (bnorm == 0.0) {
     CK(cudaMemsetAsync(m->x, 0, n * 8, s));
     rel = 0.0;
-  } else if (!(rel < o->rel_tol)) {
+  } else if (!(rel < o->rel_tol) && o->max_iter > 0) {
     precondition();
     CK(cudaMemcpyAsync(m->p, m->z, n * 8, cudaMemcpyDeviceToDevice, s));
-    double rz = dot(m->r, m->z);
-    status = PB_ERR_NOT_CONVERGED;
-    while (it < o->max_iter) {
-      CK(apply(m->p, m->ap));
-      const double pap = dot(m->p, m->ap);
-      const double alpha = rz / pap;
-      if (!(pap > 0.0) || !std::isfinite(alpha)) {
-        status = PB_ERR_BREAKDOWN;
-        break;
+    dot(m->r, m->z, &S->rz);
+    if (!m->graph || m->graph_coef != coef) {  // capture MG_GRAPH_ITERS iterations
+      if (m->graph) cudaGraphExecDestroy(m->graph);
+      m->graph = nullptr;
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      const unsigned long long before = launches;
+      for (int k = 0; k < MG_GRAPH_ITERS && e == cudaSuccess; k++) e = iteration();
+      m->graph_launches = launches - before;
+      launches = before;  // counted when the graph runs
+      const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return pb_fail(PB_ERR_CUDA, std::string("multigrid graph capture: ") +
+                                        cudaGetErrorString(e != cudaSuccess ? e : e2));
       }
-      k_mg_update<<<nb, MG_NT, 0, s>>>(n, alpha, m->p, m->ap, m->x, m->r);
-      launches += 1;
-      it++;
-      rr = dot(m->r, m->r);
-      rel = std::sqrt(rr) / bnorm;
-      if (rel < o->rel_tol) {
-        status = PB_OK;
-        break;
+      const cudaError_t e3 = cudaGraphInstantiate(&m->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) {
+        m->graph = nullptr;
+        return pb_fail(PB_ERR_CUDA, std::string("multigrid graph: ") + cudaGetErrorString(e3));
       }
-      precondition();
-      const double rz_new = dot(m->r, m->z);
-      k_mg_direction<<<nb, MG_NT, 0, s>>>(n, rz_new / rz, m->z, m->p);
-      launches += 1;
-      rz = rz_new;
+      m->graph_coef = coef;
     }
+    while (true) {
+      CK(cudaGraphLaunch(m->graph, s));
+      launches += m->graph_launches;
+      if ((st = read_scal())) return st;
+      if (hS->done) break;
+    }
+    it = hS->it;
+    status = hS->status;
+    rel = std::sqrt(hS->rr) / bnorm;
+  } else if (!(rel < o->rel_tol)) {
+    status = PB_ERR_NOT_CONVERGED;
   }
   // true residual of the result, then phi = x
   CK(apply(m->x, m->ap));
   CK(cudaMemcpyAsync(m->z, m->ap, n * 8, cudaMemcpyDeviceToDevice, s));
   k_mg_initial_residual<<<nb, MG_NT, 0, s>>>(L0.d, g->g.px, g->b, m->z);
   launches += 1;
-  const double rr_true = dot(m->z, m->z);
+  dot(m->z, m->z, &S->rr);
   CK(cudaMemcpyAsync(phi, m->x, n * 8, cudaMemcpyDeviceToDevice, s));
-  CK(cudaStreamSynchronize(s));
+  if ((st = read_scal())) return st;
+  const double rr_true = hS->rr;
   g->ctx->stats->launches += launches;
-  g->ctx->stats->h2d += sizeof(Inst);
-  g->ctx->stats->d2h += 8ull * n_dots;
+  g->ctx->stats->h2d += sizeof(Inst) + sizeof(MgScal);
+  g->ctx->stats->d2h += sizeof(MgScal) * n_reads + 8;
   if (info) {
     info->status = status;
     info->iterations = it;

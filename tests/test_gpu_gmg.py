@@ -70,6 +70,27 @@ def test_gmg_needs_far_fewer_iterations(pbm, ctx):
     assert mg.iterations * 3 < jac.iterations
 
 
+def test_gmg_iteration_cap_and_repeat(pbm, ctx):
+    """The outer iterations run as graphs of several iterations with the CG
+    scalars on the device: a cap that is not a multiple of the graph's length
+    stops exactly there, and a second solve (the graph reused) repeats the
+    first bit for bit."""
+    p = inputs.random_small(5, 41, 37, 33, n_atoms=90)
+    phi = torch.zeros(p.grid.shape, dtype=torch.float64, device="cuda")
+    with pbm.Grid(ctx, p.grid, p.atoms) as g:
+        for cap in (1, 4, 5):
+            phi.zero_()
+            info = g.solve(phi, check=False, precision="f64", precond="gmg", tol=1e-14, max_iter=cap)
+            assert info.status == pbm.PB_ERR_NOT_CONVERGED and info.iterations == cap
+        phi.zero_()
+        a = g.solve(phi, precision="f64", precond="gmg", tol=1e-9)
+        first = phi.clone()
+        phi.zero_()
+        b = g.solve(phi, precision="f64", precond="gmg", tol=1e-9)
+        assert a.status == 0 and b.status == 0 and a.iterations == b.iterations
+        assert torch.equal(first, phi)
+
+
 def test_gmg_argument_errors(pbm, ctx):
     p = inputs.random_small(3, 12, 12, 12, n_atoms=4)
     phi = torch.zeros(p.grid.shape, dtype=torch.float64, device="cuda")
