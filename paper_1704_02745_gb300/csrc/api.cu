@@ -310,7 +310,7 @@ pb_status pb_run_setup(pb_grid *g, int n_atoms, const double *xyz, const double 
   a.code = g->code;
   a.b = g->b;
   a.ghost = g->ghost;
-  a.scratch = g->scratch + SCR_SETUP;  // 256 partials of ||b||^2
+  a.scratch = g->scratch + SCR_SETUP;  // PB_FOLD_CTAS partials of ||b||^2
   a.bnorm2 = g->scratch + SCR_BNORM2;
   a.err = g->err;
   a.kappa = g->kappa;

@@ -94,6 +94,6 @@ pb_status pb_run_ticks(pb_grid *g, int mode, int coef, int ticks);
 enum : size_t {
   SCR_ENERGY = 0,        // energy result
   SCR_BNORM2 = 1,        // ||b||^2 from the setup
-  SCR_SETUP = 8,         // 256 partials of the setup's norm reduction
-  SCR_ENERGY_PART = 264  // per-CTA partials of the energy (one per 256 atoms)
+  SCR_SETUP = 8,                        // PB_FOLD_CTAS partials of the setup's norm reduction
+  SCR_ENERGY_PART = 8 + PB_FOLD_CTAS    // per-CTA partials of the energy (one per 256 atoms)
 };
