@@ -55,6 +55,9 @@
 #ifndef PB_BF16_EARLY
 #define PB_BF16_EARLY 1
 #endif
+#ifndef PB_BF16_AHEAD
+#define PB_BF16_AHEAD 1
+#endif
 namespace pb {
 template <int CM> struct CoefEarly { static constexpr bool value = PB_COEF_EARLY && CM == COEF_F32; };
 template <int CM> struct RawEarly {
@@ -368,6 +371,7 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
   int rq = 0;
   uint32_t st_issue = SR.st;
   for (int u = 0; u < min(NS, Q); ++u) st_issue = st_issue + 1 == NS ? 0 : st_issue + 1;
+  GroupRaw16 craw_next;  // BF16 words of the plane computed in the next iteration
   for (int q = 0; q < Q; ++q) {
     const int z = G.z0 - 1 + q;
     // explicit storage: the coefficients of plane z-1 (computed in this
@@ -379,8 +383,16 @@ __device__ __forceinline__ void cg_tile(const Inst &I, const TileScal &S, int ti
       if (q >= 2 && G.vmask)
         cpre = group_coef<T, CM>(I, (size_t)(z - 1) * plane + ec0, z - 1, (G.vmask >> (NV - 1)) & 1u);
     } else if constexpr (RawEarly<CM>::value) {
+#if PB_BF16_AHEAD
+      // a plane further ahead: plane z-1's words were requested in the
+      // previous iteration, plane z's are requested now
+      craw = craw_next;
+      if (q >= 1 && z < G.z1 && G.vmask)
+        craw_next = group_raw16(I, (size_t)z * plane + ec0, z, (G.vmask >> (NV - 1)) & 1u);
+#else
       if (q >= 2 && G.vmask)
         craw = group_raw16(I, (size_t)(z - 1) * plane + ec0, z - 1, (G.vmask >> (NV - 1)) & 1u);
+#endif
     }
     const uint32_t st = SR.st;
 #ifdef PB_FAULT_TEST
