@@ -256,17 +256,6 @@ __global__ void k_mg_dot_final(const double *part, double *out) {
   }
   if (threadIdx.x == 0) *out = red[0];
 }
-// x += alpha p; r -= alpha Ap
-__global__ void k_mg_update(size_t n, double alpha, const double *p, const double *ap, double *x, double *r) {
-  MG_LOOP(t, n) {
-    x[t] = fma(alpha, p[t], x[t]);
-    r[t] = fma(-alpha, ap[t], r[t]);
-  }
-}
-// p = z + beta p
-__global__ void k_mg_direction(size_t n, double beta, const double *z, double *p) {
-  MG_LOOP(t, n) p[t] = fma(beta, p[t], z[t]);
-}
 // Scalars of the outer CG on the device, so that a graph of several
 // iterations runs without host round trips: rz = r.z, pap = p.Ap, rr = r.r,
 // rz_new = the next r.z; done stops the updates (convergence when rr <
@@ -343,8 +332,7 @@ struct pb_mg {
     float *z0 = nullptr, *z1 = nullptr, *r = nullptr, *res = nullptr;
   };
   std::vector<Level> lv;
-  double *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr, *z = nullptr, *part = nullptr,
-         *scal = nullptr;  // scal: device doubles for dot results
+  double *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr, *z = nullptr, *part = nullptr;
   MgScal *S = nullptr;     // device scalars of the outer CG
   MgScal *hS = nullptr;    // pinned host copy
   // graph of MG_GRAPH_ITERS outer iterations (captured on the first solve)
@@ -398,7 +386,7 @@ static pb_status mg_build(pb_grid *g, pb_mg **out) {
   if ((st = mg_alloc(m, (void **)&m->x, n * 8)) || (st = mg_alloc(m, (void **)&m->r, n * 8)) ||
       (st = mg_alloc(m, (void **)&m->p, n * 8)) || (st = mg_alloc(m, (void **)&m->ap, n * 8)) ||
       (st = mg_alloc(m, (void **)&m->z, n * 8)) || (st = mg_alloc(m, (void **)&m->part, MG_DOT_CTAS * 8)) ||
-      (st = mg_alloc(m, (void **)&m->scal, 4 * 8)) || (st = mg_alloc(m, (void **)&m->S, sizeof(MgScal))))
+      (st = mg_alloc(m, (void **)&m->S, sizeof(MgScal))))
     return fail(st);
   if (cudaMallocHost((void **)&m->hS, sizeof(MgScal)) != cudaSuccess) {
     cudaGetLastError();
