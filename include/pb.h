@@ -77,7 +77,8 @@ enum {
 /* NONE: plain CG; JACOBI: M = diag A (Sec. 2.4); GMG: a geometric-multigrid
  * V-cycle (Sec. 2 lists GMG; Sec. 4 names multigrid as the next step): coarse
  * levels rediscretised at 2h with series-combined edges, trilinear transfer,
- * two damped-Jacobi sweeps before and after, the outer CG in FP64 and the
+ * two damped-Jacobi sweeps before and after, the outer CG in FP64 (its
+ * scalars on the device, iterations launched as CUDA graphs of three) and the
  * V-cycle in FP32 whatever opts->precision says; free-space boundary only,
  * not served by pb_server. */
 enum { PB_PRECOND_NONE = 0, PB_PRECOND_JACOBI = 1, PB_PRECOND_GMG = 2 };

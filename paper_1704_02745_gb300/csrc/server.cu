@@ -206,11 +206,10 @@ struct pb_server {
   // setups of admitted snapshots, several at once and beside the running graph
   static constexpr int SETUP_STREAMS = 4;
   cudaStream_t setup_stream[SETUP_STREAMS] = {};
-  // per slot: after the last compute-stream work on its grid (creation, or the
-  // unpack and energy of its last solve); after its setup (setup stream)
   // per slot: ev_energy after the last solve's energy (its atoms may then be
-  // replaced), ev_idle after every read of the grid (phi read-out included),
-  // ev_ready after the next snapshot's setup
+  // replaced), ev_idle after every read of the grid (creation, or the energy
+  // and phi read-out of its last solve), ev_ready after the next snapshot's
+  // setup (setup stream)
   std::vector<cudaEvent_t> ev_idle, ev_ready, ev_energy;
   cudaGraphExec_t graph = nullptr;
 #ifndef PB_SERVER_TICKS
@@ -1138,9 +1137,9 @@ extern "C" pb_status pb_server_create(pb_ctx *ctx, size_t budget, const pb_solve
 #endif
   {
     // setups first: a snapshot waiting for its setup is a slot the batch lacks;
-    // and a finished solve's unpack and energy, whose grid the trajectory's
+    // and a finished solve's energy and phi copy, whose grid the trajectory's
     // next snapshot waits for (the graph's persistent kernels would otherwise
-    // keep them off the SMs until the graph ends)
+    // keep the energy kernels off the SMs until the graph ends)
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
     const int prio = PB_SETUP_PRIORITY ? greatest : least;
