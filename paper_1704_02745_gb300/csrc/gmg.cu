@@ -149,9 +149,20 @@ struct MgOp {  // FP32 operator of one level (device pointers)
   const float *ex, *ey, *ez, *diag;
 };
 
+// Node indices in 32 bits (a grid has at most 2e9 nodes, checked when it is
+// created): 32-bit division costs a fraction of 64-bit division per node.
+__device__ __forceinline__ void mg_ijk(const MgDims &d, size_t t, uint32_t &i, uint32_t &j, uint32_t &k) {
+  const uint32_t tt = (uint32_t)t, row = tt / (uint32_t)d.nx;
+  i = tt - row * (uint32_t)d.nx;
+  k = row / (uint32_t)d.ny;
+  j = row - k * (uint32_t)d.ny;
+}
+
 __device__ __forceinline__ float mg_apply(const MgOp &A, const float *u, size_t t) {
   const int nx = A.d.nx, ny = A.d.ny, nz = A.d.nz;
-  const size_t i = t % nx, j = (t / nx) % ny, k = t / ((size_t)nx * ny);
+  uint32_t i32, j32, k32;
+  mg_ijk(A.d, t, i32, j32, k32);
+  const size_t i = i32, j = j32, k = k32;
   const size_t xr = (k * ny + j) * (nx + 1) + i, yr = (k * (ny + 1) + j) * nx + i, pl = (size_t)nx * ny;
   float s = 0.f;
   if (i > 0) s += A.ex[xr] * u[t - 1];
@@ -179,7 +190,9 @@ __global__ void k_mg_residual(MgOp A, const float *z, const float *r, float *res
 }
 __global__ void k_mg_restrict(MgDims f, MgDims c, const float *res, float *rc) {
   MG_LOOP(t, c.nodes()) {
-    const long I = t % c.nx, J = (t / c.nx) % c.ny, K = t / ((size_t)c.nx * c.ny);
+    uint32_t I32, J32, K32;
+    mg_ijk(c, t, I32, J32, K32);
+    const long I = I32, J = J32, K = K32;
     float s = 0.f;
     for (int dk = -1; dk <= 1; dk++) {
       const long k = 2 * K + dk;
@@ -202,7 +215,9 @@ __global__ void k_mg_restrict(MgDims f, MgDims c, const float *res, float *rc) {
 // (i+1)/2 (odd), per axis; coarse indices past the end are the zero ghost.
 __global__ void k_mg_prolong_add(MgDims f, MgDims c, const float *e, float *z) {
   MG_LOOP(t, f.nodes()) {
-    const long i = t % f.nx, j = (t / f.nx) % f.ny, k = t / ((size_t)f.nx * f.ny);
+    uint32_t i32, j32, k32;
+    mg_ijk(f, t, i32, j32, k32);
+    const long i = i32, j = j32, k = k32;
     float s = 0.f;
     for (int ck = 0; ck < 2; ck++) {
       const long K = ck ? (k + 1) / 2 : k / 2;
