@@ -11,17 +11,24 @@ static int blocks_for(size_t n, int nt) {
   return (int)(b < 152 * 32 ? (b ? b : 1) : 152 * 32);
 }
 
+// Node indices split in 32-bit arithmetic: a grid has at most 2e9 nodes
+// (checked when it is created), and 32-bit division costs a fraction of
+// 64-bit division per node.
+__device__ __forceinline__ size_t padded_of(size_t t, int nx, int px) {
+  const uint32_t tt = (uint32_t)t, row = tt / (uint32_t)nx;
+  return (size_t)row * px + (tt - row * (uint32_t)nx);
+}
 __global__ void k_pack(const double *dense, double *padded, int nx, int ny, int nz, int px) {
   const size_t n = (size_t)nx * ny * nz;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x)
-    padded[(t / nx) * px + t % nx] = dense[t];
+    padded[padded_of(t, nx, px)] = dense[t];
 }
 __global__ void k_unpack(const double *padded, double *dense, int nx, int ny, int nz, int px) {
   const size_t n = (size_t)nx * ny * nz;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x)
-    dense[t] = padded[(t / nx) * px + t % nx];
+    dense[t] = padded[padded_of(t, nx, px)];
 }
 
 cudaError_t launch_pack(const double *dense, double *padded, int nx, int ny, int nz, int px,
@@ -43,9 +50,10 @@ __global__ void k_apply(const Inst *dI, const T *u, T *au) {
   const size_t n = (size_t)nx * ny * nz;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % nx);
-    const size_t row = t / nx;
-    const int j = (int)(row % ny), k = (int)(row / ny);
+    const uint32_t tt = (uint32_t)t, row32 = tt / (uint32_t)nx, k32 = row32 / (uint32_t)ny;
+    const int i = (int)(tt - row32 * (uint32_t)nx);
+    const int j = (int)(row32 - k32 * (uint32_t)ny), k = (int)k32;
+    const size_t row = row32;
     const size_t e = row * I.px + i;
     const NodeCoef<T> c = node_coef<T, CM>(I, e, k);
     T s = 0;
